@@ -1,0 +1,169 @@
+/*
+ * swmm.h - memory-efficient Strassen-Winograd matrix multiplication on GB300.
+ *
+ * C ABI of the library.  It implements the schedules of Boyer, Dumas, Pernet
+ * and Zhou, "Memory efficient scheduling of Strassen-Winograd's matrix
+ * multiplication algorithm" (ISSAC 2009):
+ *
+ *   Section 2  : Winograd's 2x2 block algorithm (8 pre-additions, 7
+ *                products, 7 post-additions).
+ *   Table 1    : C <- AB with two temporaries (Douglas et al.).
+ *   Table 2    : C <- alpha AB + beta C with three temporaries
+ *                (Huss-Lederman et al.).
+ *   Tables 3-5 : C <- AB overwriting A and B (IP), A (OvL) or B (OvR).
+ *   Tables 6-8 : C <- alpha AB + beta C overwriting A and B (AcLR), B (AccR),
+ *                B12 and B21 (AcR, rectangular).
+ *   Table 9    : C <- alpha AB + beta C, read-only inputs, two temporaries
+ *                (Acc, Section 6).
+ *   Alg. 2     : IPMM, C <- AB with read-only inputs and no extra memory
+ *                (Section 7.1); temporaries are carved from C22.
+ *
+ * Conventions (every entry point):
+ *   - Matrices are row-major.  lda, ldb, ldc are leading dimensions in
+ *     elements, >= the number of columns.
+ *   - A, B, C are DEVICE pointers owned by the caller.  Mode SWMM_MODP:
+ *     int32 elements holding values in [0, p); outputs are canonical in
+ *     [0, p).  Mode SWMM_FP32: float elements.
+ *   - alpha and beta point to HOST scalars: uint32_t (reduced mod p by the
+ *     library) in SWMM_MODP mode, float in SWMM_FP32 mode.
+ *   - Calls are asynchronous on the handle's stream.  Workspace (the
+ *     schedules' temporaries X, Y, Z) is allocated stream-ordered from the
+ *     device's default memory pool for the duration of a call, sized exactly
+ *     to the plan's peak; its size is reported by swmm_get_stats.
+ *   - Argument errors are detected before any launch and return SWMM_EINVAL
+ *     (see swmm_last_error for the reason); a CUDA failure returns
+ *     SWMM_ECUDA.  Device-side waits are bounded: a kernel that gives up
+ *     records SWMM_ETIMEOUT, reported by swmm_sync.
+ *   - A and B must not overlap C.  A and B may overlap each other only for
+ *     the read-only schedules.
+ */
+#ifndef SWMM_H
+#define SWMM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* return codes */
+#define SWMM_OK 0
+#define SWMM_EINVAL 1
+#define SWMM_ENOMEM 2
+#define SWMM_EUNSUPPORTED 3
+#define SWMM_ECUDA 4
+#define SWMM_ETIMEOUT 5
+
+/* arithmetic modes */
+#define SWMM_MODP 0 /* exact arithmetic over Z/pZ, 2 < p < 2^16 */
+#define SWMM_FP32 1 /* float32 storage, 3 x bf16 split products (Section 2
+                       algorithm over the reals; accuracy mode) */
+
+/* schedules (the table numbers of the paper) */
+#define SWMM_CLASSICAL 0 /* one classical product, no Winograd level */
+#define SWMM_T1_DHSS 1   /* Table 1, C <- AB, read-only inputs */
+#define SWMM_T2_HLJJTT 2 /* Table 2, C <- aAB + bC, read-only inputs */
+#define SWMM_T3_IP 3     /* Table 3, C <- AB, overwrites A and B */
+#define SWMM_T4_OVL 4    /* Table 4, C <- AB, overwrites A */
+#define SWMM_T5_OVR 5    /* Table 5, C <- AB, overwrites B */
+#define SWMM_T6_ACLR 6   /* Table 6, C <- aAB + bC, overwrites A and B */
+#define SWMM_T7_ACCR 7   /* Table 7, C <- aAB + bC, overwrites B */
+#define SWMM_T8_ACR 8    /* Table 8, C <- aAB + bC, overwrites B12, B21 */
+#define SWMM_T9_ACC 9    /* Table 9, C <- aAB + bC, read-only inputs */
+#define SWMM_IPMM 10     /* Algorithm 2, C <- AB, read-only, no extra memory */
+#define SWMM_T4M_OVL 11  /* Section 5.1 variant of Table 4: overwrites A11, A21 */
+
+/* flags */
+#define SWMM_FLAG_UNFUSED 1u   /* run the table at every level down to
+                                  classical leaves (the literal schedule);
+                                  default fuses the last Winograd level
+                                  into one grouped leaf launch */
+#define SWMM_FLAG_SIMT_LEAF 2u /* leaves on a plain CUDA-core kernel instead
+                                  of the tcgen05 kernel (diagnostics) */
+
+typedef struct swmm_ctx *swmm_t;
+
+typedef struct {
+  int32_t mode;        /* SWMM_MODP or SWMM_FP32 */
+  uint32_t p;          /* modulus for SWMM_MODP: 2 < p < 65536 */
+  int32_t sched;       /* SWMM_CLASSICAL ... SWMM_T4M_OVL */
+  int32_t depth;       /* Winograd recursion levels (0 = classical) */
+  uint32_t flags;      /* SWMM_FLAG_* */
+  int32_t ipmm_cutoff; /* IPMM: classical base case once the C block is
+                          <= this size (0 = 1024) */
+  int32_t ipmm_acc;    /* IPMM accumulation schedule: SWMM_T2_HLJJTT
+                          (default, 0) or SWMM_T9_ACC (Section 7.1 end) */
+  int32_t reserved;
+} swmm_opts;
+
+typedef struct {
+  int64_t workspace_bytes;    /* device bytes allocated for temporaries */
+  int64_t plan_extra_elems;   /* peak temporary elements of the plan run */
+  int64_t paper_extra_elems;  /* the paper's count at the same depth for the
+                                 levels that materialise temporaries */
+  int64_t add_elems;          /* element operations of addition passes */
+  int64_t leaf_flops;         /* 2 m n k summed over leaf products */
+  int64_t leaf_launches;      /* leaf GEMM kernel launches */
+  int64_t ew_launches;        /* elementwise kernel launches */
+  int64_t leaf_products;      /* leaf products computed */
+  int64_t staging_bytes;      /* device bytes of tensor-core operand staging
+                                 (packed limb planes of the leaf operands;
+                                 not part of the schedules' temporaries) */
+  int64_t reserved[7];
+} swmm_stats;
+
+/* Create a handle bound to CUDA device `device` and stream `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  *h receives the
+ * handle; destroy it with swmm_destroy. */
+int swmm_create(swmm_t *h, int device, void *cuda_stream);
+int swmm_destroy(swmm_t h);
+int swmm_set_stream(swmm_t h, void *cuda_stream);
+
+/* C <- A B (m x k times k x n).  A and B are read-only: allowed schedules
+ * SWMM_CLASSICAL, SWMM_T1_DHSS, SWMM_IPMM (Table 1, Algorithm 2).
+ * IPMM needs m = n and k a multiple of n/2 at every level (Section 7.1);
+ * other shapes return SWMM_EINVAL. */
+int swmm_mul(swmm_t h, int64_t m, int64_t k, int64_t n,
+             const void *A, int64_t lda, const void *B, int64_t ldb,
+             void *C, int64_t ldc, const swmm_opts *opts);
+
+/* C <- alpha A B + beta C with read-only A and B: SWMM_CLASSICAL,
+ * SWMM_T2_HLJJTT (Table 2), SWMM_T9_ACC (Table 9, square). */
+int swmm_muladd(swmm_t h, int64_t m, int64_t k, int64_t n, const void *alpha,
+                const void *A, int64_t lda, const void *B, int64_t ldb,
+                const void *beta, void *C, int64_t ldc, const swmm_opts *opts);
+
+/* Schedules that may overwrite their inputs (Sections 5.1-5.3).
+ * beta == NULL: C <- alpha A B with SWMM_T3_IP (k = n <= m), SWMM_T4_OVL,
+ * SWMM_T4M_OVL, SWMM_T5_OVR (square).  beta != NULL: C <- alpha A B + beta C
+ * with SWMM_T6_ACLR, SWMM_T7_ACCR (square), SWMM_T8_ACR (any even shape).
+ * On return the overwritten operand blocks hold unspecified values:
+ *   IP, AcLR: all of A and B;  OvL: A;  OvLM: A11, A21;  OvR, AccR: B;
+ *   AcR: B12, B21.  Every other block is left bit-identical. */
+int swmm_mul_inplace(swmm_t h, int64_t m, int64_t k, int64_t n,
+                     void *A, int64_t lda, void *B, int64_t ldb,
+                     void *C, int64_t ldc, const void *alpha, const void *beta,
+                     const swmm_opts *opts);
+
+/* Peak temporary elements the plan for (m, k, n, opts) uses
+ * (*plan_elems) and the paper's count for the same levels (*paper_elems;
+ * Lemma 1 sums, Section 3).  No device work; h may be NULL. */
+int swmm_workspace_elems(swmm_t h, int64_t m, int64_t k, int64_t n,
+                         const swmm_opts *opts, int64_t *paper_elems,
+                         int64_t *plan_elems);
+
+/* Statistics of the last completed call on this handle. */
+int swmm_get_stats(swmm_t h, swmm_stats *out);
+
+/* Wait for the handle's stream and report device-side errors
+ * (SWMM_ETIMEOUT if a kernel's bounded wait gave up). */
+int swmm_sync(swmm_t h);
+
+const char *swmm_strerror(int code);
+/* Text of the last error on this handle (empty if none). */
+const char *swmm_last_error(swmm_t h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SWMM_H */

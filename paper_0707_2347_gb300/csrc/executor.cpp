@@ -1,0 +1,477 @@
+// Recursive executor of the schedules (Tables 1-9, Algorithm 2).
+//
+// A call D <- alpha L R (+ beta D) of kind k with depth d:
+//   * d == 0, or a dimension odd or < 2: one classical leaf product;
+//   * d == 1 with fusion on: the whole last Winograd level (Section 2) in one
+//     grouped tensor-core launch: seven products whose operands are the
+//     signed quadrant sums S1..S4 / T1..T4 formed while packing, and whose
+//     results are added into the four quadrants of D (the post-additions
+//     U1..U7) -- no temporary of this level is materialised;
+//   * otherwise: the rows of table k, in order, each ADD/COPY row one
+//     elementwise launch and each MUL row a recursive call of depth d - 1.
+// Temporaries of a level come from the handle's workspace (a bump allocator,
+// so the peak is exactly the sum over the live levels, Lemma 1) or, inside
+// Algorithm 2, are carved from C22.
+#include "executor.h"
+
+#include <algorithm>
+#include <cstring>
+
+namespace swmm {
+
+namespace {
+int64_t rup(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+bool aligned16(const void *p, int64_t ld) { return ((uintptr_t)p % 16 == 0) && (ld % 4 == 0); }
+}  // namespace
+
+Scalar Exec::one() const {
+  Scalar s;
+  s.u = 1;
+  s.f = 1.f;
+  return s;
+}
+Scalar Exec::neg(Scalar s) const {
+  Scalar r;
+  r.u = s.u == 0 ? 0 : p - s.u;
+  r.f = -s.f;
+  return r;
+}
+
+void Exec::check(cudaError_t e, const char *what) {
+  if (e != cudaSuccess && cuda_err == cudaSuccess) {
+    cuda_err = e;
+    fail = std::string(what) + ": " + cudaGetErrorString(e);
+  }
+}
+
+View Exec::alloc_tmp(int64_t rows, int64_t cols) {
+  View v;
+  v.rows = rows;
+  v.cols = cols;
+  v.ld = cols;
+  v.ptr = ws ? ws + ws_top : nullptr;
+  ws_top += rup(rows * cols * 4, 256);
+  ws_peak = std::max(ws_peak, ws_top);
+  tmp_elems += rows * cols;
+  tmp_peak_elems = std::max(tmp_peak_elems, tmp_elems);
+  return v;
+}
+
+void Exec::add(View d, View s1, View s2, Scalar c1, Scalar c2) {
+  add_elems += d.rows * d.cols;
+  ++ew_launches;
+  if (dry) return;
+  if (fp32)
+    check(launch_add_f(d, s1, s2, c1.f, c2.f, stream), "add");
+  else
+    check(launch_add(d, s1, s2, c1.u, c2.u, p, 0, stream), "add");
+}
+
+void Exec::scale(View d, bool keep, Scalar beta) {
+  ++ew_launches;
+  if (dry) return;
+  if (fp32)
+    check(launch_scale_f(d, keep ? beta.f : 0.f, stream), "scale");
+  else
+    check(launch_scale_modp(d, keep ? beta.u : 0u, p, stream), "scale");
+}
+
+// ----------------------------------------------------------------- leaves
+static void fill_common(GemmParams &P, const Exec &x, Scalar alpha, bool acc, Scalar beta, int epi) {
+  std::memset(&P, 0, sizeof(P));
+  P.epilogue = epi;
+  P.p = x.p ? x.p : 1;
+  P.alpha_u = alpha.u;
+  P.beta_u = beta.u;
+  P.alpha_f = alpha.f;
+  P.beta_f = beta.f;
+  P.barrett = x.p ? (uint32_t)(0x100000000ull / x.p) : 0;
+  P.inv_p = x.p ? 1.0f / (float)x.p : 0.f;
+  P.use_beta = acc ? 1 : 0;
+  P.err = x.err;
+}
+
+void Exec::leaf(Scalar alpha, bool acc, Scalar beta, View L, View R, View D) {
+  const int64_t m = L.rows, k = L.cols, n = R.cols;
+  if (m == 0 || n == 0) return;
+  if (k == 0) {  // empty inner dimension: D <- beta D (or 0)
+    scale(D, acc, beta);
+    return;
+  }
+  leaf_flops += 2 * m * n * k;
+  ++leaf_products;
+  ++leaf_launches;
+  GemmParams P;
+  fill_common(P, *this, alpha, acc, beta, EPI_STORE);
+  if (simt) {
+    if (dry) return;
+    SimtArgs S;
+    std::memset(&S, 0, sizeof(S));
+    S.a[0] = L.ptr;
+    S.lda[0] = L.ld;
+    S.sa[0] = 1;
+    S.na = 1;
+    S.b[0] = R.ptr;
+    S.ldb[0] = R.ld;
+    S.sb[0] = 1;
+    S.nb = 1;
+    S.t[0].ptr = D.ptr;
+    S.t[0].ld = D.ld;
+    S.t[0].sign = 1;
+    S.ntargets = 1;
+    S.M = (int)m;
+    S.N = (int)n;
+    S.K = (int)k;
+    check(launch_leaf_simt(S, P, mode, stream), "simt leaf");
+    return;
+  }
+  const int pl = planes_of(mode), bn = bn_of(mode);
+  const int64_t Mp = rup(m, kBM), Np = rup(n, bn), Kp = rup(k, kBK);
+  const int64_t abytes = rup(pl * Mp * Kp * 2, 1024), bbytes = rup(pl * Np * Kp * 2, 1024);
+  stage_need = std::max(stage_need, abytes + bbytes);
+  ew_launches += 2;
+  if (dry) return;
+  uint16_t *Ap = reinterpret_cast<uint16_t *>(stage);
+  uint16_t *Bp = reinterpret_cast<uint16_t *>(stage + abytes);
+  PackArgs pa;
+  std::memset(&pa, 0, sizeof(pa));
+  pa.src[0] = L.ptr;
+  pa.ld[0] = L.ld;
+  pa.nsrc = 1;
+  pa.out[0] = Ap;
+  pa.coef[0][0] = 1;
+  pa.nout = 1;
+  pa.rows = (int)m;
+  pa.cols = (int)k;
+  pa.prow_pad = (int)Mp;
+  pa.pcol_pad = (int)Kp;
+  pa.transpose = 0;
+  pa.p = p;
+  check(launch_pack(pa, mode, stream), "pack A");
+  pa.src[0] = R.ptr;
+  pa.ld[0] = R.ld;
+  pa.out[0] = Bp;
+  pa.rows = (int)k;
+  pa.cols = (int)n;
+  pa.prow_pad = (int)Np;
+  pa.pcol_pad = (int)Kp;
+  pa.transpose = 1;
+  check(launch_pack(pa, mode, stream), "pack B");
+  Product &pr = P.prod[0];
+  if (!make_tmap(&pr.ta, Ap, pl * Mp, Kp, kBM) || !make_tmap(&pr.tb, Bp, pl * Np, Kp, bn)) {
+    if (fail.empty()) fail = "tensor map encoding failed";
+    return;
+  }
+  pr.t[0].ptr = D.ptr;
+  pr.t[0].ld = D.ld;
+  pr.t[0].sign = 1;
+  pr.t[0].vec_ok = aligned16(D.ptr, D.ld);
+  pr.ntargets = 1;
+  pr.M = (int)m;
+  pr.N = (int)n;
+  pr.Kpad = (int)Kp;
+  pr.a_plane_rows = (int)Mp;
+  pr.b_plane_rows = (int)Np;
+  pr.tiles_m = (int)(Mp / kBM);
+  pr.tiles_n = (int)(Np / bn);
+  pr.tile_begin = 0;
+  P.nprod = 1;
+  P.total_tiles = pr.tiles_m * pr.tiles_n;
+  check(launch_gemm_tc(P, mode, num_sms, stream), "leaf gemm");
+}
+
+// One whole Winograd level (Section 2) with fused pre- and post-additions.
+// Products and where their signed, alpha-scaled results go:
+//   P1 = A11 B11 -> +C11 +C12 +C21 +C22     P5 = S1 T1 -> +C12 +C22
+//   P2 = A12 B21 -> +C11                     P6 = S2 T2 -> +C12 +C21 +C22
+//   P3 = S4 B22  -> +C12                     P7 = S3 T3 -> +C21 +C22
+//   P4 = A22 T4  -> -C21
+// with S1 = A21 + A22, S2 = S1 - A11, S3 = A11 - A21, S4 = A12 - S2 and
+// T1 = B12 - B11, T2 = B22 - T1, T3 = B22 - B12, T4 = T2 - B21, i.e.
+// C11 = U1, C12 = U5, C21 = U6, C22 = U7.
+void Exec::fused_level(Scalar alpha, bool acc, Scalar beta, View L, View R, View D) {
+  // operand coefficients over (X11, X12, X21, X22)
+  static const int8_t acoef[7][4] = {
+      {1, 0, 0, 0},    // A11
+      {0, 1, 0, 0},    // A12
+      {1, 1, -1, -1},  // S4 = A12 - A21 - A22 + A11
+      {0, 0, 0, 1},    // A22
+      {0, 0, 1, 1},    // S1 = A21 + A22
+      {-1, 0, 1, 1},   // S2 = A21 + A22 - A11
+      {1, 0, -1, 0},   // S3 = A11 - A21
+  };
+  static const int8_t bcoef[7][4] = {
+      {1, 0, 0, 0},    // B11
+      {0, 0, 1, 0},    // B21
+      {0, 0, 0, 1},    // B22
+      {1, -1, -1, 1},  // T4 = B22 - B12 + B11 - B21
+      {-1, 1, 0, 0},   // T1 = B12 - B11
+      {1, -1, 0, 1},   // T2 = B22 - B12 + B11
+      {0, -1, 0, 1},   // T3 = B22 - B12
+  };
+  // targets: quadrant index (0 = C11, 1 = C12, 2 = C21, 3 = C22) and sign
+  static const int8_t tgt[7][4] = {
+      {1, 1, 1, 1}, {1, 0, 0, 0}, {0, 1, 0, 0}, {0, 0, -1, 0}, {0, 1, 0, 1}, {0, 1, 1, 1}, {0, 0, 1, 1},
+  };
+  const int64_t hm = L.rows / 2, hk = L.cols / 2, hn = R.cols / 2;
+  View Lq[4] = {L.quad(0, 0), L.quad(0, 1), L.quad(1, 0), L.quad(1, 1)};
+  View Rq[4] = {R.quad(0, 0), R.quad(0, 1), R.quad(1, 0), R.quad(1, 1)};
+  View Dq[4] = {D.quad(0, 0), D.quad(0, 1), D.quad(1, 0), D.quad(1, 1)};
+  leaf_flops += 7 * 2 * hm * hn * hk;
+  leaf_products += 7;
+  ++leaf_launches;
+  // D <- beta D (or 0), as float32 for the reductions
+  ++ew_launches;
+  if (!dry) {
+    if (fp32)
+      check(launch_scale_f(D, acc ? beta.f : 0.f, stream), "fused prologue");
+    else
+      check(launch_to_float_scaled(D, acc ? beta.u : 0u, p, stream), "fused prologue");
+  }
+  GemmParams P;
+  fill_common(P, *this, alpha, false, beta, EPI_REDUCE);
+  if (simt) {
+    if (!dry) {
+      for (int i = 0; i < 7; ++i) {
+        SimtArgs S;
+        std::memset(&S, 0, sizeof(S));
+        for (int q = 0; q < 4; ++q) {
+          if (acoef[i][q]) {
+            S.a[S.na] = Lq[q].ptr;
+            S.lda[S.na] = Lq[q].ld;
+            S.sa[S.na++] = acoef[i][q];
+          }
+          if (bcoef[i][q]) {
+            S.b[S.nb] = Rq[q].ptr;
+            S.ldb[S.nb] = Rq[q].ld;
+            S.sb[S.nb++] = bcoef[i][q];
+          }
+          if (tgt[i][q]) {
+            S.t[S.ntargets].ptr = Dq[q].ptr;
+            S.t[S.ntargets].ld = Dq[q].ld;
+            S.t[S.ntargets++].sign = tgt[i][q];
+          }
+        }
+        S.M = (int)hm;
+        S.N = (int)hn;
+        S.K = (int)hk;
+        check(launch_leaf_simt(S, P, mode, stream), "simt fused leaf");
+      }
+    }
+  } else {
+    const int pl = planes_of(mode), bn = bn_of(mode);
+    const int64_t Mp = rup(hm, kBM), Np = rup(hn, bn), Kp = rup(hk, kBK);
+    const int64_t abytes = rup(pl * Mp * Kp * 2, 1024), bbytes = rup(pl * Np * Kp * 2, 1024);
+    stage_need = std::max(stage_need, 7 * (abytes + bbytes));
+    ew_launches += 2;
+    if (!dry) {
+      PackArgs pa, pb;
+      std::memset(&pa, 0, sizeof(pa));
+      std::memset(&pb, 0, sizeof(pb));
+      for (int q = 0; q < 4; ++q) {
+        pa.src[q] = Lq[q].ptr;
+        pa.ld[q] = Lq[q].ld;
+        pb.src[q] = Rq[q].ptr;
+        pb.ld[q] = Rq[q].ld;
+      }
+      pa.nsrc = pb.nsrc = 4;
+      pa.nout = pb.nout = 7;
+      for (int i = 0; i < 7; ++i) {
+        pa.out[i] = reinterpret_cast<uint16_t *>(stage + i * abytes);
+        pb.out[i] = reinterpret_cast<uint16_t *>(stage + 7 * abytes + i * bbytes);
+        for (int q = 0; q < 4; ++q) {
+          pa.coef[i][q] = acoef[i][q];
+          pb.coef[i][q] = bcoef[i][q];
+        }
+      }
+      pa.rows = (int)hm;
+      pa.cols = (int)hk;
+      pa.prow_pad = (int)Mp;
+      pa.pcol_pad = (int)Kp;
+      pa.transpose = 0;
+      pa.p = p;
+      pb.rows = (int)hk;
+      pb.cols = (int)hn;
+      pb.prow_pad = (int)Np;
+      pb.pcol_pad = (int)Kp;
+      pb.transpose = 1;
+      pb.p = p;
+      check(launch_pack(pa, mode, stream), "fused pack A");
+      check(launch_pack(pb, mode, stream), "fused pack B");
+      int tiles = 0;
+      for (int i = 0; i < 7; ++i) {
+        Product &pr = P.prod[i];
+        if (!make_tmap(&pr.ta, pa.out[i], pl * Mp, Kp, kBM) || !make_tmap(&pr.tb, pb.out[i], pl * Np, Kp, bn)) {
+          if (fail.empty()) fail = "tensor map encoding failed";
+          return;
+        }
+        pr.ntargets = 0;
+        for (int q = 0; q < 4; ++q) {
+          if (!tgt[i][q]) continue;
+          Target &T = pr.t[pr.ntargets++];
+          T.ptr = Dq[q].ptr;
+          T.ld = Dq[q].ld;
+          T.sign = tgt[i][q];
+          T.vec_ok = aligned16(Dq[q].ptr, Dq[q].ld);
+        }
+        pr.M = (int)hm;
+        pr.N = (int)hn;
+        pr.Kpad = (int)Kp;
+        pr.a_plane_rows = (int)Mp;
+        pr.b_plane_rows = (int)Np;
+        pr.tiles_m = (int)(Mp / kBM);
+        pr.tiles_n = (int)(Np / bn);
+        pr.tile_begin = tiles;
+        tiles += pr.tiles_m * pr.tiles_n;
+      }
+      P.nprod = 7;
+      P.total_tiles = tiles;
+      check(launch_gemm_tc(P, mode, num_sms, stream), "fused gemm");
+    }
+  }
+  ++ew_launches;
+  if (!dry && !fp32) check(launch_from_float_mod(D, p, stream), "fused epilogue");
+}
+
+// ------------------------------------------------------------- recursion
+void Exec::call(Kind k, Scalar alpha, bool acc, Scalar beta, View L, View R, View D, int depth, const Arena &ar) {
+  if (!ok()) return;
+  const int64_t m = L.rows, kk = L.cols, n = R.cols;
+  const bool split = depth > 0 && m >= 2 && kk >= 2 && n >= 2 && m % 2 == 0 && kk % 2 == 0 && n % 2 == 0;
+  if (!split) {
+    leaf(alpha, acc, beta, L, R, D);
+    return;
+  }
+  if (fused && depth == 1) {
+    fused_level(alpha, acc, beta, L, R, D);
+    return;
+  }
+  table(k, alpha, acc, beta, L, R, D, depth, ar);
+}
+
+void Exec::table(Kind k, Scalar alpha, bool acc, Scalar beta, View L, View R, View D, int depth,
+                 const Arena &ar) {
+  const KindInfo &K = kind_info(k);
+  const int64_t hm = L.rows / 2, hk = L.cols / 2, hn = R.cols / 2;
+  auto dims = [&](Shape s, int64_t &r, int64_t &c) {
+    r = s == SH_B ? hk : hm;
+    c = s == SH_A ? hk : hn;
+  };
+  // bounding box of every temporary over the values the table stores there
+  int64_t tr[3] = {0, 0, 0}, tc[3] = {0, 0, 0};
+  for (const Row &row : *K.table) {
+    if (row.dst >= LX && row.dst <= LZ) {
+      int64_t r, c;
+      dims(row.op == OP_MUL ? SH_C : row.shape, r, c);
+      const int t = row.dst - LX;
+      tr[t] = std::max(tr[t], r);
+      tc[t] = std::max(tc[t], c);
+    }
+  }
+  View tmp[3];
+  Arena sub = ar;
+  const int64_t mark_top = ws_top, mark_elems = tmp_elems;
+  if (ar.carve) {
+    const View &g = ar.region;
+    View qd[3] = {g.quad(0, 0), g.quad(0, 1), g.quad(1, 0)};
+    int used = 0;
+    for (int t = 0; t < 3; ++t) {
+      if (!tr[t]) continue;
+      if (tr[t] > qd[used].rows || tc[t] > qd[used].cols) {
+        if (fail.empty()) fail = "temporary does not fit in the carved scratch block";
+        return;
+      }
+      tmp[t] = qd[used++].sub(0, 0, tr[t], tc[t]);
+    }
+    sub.carve = true;
+    sub.region = g.quad(1, 1);
+  } else {
+    for (int t = 0; t < 3; ++t)
+      if (tr[t]) tmp[t] = alloc_tmp(tr[t], tc[t]);
+  }
+  View loc[NLOC];
+  const View Lq[4] = {L.quad(0, 0), L.quad(0, 1), L.quad(1, 0), L.quad(1, 1)};
+  const View Rq[4] = {R.quad(0, 0), R.quad(0, 1), R.quad(1, 0), R.quad(1, 1)};
+  const View Dq[4] = {D.quad(0, 0), D.quad(0, 1), D.quad(1, 0), D.quad(1, 1)};
+  for (int q = 0; q < 4; ++q) {
+    loc[A11 + q] = Lq[q];
+    loc[B11 + q] = Rq[q];
+    loc[C11 + q] = Dq[q];
+  }
+  loc[LX] = tmp[0];
+  loc[LY] = tmp[1];
+  loc[LZ] = tmp[2];
+  auto at = [&](Loc l, Shape s) -> View {
+    int64_t r, c;
+    dims(s, r, c);
+    const View &v = loc[l];
+    if (r > v.rows || c > v.cols) {
+      if (fail.empty()) fail = std::string(K.name) + ": value does not fit its location (shape precondition)";
+      return v;
+    }
+    return v.sub(0, 0, r, c);
+  };
+  auto coef = [&](Coef c) -> Scalar {
+    switch (c) {
+      case CF_ONE: return one();
+      case CF_NEG: return neg(one());
+      case CF_ALPHA: return alpha;
+      case CF_NALPHA: return neg(alpha);
+      case CF_BETA: return beta;
+      case CF_NBETA: return neg(beta);
+    }
+    return one();
+  };
+  for (const Row &row : *K.table) {
+    if (!ok()) return;
+    if (row.op == OP_ADD) {
+      add(at(row.dst, row.shape), at(row.s1, row.shape), at(row.s2, row.shape), coef(row.c1), coef(row.c2));
+    } else if (row.op == OP_COPY) {
+      View d = at(row.dst, row.shape);
+      ++ew_launches;
+      add_elems += d.rows * d.cols;
+      if (!dry) check(launch_copy(d, at(row.s1, row.shape), stream), "copy");
+    } else {
+      const KindInfo &S = kind_info(row.kind);
+      call(row.kind, coef(row.c1), S.accumulate, row.acc ? coef(row.cacc) : Scalar{}, at(row.s1, SH_A),
+           at(row.s2, SH_B), at(row.dst, SH_C), depth - 1, sub);
+    }
+  }
+  if (!ar.carve) {
+    ws_top = mark_top;
+    tmp_elems = mark_elems;
+  }
+}
+
+// Algorithm 2: C11, C12, C21 by n/2 x n/2 Winograd products over the 2k/n
+// block columns (Table 1 first, then the accumulating schedule), all
+// temporaries carved from C22; then C22 recursively; classical base case.
+void Exec::ipmm(View L, View R, View D, int depth, int64_t cutoff, Kind acc_kind) {
+  if (!ok()) return;
+  const int64_t n = D.rows, k = L.cols;
+  if (n <= cutoff || n % 2 || n < 2 || k % (n / 2)) {
+    leaf(one(), false, Scalar{}, L, R, D);
+    return;
+  }
+  const int64_t h = n / 2, nb = k / h;
+  int d = 0;
+  for (int64_t s = h; d < depth && s % 2 == 0 && s >= 2; s /= 2) ++d;
+  Arena ar;
+  ar.carve = true;
+  ar.region = D.quad(1, 1);
+  const View Cq[3] = {D.quad(0, 0), D.quad(0, 1), D.quad(1, 0)};
+  const int ai[3] = {0, 0, 1}, bj[3] = {0, 1, 0};
+  for (int i = 0; i < nb; ++i) {
+    for (int c = 0; c < 3; ++c) {
+      View Ab = L.sub(ai[c] * h, i * h, h, h);
+      View Bb = R.sub(i * h, bj[c] * h, h, h);
+      if (i == 0)
+        call(K_T1, one(), false, Scalar{}, Ab, Bb, Cq[c], d, ar);
+      else
+        call(acc_kind, one(), true, one(), Ab, Bb, Cq[c], d, ar);
+    }
+  }
+  ipmm(L.sub(h, 0, h, k), R.sub(0, h, k, h), D.quad(1, 1), depth, cutoff, acc_kind);
+}
+
+}  // namespace swmm

@@ -1,0 +1,70 @@
+// Recursive executor: walks the paper's schedule tables and lowers each row
+// to kernel launches on one stream, in row order.
+#pragma once
+
+#include <cstdint>
+#include <string>
+
+#include "schedules.h"
+#include "swmm_internal.h"
+
+namespace swmm {
+
+struct Scalar {
+  uint32_t u = 0;  // mod p value in [0, p)
+  float f = 0.f;   // FP32 mode value
+};
+
+// Where a recursion level takes its temporaries X, Y, Z from.
+struct Arena {
+  bool carve = false;  // true: quadrants of `region` (Algorithm 2 carves C22)
+  View region;
+};
+
+struct Exec {
+  // configuration
+  int mode = MODE_MODP2;
+  uint32_t p = 0;
+  bool fp32 = false;
+  bool fused = true;
+  bool simt = false;
+  bool dry = true;  // planning pass: count and size, launch nothing
+  cudaStream_t stream = nullptr;
+  int num_sms = 152;
+  int *err = nullptr;
+
+  // workspace for temporaries (bump allocator, bytes)
+  char *ws = nullptr;
+  int64_t ws_top = 0, ws_peak = 0;
+  // tensor-core operand staging (reused by every leaf launch, bytes)
+  char *stage = nullptr;
+  int64_t stage_need = 0;
+
+  // statistics
+  int64_t tmp_elems = 0, tmp_peak_elems = 0;
+  int64_t add_elems = 0, leaf_flops = 0, leaf_launches = 0, ew_launches = 0, leaf_products = 0;
+
+  cudaError_t cuda_err = cudaSuccess;
+  std::string fail;  // first failure description
+
+  bool ok() const { return cuda_err == cudaSuccess && fail.empty(); }
+
+  // D <- alpha L R (+ beta D when acc) by schedule `k` with `depth` levels.
+  void call(Kind k, Scalar alpha, bool acc, Scalar beta, View L, View R, View D, int depth, const Arena &ar);
+  // classical leaf product (one tensor-core launch)
+  void leaf(Scalar alpha, bool acc, Scalar beta, View L, View R, View D);
+  // Algorithm 2 (IPMM)
+  void ipmm(View L, View R, View D, int depth, int64_t cutoff, Kind acc_kind);
+
+ private:
+  void fused_level(Scalar alpha, bool acc, Scalar beta, View L, View R, View D);
+  void table(Kind k, Scalar alpha, bool acc, Scalar beta, View L, View R, View D, int depth, const Arena &ar);
+  void add(View d, View s1, View s2, Scalar c1, Scalar c2);
+  void scale(View d, bool keep, Scalar beta);  // d <- beta d, or 0
+  void check(cudaError_t e, const char *what);
+  View alloc_tmp(int64_t rows, int64_t cols);
+  Scalar one() const;
+  Scalar neg(Scalar s) const;
+};
+
+}  // namespace swmm

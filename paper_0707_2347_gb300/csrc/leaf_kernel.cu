@@ -1,0 +1,852 @@
+// Leaf products of the Strassen-Winograd recursion on the sm_103a tensor
+// cores (tcgen05 MMA, accumulators in tensor memory, operands staged by TMA).
+//
+// Two kernels:
+//
+// pack_* : operand staging.  One launch reads the four quadrants of a
+//   Winograd level's operand once and writes the seven signed combinations
+//   the level multiplies (A11, A12, A22, S1..S4 or B11, B21, B22, T1..T4,
+//   Section 2), already converted to the tensor-core number format, so the
+//   pre-additions never exist as int32/float blocks in HBM.  Exact
+//   arithmetic over Z/pZ on the floating-point tensor pipe (sm_103a has no
+//   integer tcgen05 MMA): each entry is brought to a centred representative
+//   and split into fp16 limbs of magnitude <= 128 (one limb when p <= 256,
+//   x = 256 h + l when p < 2^16); fp16 holds these integers exactly.  FP32
+//   mode splits each float into bf16 hi + lo.
+//
+// gemm_* : persistent warp-specialised GEMM over up to seven products (one
+//   fused Winograd level, or one classical leaf).  Warp 0 issues TMA loads
+//   of 128-byte-swizzled K-major tiles into a shared-memory ring, warp 1
+//   allocates tensor memory and issues tcgen05.mma from one thread, warps
+//   2-5 drain the accumulators.  Limb products are <= 2^14 in magnitude, so
+//   an fp32 accumulator summing at most 1024 of them stays below 2^24 and is
+//   exact; longer K is reduced mod p in place in tensor memory every 960 K.
+//   The epilogue recombines 2^16 hh + 2^8 (hl + lh) + ll mod p with exact
+//   fp32 operations, applies alpha / beta, and either stores (one target)
+//   or adds its signed contribution into up to four float targets with
+//   vector reductions (the post-additions U1..U7 of a fused level).
+// Every mbarrier wait is bounded (globaltimer); on expiry the kernel sets the
+// error word and unwinds, freeing its tensor memory.
+#include <cstdint>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "swmm_internal.h"
+
+namespace swmm {
+namespace dev {
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// ---------------------------------------------------------- conversions
+// x in [0, p) -> u = c + 32896 with c = x (mod p), c in [-32896, 32895]
+__device__ __forceinline__ uint32_t centre16(uint32_t x, uint32_t p) {
+  uint32_t t = x + 32896u;
+  return __viaddmin_u32(t, 0u - p, t);  // the wrapped t - p is huge unless x >= p - 32896
+}
+// x in [0, p), p <= 256 -> u = c + 128 with c = x (mod p), c in [-128, 127]
+__device__ __forceinline__ uint32_t centre8(uint32_t x, uint32_t p) {
+  uint32_t t = x + 128u;
+  return __viaddmin_u32(t, 0u - p, t);
+}
+__device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t sel) {
+  uint32_t d;
+  asm("prmt.b32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(sel));
+  return d;
+}
+// two offset values v in [0, 256] in the 16-bit halves -> fp16x2 of v - 128:
+// 0x6400 | v is the fp16 of 1024 + v, and 1024 + v - 1152 is exact.
+__device__ __forceinline__ uint32_t offset_to_h2(uint32_t packed) {
+  uint32_t h = packed | 0x64006400u;
+  __half2 r = __hsub2(*reinterpret_cast<__half2 *>(&h), __halves2half2(__ushort_as_half(0x6480), __ushort_as_half(0x6480)));
+  return *reinterpret_cast<uint32_t *>(&r);
+}
+// x in [0, 4p] -> [0, p)
+__device__ __forceinline__ uint32_t red4p(uint32_t x, uint32_t p) {
+  x = min(x, x - 2 * p);  // [0, 2p]
+  x = min(x, x - p);      // [0, p]
+  return min(x, x - p);
+}
+
+// 8 combined values -> plane 0 and plane 1 (16 bytes each)
+template <int MODE>
+__device__ __forceinline__ void convert8(const uint32_t (&x)[8], uint32_t p, uint4 &o0, uint4 &o1) {
+  uint32_t w0[4], w1[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    if (MODE == MODE_MODP2) {
+      uint32_t u0 = centre16(x[2 * j], p), u1 = centre16(x[2 * j + 1], p);
+      w0[j] = offset_to_h2(prmt(u0, u1, 0x6521u));               // h + 128 = u >> 8
+      w1[j] = offset_to_h2(prmt(u0, u1, 0x4400u) & 0x00FF00FFu);  // l + 128 = u & 255
+    } else if (MODE == MODE_MODP1) {
+      uint32_t u0 = centre8(x[2 * j], p), u1 = centre8(x[2 * j + 1], p);
+      w0[j] = offset_to_h2(prmt(u0, u1, 0x4400u) & 0x00FF00FFu);
+      w1[j] = 0;
+    } else {
+      float a = __uint_as_float(x[2 * j]), b = __uint_as_float(x[2 * j + 1]);
+      __nv_bfloat162 hi = __floats2bfloat162_rn(a, b);
+      uint32_t hb = *reinterpret_cast<uint32_t *>(&hi);
+      float ha = __uint_as_float(hb << 16), hbf = __uint_as_float(hb & 0xFFFF0000u);
+      __nv_bfloat162 lo = __floats2bfloat162_rn(a - ha, b - hbf);
+      w0[j] = hb;
+      w1[j] = *reinterpret_cast<uint32_t *>(&lo);
+    }
+  }
+  o0 = make_uint4(w0[0], w0[1], w0[2], w0[3]);
+  o1 = make_uint4(w1[0], w1[1], w1[2], w1[3]);
+}
+
+// signed combination of up to four source values for output o
+template <int MODE>
+__device__ __forceinline__ uint32_t combine(const PackArgs &a, int o, const uint32_t *v, uint32_t p) {
+  if (MODE == MODE_FP32) {
+    float s = 0.f;
+#pragma unroll
+    for (int q = 0; q < kMaxSrc; ++q) {
+      const int c = a.coef[o][q];
+      if (c > 0) s += __uint_as_float(v[q]);
+      if (c < 0) s -= __uint_as_float(v[q]);
+    }
+    return __float_as_uint(s);
+  } else {
+    uint32_t s = 0;
+#pragma unroll
+    for (int q = 0; q < kMaxSrc; ++q) {
+      const int c = a.coef[o][q];
+      if (c > 0) s += v[q];
+      if (c < 0) s += p - v[q];
+    }
+    return red4p(s, p);
+  }
+}
+
+// ------------------------------------------------------------------ pack
+// plain layout: thread = 8 consecutive columns of one row
+template <int MODE>
+__global__ void pack_rows_kernel(const __grid_constant__ PackArgs a) {
+  constexpr int PL = MODE == MODE_MODP1 ? 1 : 2;
+  const int64_t units = (int64_t)a.prow_pad * (a.pcol_pad / 8);
+  const int64_t plane = (int64_t)a.prow_pad * a.pcol_pad;
+  for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < units; u += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(u / (a.pcol_pad / 8));
+    const int c0 = (int)(u - (int64_t)r * (a.pcol_pad / 8)) * 8;
+    uint32_t v[kMaxSrc][8];
+#pragma unroll
+    for (int q = 0; q < kMaxSrc; ++q) {
+      if (q < a.nsrc) {
+        const char *base = a.src[q] + 4 * ((int64_t)r * a.ld[q] + c0);
+        const bool fast = r < a.rows && c0 + 8 <= a.cols && ((uintptr_t)base & 15) == 0;
+        if (fast) {
+          uint4 x0 = *reinterpret_cast<const uint4 *>(base), x1 = *reinterpret_cast<const uint4 *>(base + 16);
+          v[q][0] = x0.x; v[q][1] = x0.y; v[q][2] = x0.z; v[q][3] = x0.w;
+          v[q][4] = x1.x; v[q][5] = x1.y; v[q][6] = x1.z; v[q][7] = x1.w;
+        } else {
+#pragma unroll
+          for (int e = 0; e < 8; ++e)
+            v[q][e] = (r < a.rows && c0 + e < a.cols) ? reinterpret_cast<const uint32_t *>(base)[e] : 0u;
+        }
+      } else {
+#pragma unroll
+        for (int e = 0; e < 8; ++e) v[q][e] = 0;
+      }
+    }
+    for (int o = 0; o < a.nout; ++o) {
+      uint32_t x[8];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        uint32_t w[kMaxSrc];
+#pragma unroll
+        for (int q = 0; q < kMaxSrc; ++q) w[q] = v[q][e];
+        x[e] = combine<MODE>(a, o, w, a.p);
+      }
+      uint4 o0, o1;
+      convert8<MODE>(x, a.p, o0, o1);
+      uint16_t *dst = a.out[o] + (int64_t)r * a.pcol_pad + c0;
+      *reinterpret_cast<uint4 *>(dst) = o0;
+      if (PL == 2) *reinterpret_cast<uint4 *>(dst + plane) = o1;
+    }
+  }
+}
+
+// transposed layout: a CTA stages a 32 (source rows) x 64 (source cols) tile
+// of every source in shared memory, then writes packed rows = source cols.
+template <int MODE>
+__global__ void __launch_bounds__(256) pack_cols_kernel(const __grid_constant__ PackArgs a) {
+  constexpr int PL = MODE == MODE_MODP1 ? 1 : 2;
+  __shared__ uint32_t tile[kMaxSrc][32][65];
+  const int r0 = blockIdx.y * 32;  // source rows = packed columns (K)
+  const int c0 = blockIdx.x * 64;  // source cols = packed rows (N)
+  const int t = threadIdx.x;
+  const int64_t plane = (int64_t)a.prow_pad * a.pcol_pad;
+  // load: 32 rows x 64 cols = 512 vectors of 4; 2 per thread
+  for (int q = 0; q < a.nsrc; ++q) {
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      const int vi = t + 256 * i;
+      const int rr = vi >> 4, cc = (vi & 15) * 4;
+      const int gr = r0 + rr, gc = c0 + cc;
+      const char *base = a.src[q] + 4 * ((int64_t)gr * a.ld[q] + gc);
+      uint32_t w[4];
+      if (gr < a.rows && gc + 4 <= a.cols && ((uintptr_t)base & 15) == 0) {
+        uint4 x = *reinterpret_cast<const uint4 *>(base);
+        w[0] = x.x; w[1] = x.y; w[2] = x.z; w[3] = x.w;
+      } else {
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+          w[e] = (gr < a.rows && gc + e < a.cols) ? reinterpret_cast<const uint32_t *>(base)[e] : 0u;
+      }
+#pragma unroll
+      for (int e = 0; e < 4; ++e) tile[q][rr][cc + e] = w[e];
+    }
+  }
+  for (int q = a.nsrc; q < kMaxSrc; ++q)
+    for (int i = t; i < 32 * 64; i += 256) tile[q][i >> 6][i & 63] = 0;
+  __syncthreads();
+  // write: packed row c0 + (t >> 2), packed columns r0 + 8 * (t & 3) .. + 8
+  const int pc = t >> 2, pr8 = (t & 3) * 8;
+  for (int o = 0; o < a.nout; ++o) {
+    uint32_t x[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      uint32_t w[kMaxSrc];
+#pragma unroll
+      for (int q = 0; q < kMaxSrc; ++q) w[q] = tile[q][pr8 + e][pc];
+      x[e] = combine<MODE>(a, o, w, a.p);
+    }
+    uint4 o0, o1;
+    convert8<MODE>(x, a.p, o0, o1);
+    uint16_t *dst = a.out[o] + (int64_t)(c0 + pc) * a.pcol_pad + r0 + pr8;
+    *reinterpret_cast<uint4 *>(dst) = o0;
+    if (PL == 2) *reinterpret_cast<uint4 *>(dst + plane) = o1;
+  }
+}
+
+// ------------------------------------------------------------ GEMM glue
+constexpr int kThreads = 192;
+constexpr int kChunkKB = 15;                  // k-blocks between in-place reductions
+constexpr uint64_t kWaitNs = 4000000000ull;  // bounded wait: 4 s
+constexpr int kPlaneBytes = kBM * kBK * 2;    // 16 KB
+constexpr int kBBytes = 256 * kBK * 2;        // 32 KB
+
+template <int MODE>
+struct Cfg;
+template <>
+struct Cfg<MODE_MODP1> {
+  static constexpr int BN = 256, A_PLANES = 1, STAGES = 4, ACC_BUFS = 2, BUF_COLS = 256;
+};
+template <>
+struct Cfg<MODE_MODP2> {
+  static constexpr int BN = 128, A_PLANES = 2, STAGES = 3, ACC_BUFS = 1, BUF_COLS = 512;
+};
+template <>
+struct Cfg<MODE_FP32> {
+  static constexpr int BN = 128, A_PLANES = 2, STAGES = 3, ACC_BUFS = 2, BUF_COLS = 256;
+};
+template <int MODE>
+__host__ __device__ constexpr int stage_bytes() {
+  return Cfg<MODE>::A_PLANES * kPlaneBytes + kBBytes;
+}
+template <int MODE>
+__host__ __device__ constexpr int smem_bytes() {
+  return Cfg<MODE>::STAGES * stage_bytes<MODE>() + 1024 + 256;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *b, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count));
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t *b, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ uint64_t gtime() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+struct Ctl {
+  volatile int abort;
+  uint32_t tmem_base;
+};
+
+__device__ __forceinline__ bool wait_bar(uint64_t *b, uint32_t parity, Ctl *ctl, int *err) {
+  if (mbar_try(b, parity)) return true;
+  const uint64_t t0 = gtime();
+  for (uint32_t it = 0;; ++it) {
+    if (mbar_try(b, parity)) return true;
+    if ((it & 63) == 63) {
+      if (ctl->abort) return false;
+      if (gtime() - t0 > kWaitNs) {
+        ctl->abort = 1;
+        if (err) atomicExch(err, kErrTimeout);
+        return false;
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_commit(uint64_t *b) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(b))
+               : "memory");
+}
+__device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void tma_load(uint32_t dst, const CUtensorMap *map, int x, int y, uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          dst),
+      "l"(map), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float *v) {
+  uint32_t r[8];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+#pragma unroll
+  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const float *v) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr),
+               "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
+               "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
+               "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7]))
+               : "memory");
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row
+// core groups 1024 bytes apart (stride byte offset), descriptor version 1.
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+  uint64_t d = (uint64_t)((saddr & 0x3FFFF) >> 4);
+  d |= (uint64_t)1 << 16;            // leading byte offset (unused for this layout)
+  d |= (uint64_t)(1024 >> 4) << 32;  // stride byte offset
+  d |= (uint64_t)1 << 46;            // version
+  d |= (uint64_t)2 << 61;            // 128-byte swizzle
+  return d;
+}
+// Instruction descriptor, kind::f16: D fp32, A/B fp16 (fmt 0) or bf16 (1),
+// K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+__host__ __device__ constexpr uint32_t idesc_f16(int ab_fmt, int M, int N) {
+  return (1u << 4) | ((uint32_t)ab_fmt << 7) | ((uint32_t)ab_fmt << 10) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+
+struct TileInfo {
+  int pi, m0, n0;
+};
+template <int BN>
+__device__ __forceinline__ TileInfo decode(const GemmParams &P, int g) {
+  int pi = 0;
+  while (pi + 1 < P.nprod && g >= P.prod[pi + 1].tile_begin) ++pi;
+  const Product &pr = P.prod[pi];
+  const int local = g - pr.tile_begin;
+  const int G = 16;  // tile rows visited together (L2 reuse of B' columns)
+  const int per_group = G * pr.tiles_n;
+  const int gid = local / per_group;
+  const int first = gid * G;
+  const int gs = min(pr.tiles_m - first, G);
+  const int r = local - gid * per_group;
+  TileInfo t;
+  t.pi = pi;
+  t.m0 = (first + r % gs) * kBM;
+  t.n0 = (r / gs) * BN;
+  return t;
+}
+
+// --------------------------------------------------------- epilogue math
+struct Epi {
+  uint32_t p, m;
+  float pf, inv_p;
+  __device__ __forceinline__ float fr(float f) const {  // centred residue, exact |f| <= 2^24
+    const float MAGIC = 12582912.0f;                     // 1.5 * 2^23: rint via addition
+    float q = __fmaf_rn(f, inv_p, MAGIC) - MAGIC;
+    return __fmaf_rn(q, -pf, f);
+  }
+  __device__ __forceinline__ uint32_t canon(float r) const {  // r in (-p, p) -> [0, p)
+    r = r < 0.f ? r + pf : r;
+    return __float_as_uint(r + 12582912.0f) - 0x4B400000u;
+  }
+  __device__ __forceinline__ uint32_t mulmod(uint32_t u, uint32_t x) const {
+    uint32_t prod = u * x;
+    uint32_t q = __umulhi(prod, m);
+    uint32_t r = prod - q * p;
+    return min(r, r - p);
+  }
+};
+
+// write 4 consecutive mod p results (or 4 floats in FP32 mode) of one row
+template <bool FP>
+__device__ __forceinline__ void emit4(const GemmParams &P, const Product &pr, const Epi &E, int gr, int gc,
+                                      uint32_t (&v)[4]) {
+  if (P.epilogue == EPI_STORE) {
+    const Target &T = pr.t[0];
+    char *base = (char *)T.ptr + 4 * ((int64_t)gr * T.ld + gc);
+    const bool vec = T.vec_ok && gc + 4 <= pr.N;
+    if (P.use_beta) {
+      uint32_t s[4];
+      if (vec) {
+        uint4 q = *reinterpret_cast<const uint4 *>(base);
+        s[0] = q.x; s[1] = q.y; s[2] = q.z; s[3] = q.w;
+      } else {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) s[e] = gc + e < pr.N ? reinterpret_cast<const uint32_t *>(base)[e] : 0u;
+      }
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        if (FP) {
+          v[e] = __float_as_uint(__uint_as_float(v[e]) + P.beta_f * __uint_as_float(s[e]));
+        } else {
+          uint32_t w = v[e] + E.mulmod(P.beta_u, s[e]);
+          v[e] = min(w, w - E.p);
+        }
+      }
+    }
+    if (vec) {
+      *reinterpret_cast<uint4 *>(base) = make_uint4(v[0], v[1], v[2], v[3]);
+    } else {
+#pragma unroll
+      for (int e = 0; e < 4; ++e)
+        if (gc + e < pr.N) reinterpret_cast<uint32_t *>(base)[e] = v[e];
+    }
+  } else {
+    for (int t = 0; t < pr.ntargets; ++t) {
+      const Target &T = pr.t[t];
+      float f[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        if (FP)
+          f[e] = T.sign > 0 ? __uint_as_float(v[e]) : -__uint_as_float(v[e]);
+        else
+          f[e] = (float)(T.sign > 0 ? v[e] : (v[e] == 0 ? 0u : E.p - v[e]));
+      }
+      float *base = reinterpret_cast<float *>((char *)T.ptr + 4 * ((int64_t)gr * T.ld + gc));
+      if (T.vec_ok && gc + 4 <= pr.N) {
+        asm volatile("red.global.add.v4.f32 [%0], {%1,%2,%3,%4};" ::"l"(base), "f"(f[0]), "f"(f[1]), "f"(f[2]),
+                     "f"(f[3])
+                     : "memory");
+      } else {
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+          if (gc + e < pr.N) atomicAdd(base + e, f[e]);
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------- the GEMM
+template <int MODE>
+__global__ void __launch_bounds__(kThreads, 1) gemm_kernel(const __grid_constant__ GemmParams P) {
+  using C = Cfg<MODE>;
+  constexpr int BN = C::BN;
+  constexpr int SB = stage_bytes<MODE>();
+  constexpr bool modp = MODE != MODE_FP32;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + C::STAGES * SB);
+  uint64_t *full = bars;                      // [STAGES]
+  uint64_t *empty = bars + C::STAGES;         // [STAGES]
+  uint64_t *acc_full = bars + 2 * C::STAGES;  // [2]
+  uint64_t *acc_empty = acc_full + 2;         // [2]
+  uint64_t *drain_full = acc_empty + 2;
+  uint64_t *drain_empty = drain_full + 1;
+  uint64_t *final_bar = drain_empty + 1;
+  Ctl *ctl = reinterpret_cast<Ctl *>(final_bar + 1);
+
+  const int tid = threadIdx.x;
+  const int warp = tid >> 5;
+  const int lane = tid & 31;
+
+  if (tid == 0) {
+    for (int s = 0; s < C::STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&acc_full[b], 1);
+      mbar_init(&acc_empty[b], 128);
+    }
+    mbar_init(drain_full, 1);
+    mbar_init(drain_empty, 128);
+    mbar_init(final_bar, 1);
+    ctl->abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(&ctl->tmem_base)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = ctl->tmem_base;
+
+  if (warp == 0) {
+    // =============================== TMA producer ===============================
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0;
+      for (int g = blockIdx.x; g < P.total_tiles; g += gridDim.x) {
+        const TileInfo ti = decode<BN>(P, g);
+        const Product &pr = P.prod[ti.pi];
+        const int nkb = pr.Kpad / kBK;
+        bool bad = false;
+        for (int kb = 0; kb < nkb; ++kb) {
+          if (!wait_bar(&empty[stage], phase ^ 1, ctl, P.err)) {
+            bad = true;
+            break;
+          }
+          const uint32_t sA = smem_u32(smem + stage * SB);
+          const uint32_t sB = sA + C::A_PLANES * kPlaneBytes;
+          mbar_expect_tx(&full[stage], SB);
+          const int k0 = kb * kBK;
+          tma_load(sA, &pr.ta, k0, ti.m0, &full[stage]);
+          if (C::A_PLANES == 2) tma_load(sA + kPlaneBytes, &pr.ta, k0, pr.a_plane_rows + ti.m0, &full[stage]);
+          if (MODE == MODE_MODP1) {
+            tma_load(sB, &pr.tb, k0, ti.n0, &full[stage]);  // 256-row box
+          } else {
+            tma_load(sB, &pr.tb, k0, ti.n0, &full[stage]);
+            tma_load(sB + kPlaneBytes, &pr.tb, k0, pr.b_plane_rows + ti.n0, &full[stage]);
+          }
+          if (++stage == C::STAGES) {
+            stage = 0;
+            phase ^= 1;
+          }
+        }
+        if (bad) break;
+      }
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    // ================================ MMA issuer ================================
+    if (lane == 0) {
+      const uint32_t fmt = MODE == MODE_FP32 ? 1 : 0;
+      const uint32_t id256 = idesc_f16(fmt, kBM, 256);
+      const uint32_t id128 = idesc_f16(fmt, kBM, 128);
+      int stage = 0;
+      uint32_t phase = 0, tcount = 0, dcount = 0;
+      for (int g = blockIdx.x; g < P.total_tiles; g += gridDim.x, ++tcount) {
+        const TileInfo ti = decode<BN>(P, g);
+        const Product &pr = P.prod[ti.pi];
+        const int nkb = pr.Kpad / kBK;
+        const int buf = C::ACC_BUFS == 2 ? (int)(tcount & 1) : 0;
+        const uint32_t use = C::ACC_BUFS == 2 ? (tcount >> 1) : tcount;
+        if (!wait_bar(&acc_empty[buf], (use & 1) ^ 1, ctl, P.err)) break;
+        tc_fence_after();
+        const uint32_t d = tmem + (uint32_t)(buf * C::BUF_COLS);
+        bool bad = false;
+        for (int kb = 0; kb < nkb; ++kb) {
+          if (!wait_bar(&full[stage], phase, ctl, P.err)) {
+            bad = true;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t sA = smem_u32(smem + stage * SB);
+          const uint32_t sB = sA + C::A_PLANES * kPlaneBytes;
+#pragma unroll
+          for (int k = 0; k < kBK / 16; ++k) {
+            const uint32_t acc = (kb > 0 || k > 0) ? 1u : 0u;
+            const uint64_t a0 = sdesc(sA + 32 * k);
+            const uint64_t bd = sdesc(sB + 32 * k);
+            if (MODE == MODE_MODP1) {
+              tc_mma(d, a0, bd, id256, acc);
+            } else if (MODE == MODE_MODP2) {
+              const uint64_t a1 = sdesc(sA + kPlaneBytes + 32 * k);
+              tc_mma(d, a0, bd, id256, acc);        // [hh | hl]
+              tc_mma(d + 256, a1, bd, id256, acc);  // [lh | ll]
+            } else {
+              const uint64_t a1 = sdesc(sA + kPlaneBytes + 32 * k);
+              tc_mma(d, a0, bd, id256, acc);       // [hi*hi | hi*lo]
+              tc_mma(d + 128, a1, bd, id128, 1u);  // lo*hi onto the hi*lo half
+            }
+          }
+          tc_commit(&empty[stage]);
+          if (++stage == C::STAGES) {
+            stage = 0;
+            phase ^= 1;
+          }
+          if (modp && nkb > 16 && (kb + 1) % kChunkKB == 0 && kb + 1 < nkb) {
+            // keep every fp32 partial sum below 2^24: reduce mod p in place
+            tc_commit(drain_full);
+            if (!wait_bar(drain_empty, dcount & 1, ctl, P.err)) {
+              bad = true;
+              break;
+            }
+            ++dcount;
+            tc_fence_after();
+          }
+        }
+        if (bad) break;
+        tc_commit(&acc_full[buf]);
+      }
+      tc_commit(final_bar);  // no MMA may still run when the allocation is freed
+      wait_bar(final_bar, 0, ctl, nullptr);
+    }
+    __syncwarp();
+  } else {
+    // ================================= epilogue =================================
+    const int q4 = warp & 3;  // tensor-memory lane quadrant this warp may access
+    const int row = q4 * 32 + lane;
+    const uint32_t lane_addr = (uint32_t)((q4 * 32) << 16);
+    Epi E;
+    E.p = P.p;
+    E.m = P.barrett;
+    E.pf = (float)P.p;
+    E.inv_p = P.inv_p;
+    uint32_t tcount = 0, dcount = 0;
+    for (int g = blockIdx.x; g < P.total_tiles; g += gridDim.x, ++tcount) {
+      const TileInfo ti = decode<BN>(P, g);
+      const Product &pr = P.prod[ti.pi];
+      const int nkb = pr.Kpad / kBK;
+      const int buf = C::ACC_BUFS == 2 ? (int)(tcount & 1) : 0;
+      const uint32_t use = C::ACC_BUFS == 2 ? (tcount >> 1) : tcount;
+      const uint32_t d = tmem + lane_addr + (uint32_t)(buf * C::BUF_COLS);
+      if (modp && nkb > 16) {
+        const int ndrain = (nkb - 1) / kChunkKB;
+        bool bad = false;
+        for (int q = 0; q < ndrain; ++q, ++dcount) {
+          if (!wait_bar(drain_full, dcount & 1, ctl, P.err)) {
+            bad = true;
+            break;
+          }
+          tc_fence_after();
+          constexpr int cols = MODE == MODE_MODP2 ? 512 : 256;
+          for (int c = 0; c < cols; c += 8) {
+            float v[8];
+            tmem_ld8(d + c, v);
+            tmem_wait_ld();
+#pragma unroll
+            for (int e = 0; e < 8; ++e) v[e] = E.fr(v[e]);
+            tmem_st8(d + c, v);
+          }
+          tmem_wait_st();
+          tc_fence_before();
+          mbar_arrive(drain_empty);
+        }
+        if (bad) break;
+      }
+      if (!wait_bar(&acc_full[buf], use & 1, ctl, P.err)) break;
+      tc_fence_after();
+      const int gr = ti.m0 + row;
+      const bool row_ok = gr < pr.M;
+      if (MODE == MODE_MODP2) {
+        uint32_t res[BN];
+#pragma unroll
+        for (int c = 0; c < BN; c += 8) {
+          float hh[8], hl[8], lh[8], ll[8];
+          tmem_ld8(d + c, hh);
+          tmem_ld8(d + 128 + c, hl);
+          tmem_ld8(d + 256 + c, lh);
+          tmem_ld8(d + 384 + c, ll);
+          tmem_wait_ld();
+#pragma unroll
+          for (int e = 0; e < 8; ++e) {
+            // 2^16 hh + 2^8 (hl + lh) + ll, every intermediate an exact fp32 integer
+            const float s = E.fr(E.fr(hl[e]) + E.fr(lh[e]));
+            const float t1 = E.fr(__fmaf_rn(256.f, E.fr(hh[e]), s));
+            const float t2 = E.fr(__fmaf_rn(256.f, t1, E.fr(ll[e])));
+            res[c + e] = E.canon(t2);
+          }
+        }
+        tc_fence_before();
+        mbar_arrive(&acc_empty[buf]);  // tensor memory free: the next tile's MMAs may start
+        if (row_ok) {
+#pragma unroll
+          for (int c = 0; c < BN; c += 4) {
+            const int gc = ti.n0 + c;
+            if (gc < pr.N) {
+              uint32_t v[4] = {res[c], res[c + 1], res[c + 2], res[c + 3]};
+              if (P.alpha_u != 1) {
+#pragma unroll
+                for (int e = 0; e < 4; ++e) v[e] = E.mulmod(P.alpha_u, v[e]);
+              }
+              emit4<false>(P, pr, E, gr, gc, v);
+            }
+          }
+        }
+      } else {
+        // MODP1 / FP32: 8-column slices straight from tensor memory
+        constexpr int NC = MODE == MODE_FP32 ? 128 : BN;
+        for (int c = 0; c < NC; c += 8) {
+          float a8[8], b8[8];
+          tmem_ld8(d + c, a8);
+          if (MODE == MODE_FP32) tmem_ld8(d + 128 + c, b8);
+          tmem_wait_ld();
+          const int gc = ti.n0 + c;
+          if (!row_ok || gc >= pr.N) continue;
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int gc4 = gc + 4 * h;
+            if (gc4 < pr.N) {
+              uint32_t v[4];
+              if (MODE == MODE_MODP1) {
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                  v[e] = E.canon(E.fr(a8[4 * h + e]));
+                  if (P.alpha_u != 1) v[e] = E.mulmod(P.alpha_u, v[e]);
+                }
+                emit4<false>(P, pr, E, gr, gc4, v);
+              } else {
+#pragma unroll
+                for (int e = 0; e < 4; ++e) v[e] = __float_as_uint(P.alpha_f * (a8[4 * h + e] + b8[4 * h + e]));
+                emit4<true>(P, pr, E, gr, gc4, v);
+              }
+            }
+          }
+        }
+        tc_fence_before();
+        mbar_arrive(&acc_empty[buf]);
+      }
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem));
+  }
+}
+
+// ------------------------------------------------------------ SIMT leaf
+__global__ void leaf_simt_kernel(const __grid_constant__ SimtArgs A, const __grid_constant__ GemmParams P, int mode) {
+  const int r = blockIdx.y * 16 + threadIdx.y;
+  const int c = blockIdx.x * 16 + threadIdx.x;
+  if (r >= A.M || c >= A.N) return;
+  const uint64_t p = P.p;
+  uint64_t acc = 0;
+  double facc = 0.0;
+  for (int k = 0; k < A.K; ++k) {
+    if (mode != MODE_FP32) {
+      int64_t a = 0, b = 0;
+      for (int t = 0; t < A.na; ++t) {
+        int64_t v = *((const int32_t *)A.a[t] + (int64_t)r * A.lda[t] + k);
+        a += A.sa[t] > 0 ? v : -v;
+      }
+      for (int t = 0; t < A.nb; ++t) {
+        int64_t v = *((const int32_t *)A.b[t] + (int64_t)k * A.ldb[t] + c);
+        b += A.sb[t] > 0 ? v : -v;
+      }
+      a = ((a % (int64_t)p) + (int64_t)p) % (int64_t)p;
+      b = ((b % (int64_t)p) + (int64_t)p) % (int64_t)p;
+      acc = (acc + (uint64_t)a * (uint64_t)b) % p;
+    } else {
+      float a = 0.f, b = 0.f;
+      for (int t = 0; t < A.na; ++t) {
+        float v = *((const float *)A.a[t] + (int64_t)r * A.lda[t] + k);
+        a += A.sa[t] > 0 ? v : -v;
+      }
+      for (int t = 0; t < A.nb; ++t) {
+        float v = *((const float *)A.b[t] + (int64_t)k * A.ldb[t] + c);
+        b += A.sb[t] > 0 ? v : -v;
+      }
+      facc += (double)a * (double)b;
+    }
+  }
+  if (mode != MODE_FP32) {
+    uint64_t v = (acc * P.alpha_u) % p;
+    if (P.epilogue == EPI_STORE) {
+      uint32_t *dst = (uint32_t *)A.t[0].ptr + (int64_t)r * A.t[0].ld + c;
+      if (P.use_beta) v = (v + (uint64_t)P.beta_u * (*dst)) % p;
+      *dst = (uint32_t)v;
+    } else {
+      for (int t = 0; t < A.ntargets; ++t) {
+        float *dst = (float *)A.t[t].ptr + (int64_t)r * A.t[t].ld + c;
+        uint64_t w = A.t[t].sign > 0 ? v : (p - v) % p;
+        atomicAdd(dst, (float)w);
+      }
+    }
+  } else {
+    float v = P.alpha_f * (float)facc;
+    if (P.epilogue == EPI_STORE) {
+      float *dst = (float *)A.t[0].ptr + (int64_t)r * A.t[0].ld + c;
+      if (P.use_beta) v += P.beta_f * (*dst);
+      *dst = v;
+    } else {
+      for (int t = 0; t < A.ntargets; ++t) {
+        float *dst = (float *)A.t[t].ptr + (int64_t)r * A.t[t].ld + c;
+        atomicAdd(dst, (float)A.t[t].sign * v);
+      }
+    }
+  }
+}
+
+}  // namespace dev
+
+// ================================================================= host side
+template <int MODE>
+static cudaError_t pack_mode(const PackArgs &a, cudaStream_t s) {
+  if (a.prow_pad == 0 || a.pcol_pad == 0) return cudaSuccess;
+  if (a.transpose) {
+    dim3 grid(a.prow_pad / 64, a.pcol_pad / 32);
+    dev::pack_cols_kernel<MODE><<<grid, 256, 0, s>>>(a);
+  } else {
+    int64_t units = (int64_t)a.prow_pad * (a.pcol_pad / 8);
+    int64_t b = (units + 255) / 256;
+    int blocks = (int)(b > 152 * 16 ? 152 * 16 : b);
+    dev::pack_rows_kernel<MODE><<<blocks, 256, 0, s>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pack(const PackArgs &a, int mode, cudaStream_t s) {
+  switch (mode) {
+    case MODE_MODP1: return pack_mode<MODE_MODP1>(a, s);
+    case MODE_MODP2: return pack_mode<MODE_MODP2>(a, s);
+    case MODE_FP32: return pack_mode<MODE_FP32>(a, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <int MODE>
+static cudaError_t gemm_mode(const GemmParams &P, int num_sms, cudaStream_t s) {
+  constexpr int smem = dev::smem_bytes<MODE>();
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(dev::gemm_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  int grid = P.total_tiles < num_sms ? P.total_tiles : num_sms;
+  if (grid <= 0) return cudaSuccess;
+  dev::gemm_kernel<MODE><<<grid, dev::kThreads, smem, s>>>(P);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gemm_tc(const GemmParams &P, int mode, int num_sms, cudaStream_t s) {
+  switch (mode) {
+    case MODE_MODP1: return gemm_mode<MODE_MODP1>(P, num_sms, s);
+    case MODE_MODP2: return gemm_mode<MODE_MODP2>(P, num_sms, s);
+    case MODE_FP32: return gemm_mode<MODE_FP32>(P, num_sms, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_leaf_simt(const SimtArgs &A, const GemmParams &P, int mode, cudaStream_t s) {
+  if (A.M == 0 || A.N == 0) return cudaSuccess;
+  dim3 block(16, 16);
+  dim3 grid((A.N + 15) / 16, (A.M + 15) / 16);
+  dev::leaf_simt_kernel<<<grid, block, 0, s>>>(A, P, mode);
+  return cudaGetLastError();
+}
+
+}  // namespace swmm

@@ -1,0 +1,142 @@
+// Internal interfaces shared by the host executor and the CUDA kernels.
+#pragma once
+
+#include <cstdint>
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+namespace swmm {
+
+constexpr int kErrTimeout = 5;  // matches SWMM_ETIMEOUT
+
+// A strided 2-D block of 32-bit elements (int32 mod p or float).
+struct View {
+  char *ptr = nullptr;
+  int64_t rows = 0, cols = 0, ld = 0;  // ld in elements
+  char *at(int64_t r, int64_t c) const { return ptr + 4 * (r * ld + c); }
+  View sub(int64_t r0, int64_t c0, int64_t nr, int64_t nc) const {
+    View v;
+    v.ptr = at(r0, c0);
+    v.rows = nr;
+    v.cols = nc;
+    v.ld = ld;
+    return v;
+  }
+  // quadrant (i, j) in {0,1}^2 of an even-sized block (Section 2 split)
+  View quad(int i, int j) const { return sub(i * (rows / 2), j * (cols / 2), rows / 2, cols / 2); }
+};
+
+// Leaf arithmetic: one fp16 limb (p <= 256), two fp16 limbs (p < 2^16), or
+// bf16 hi/lo of a float (FP32 mode).
+enum Mode : int { MODE_MODP1 = 0, MODE_MODP2 = 1, MODE_FP32 = 2 };
+
+inline int planes_of(int mode) { return mode == MODE_MODP1 ? 1 : 2; }
+inline int bn_of(int mode) { return mode == MODE_MODP1 ? 256 : 128; }
+constexpr int kBM = 128;  // leaf tile rows
+constexpr int kBK = 64;   // leaf k-block (64 halves = one 128-byte row)
+
+// ------------------------------------------------------------------ packing
+// Operand staging for the tensor cores.  A pack launch reads up to four
+// source blocks Q_0..Q_3 (rows x cols, int32 mod p or float) and writes up
+// to seven outputs; output o is sum_s coef[o][s] * Q_s, converted to limb
+// planes of 16-bit values.  Plain layout: plane-major, then rows_pad rows of
+// cols_pad halves (K contiguous).  Transposed layout (B operands): the
+// packed row index is the source column.  Entries outside rows x cols are 0.
+constexpr int kMaxSrc = 4;
+constexpr int kMaxOut = 7;
+struct PackArgs {
+  const char *src[kMaxSrc];
+  int64_t ld[kMaxSrc];
+  int32_t nsrc;
+  uint16_t *out[kMaxOut];
+  int8_t coef[kMaxOut][kMaxSrc];
+  int32_t nout;
+  int32_t rows, cols;          // source extent
+  int32_t prow_pad, pcol_pad;  // packed extent (packed rows x packed cols)
+  int32_t transpose;
+  uint32_t p;
+};
+cudaError_t launch_pack(const PackArgs &a, int mode, cudaStream_t s);
+
+// ---------------------------------------------------------------- leaf GEMM
+// One product of a grouped leaf launch: P = A' x B' from packed operands.
+// Epilogue STORE: T0 <- alpha * P + beta * T0 (only target 0).
+// Epilogue REDUCE: for each target t, T_t += sign_t * alpha * P, where the
+// targets hold float32 values (mod p values are exact integers < 2^24).
+constexpr int kMaxTargets = 4;
+constexpr int kMaxProducts = 7;
+
+struct Target {
+  void *ptr;
+  int64_t ld;
+  int32_t sign;
+  int32_t vec_ok;  // 16-byte aligned rows
+};
+
+struct Product {
+  CUtensorMap ta;  // packed A': 2-D (K_pad halves) x (planes * M_pad rows)
+  CUtensorMap tb;  // packed B': 2-D (K_pad halves) x (planes * N_pad rows)
+  Target t[kMaxTargets];
+  int32_t ntargets;
+  int32_t M, N, Kpad;
+  int32_t a_plane_rows, b_plane_rows;  // M_pad, N_pad
+  int32_t tiles_m, tiles_n;
+  int32_t tile_begin;  // first global tile index of this product
+};
+
+enum Epilogue : int { EPI_STORE = 0, EPI_REDUCE = 1 };
+
+struct GemmParams {
+  Product prod[kMaxProducts];
+  int32_t nprod;
+  int32_t total_tiles;
+  int32_t epilogue;
+  uint32_t p;        // modulus (mod p modes)
+  uint32_t alpha_u;  // alpha mod p
+  uint32_t beta_u;   // beta mod p (STORE)
+  float alpha_f, beta_f;
+  uint32_t barrett;  // floor(2^32 / p)
+  float inv_p;       // 1/p rounded to float
+  int32_t use_beta;  // STORE: read T0 and add beta * T0
+  int *err;          // device error word (bounded waits)
+};
+
+// Encode a 2-D tensor map over a packed buffer (rows x kpad halves).
+bool make_tmap(CUtensorMap *map, const void *base, int64_t rows, int64_t kpad, int box_rows);
+
+cudaError_t launch_gemm_tc(const GemmParams &P, int mode, int num_sms, cudaStream_t s);
+
+// SIMT reference leaf on raw (unpacked) operands, for diagnostics: one
+// product, operands as signed sums of up to four views.
+struct SimtArgs {
+  const char *a[4];
+  int64_t lda[4];
+  int32_t sa[4], na;
+  const char *b[4];
+  int64_t ldb[4];
+  int32_t sb[4], nb;
+  Target t[kMaxTargets];
+  int32_t ntargets;
+  int32_t M, N, K;
+};
+cudaError_t launch_leaf_simt(const SimtArgs &A, const GemmParams &P, int mode, cudaStream_t s);
+
+// -------------------------------------------------------------- elementwise
+// dst <- c1 * s1 + c2 * s2 over an r x c block; coefficients are reduced
+// mod p (mod p mode) or used as floats.  dst may equal s1 or s2 exactly.
+cudaError_t launch_add(View dst, View s1, View s2, int64_t c1, int64_t c2, uint32_t p, int fp32,
+                       cudaStream_t s);
+cudaError_t launch_add_f(View dst, View s1, View s2, float c1, float c2, cudaStream_t s);
+// dst <- coef * dst (mod p) written as float32 (REDUCE prologue); coef 0
+// writes zeros.
+cudaError_t launch_to_float_scaled(View dst, uint32_t coef, uint32_t p, cudaStream_t s);
+// FP32: dst <- coef * dst (coef 0 writes zeros)
+cudaError_t launch_scale_f(View dst, float coef, cudaStream_t s);
+// dst(float, exact integer < 2^24) -> int32 mod p, canonical (REDUCE epilogue)
+cudaError_t launch_from_float_mod(View dst, uint32_t p, cudaStream_t s);
+// mod p: dst <- coef * dst mod p (int32 in place)
+cudaError_t launch_scale_modp(View dst, uint32_t coef, uint32_t p, cudaStream_t s);
+// dst <- src
+cudaError_t launch_copy(View dst, View src, cudaStream_t s);
+
+}  // namespace swmm

@@ -1,0 +1,203 @@
+"""Python binding of the C ABI in include/swmm.h (ctypes; marshalling only).
+
+Every step of the computation runs in the library's CUDA kernels; this
+module only turns torch tensors into (device pointer, leading dimension)
+pairs, passes the current torch CUDA stream, and checks return codes.
+Loading fails loudly when the shared library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "libswmm.so")
+
+# return codes
+OK, EINVAL, ENOMEM, EUNSUPPORTED, ECUDA, ETIMEOUT = range(6)
+# modes
+MODP, FP32 = 0, 1
+# schedules (paper table numbers)
+CLASSICAL, T1_DHSS, T2_HLJJTT, T3_IP, T4_OVL, T5_OVR = 0, 1, 2, 3, 4, 5
+T6_ACLR, T7_ACCR, T8_ACR, T9_ACC, IPMM, T4M_OVL = 6, 7, 8, 9, 10, 11
+SCHED_NAMES = {CLASSICAL: "classical", T1_DHSS: "T1", T2_HLJJTT: "T2", T3_IP: "IP", T4_OVL: "OvL",
+               T5_OVR: "OvR", T6_ACLR: "AcLR", T7_ACCR: "AccR", T8_ACR: "AcR", T9_ACC: "Acc",
+               IPMM: "IPMM", T4M_OVL: "OvLM"}
+# flags
+FLAG_UNFUSED, FLAG_SIMT_LEAF = 1, 2
+
+
+class SwmmError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"swmm error {code}: {msg}")
+        self.code = code
+
+
+class _Opts(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int32), ("p", ctypes.c_uint32), ("sched", ctypes.c_int32),
+                ("depth", ctypes.c_int32), ("flags", ctypes.c_uint32), ("ipmm_cutoff", ctypes.c_int32),
+                ("ipmm_acc", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class _Stats(ctypes.Structure):
+    _fields_ = [("workspace_bytes", ctypes.c_int64), ("plan_extra_elems", ctypes.c_int64),
+                ("paper_extra_elems", ctypes.c_int64), ("add_elems", ctypes.c_int64),
+                ("leaf_flops", ctypes.c_int64), ("leaf_launches", ctypes.c_int64),
+                ("ew_launches", ctypes.c_int64), ("leaf_products", ctypes.c_int64),
+                ("staging_bytes", ctypes.c_int64), ("reserved", ctypes.c_int64 * 7)]
+
+
+# every symbol include/swmm.h declares
+EXPORTS = ["swmm_create", "swmm_destroy", "swmm_set_stream", "swmm_mul", "swmm_muladd", "swmm_mul_inplace",
+           "swmm_workspace_elems", "swmm_get_stats", "swmm_sync", "swmm_strerror", "swmm_last_error"]
+
+_lib = None
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load libswmm.so (no GPU needed).  Raises if it was not built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} not found: build the CUDA library first "
+                          "(python -c 'import __graft_entry__ as g; g.build()')")
+    lib = ctypes.CDLL(path)
+    i64, vp, cvp = ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p
+    lib.swmm_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, vp]
+    lib.swmm_destroy.argtypes = [vp]
+    lib.swmm_set_stream.argtypes = [vp, vp]
+    lib.swmm_mul.argtypes = [vp, i64, i64, i64, cvp, i64, cvp, i64, vp, i64, ctypes.POINTER(_Opts)]
+    lib.swmm_muladd.argtypes = [vp, i64, i64, i64, cvp, cvp, i64, cvp, i64, cvp, vp, i64, ctypes.POINTER(_Opts)]
+    lib.swmm_mul_inplace.argtypes = [vp, i64, i64, i64, vp, i64, vp, i64, vp, i64, cvp, cvp,
+                                     ctypes.POINTER(_Opts)]
+    lib.swmm_workspace_elems.argtypes = [vp, i64, i64, i64, ctypes.POINTER(_Opts), ctypes.POINTER(i64),
+                                         ctypes.POINTER(i64)]
+    lib.swmm_get_stats.argtypes = [vp, ctypes.POINTER(_Stats)]
+    lib.swmm_sync.argtypes = [vp]
+    lib.swmm_strerror.argtypes = [ctypes.c_int]
+    lib.swmm_strerror.restype = ctypes.c_char_p
+    lib.swmm_last_error.argtypes = [vp]
+    lib.swmm_last_error.restype = ctypes.c_char_p
+    for name in EXPORTS:
+        getattr(lib, name).restype = getattr(lib, name).restype or ctypes.c_int
+    lib.swmm_strerror.restype = ctypes.c_char_p
+    lib.swmm_last_error.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+@dataclass
+class Opts:
+    mode: int = MODP
+    p: int = 65521
+    sched: int = T9_ACC
+    depth: int = 1
+    flags: int = 0
+    ipmm_cutoff: int = 0
+    ipmm_acc: int = 0
+
+    def c(self) -> _Opts:
+        return _Opts(self.mode, self.p, self.sched, self.depth, self.flags, self.ipmm_cutoff, self.ipmm_acc, 0)
+
+
+def _scalar(mode, v):
+    if v is None:
+        return None
+    if mode == MODP:
+        return ctypes.byref(ctypes.c_uint32(int(v) & 0xFFFFFFFF))
+    return ctypes.byref(ctypes.c_float(float(v)))
+
+
+def _mat(t, what):
+    """(device pointer, ld) of a 2-D row-major torch tensor."""
+    if t is None:
+        return None, 1
+    if t.dim() != 2 or (t.shape[1] > 1 and t.stride(1) != 1):
+        raise ValueError(f"{what} must be a 2-D row-major tensor")
+    return ctypes.c_void_p(t.data_ptr()), max(int(t.stride(0)), int(t.shape[1]), 1)
+
+
+class Handle:
+    """One library handle on one CUDA device.  Calls run asynchronously on
+    the current torch CUDA stream."""
+
+    def __init__(self, device: int = 0):
+        self.lib = load()
+        self.h = ctypes.c_void_p()
+        rc = self.lib.swmm_create(ctypes.byref(self.h), int(device), None)
+        if rc != OK:
+            raise SwmmError(rc, "swmm_create failed")
+        self.device = device
+
+    def close(self):
+        if self.h:
+            self.lib.swmm_destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _stream(self):
+        import torch
+        s = torch.cuda.current_stream(self.device).cuda_stream
+        self.lib.swmm_set_stream(self.h, ctypes.c_void_p(s))
+
+    def _check(self, rc):
+        if rc != OK:
+            msg = self.lib.swmm_last_error(self.h).decode() or self.lib.swmm_strerror(rc).decode()
+            raise SwmmError(rc, msg)
+
+    def mul(self, A, B, C, opts: Opts):
+        """C <- A B (read-only A, B)."""
+        self._stream()
+        a, lda = _mat(A, "A")
+        b, ldb = _mat(B, "B")
+        c, ldc = _mat(C, "C")
+        m, k = A.shape
+        n = B.shape[1]
+        self._check(self.lib.swmm_mul(self.h, m, k, n, a, lda, b, ldb, c, ldc, ctypes.byref(opts.c())))
+        return C
+
+    def muladd(self, alpha, A, B, beta, C, opts: Opts):
+        """C <- alpha A B + beta C (read-only A, B)."""
+        self._stream()
+        a, lda = _mat(A, "A")
+        b, ldb = _mat(B, "B")
+        c, ldc = _mat(C, "C")
+        m, k = A.shape
+        n = B.shape[1]
+        self._check(self.lib.swmm_muladd(self.h, m, k, n, _scalar(opts.mode, alpha), a, lda, b, ldb,
+                                         _scalar(opts.mode, beta), c, ldc, ctypes.byref(opts.c())))
+        return C
+
+    def mul_inplace(self, A, B, C, opts: Opts, alpha=1, beta=None):
+        """Schedules that may overwrite A and/or B (Tables 3-8)."""
+        self._stream()
+        a, lda = _mat(A, "A")
+        b, ldb = _mat(B, "B")
+        c, ldc = _mat(C, "C")
+        m, k = A.shape
+        n = B.shape[1]
+        self._check(self.lib.swmm_mul_inplace(self.h, m, k, n, a, lda, b, ldb, c, ldc, _scalar(opts.mode, alpha),
+                                              _scalar(opts.mode, beta), ctypes.byref(opts.c())))
+        return C
+
+    def workspace_elems(self, m, k, n, opts: Opts):
+        paper = ctypes.c_int64()
+        plan = ctypes.c_int64()
+        self._check(self.lib.swmm_workspace_elems(self.h, m, k, n, ctypes.byref(opts.c()), ctypes.byref(paper),
+                                                  ctypes.byref(plan)))
+        return paper.value, plan.value
+
+    def stats(self) -> dict:
+        s = _Stats()
+        self._check(self.lib.swmm_get_stats(self.h, ctypes.byref(s)))
+        return {f: getattr(s, f) for f, _ in _Stats._fields_ if f != "reserved"}
+
+    def sync(self):
+        self._check(self.lib.swmm_sync(self.h))

@@ -24,3 +24,14 @@ def pytest_collection_modifyitems(config, items):
     for it in items:
         if "gpu" in it.keywords:
             it.add_marker(skip)
+
+
+@pytest.fixture(scope="session")
+def handle():
+    """A library handle on cuda:0 (builds the library if needed)."""
+    import __graft_entry__ as g
+    g.build()
+    from paper_0707_2347_gb300 import swmm as S
+    h = S.Handle(0)
+    yield h
+    h.close()
