@@ -20,7 +20,7 @@ SHAPES = [(1, 1, 1), (128, 64, 128), (256, 128, 256), (300, 200, 170), (513, 100
 
 @pytest.mark.parametrize("p", [251, 65521])
 @pytest.mark.parametrize("shape", SHAPES)
-@pytest.mark.parametrize("simt", [False, True])
+@pytest.mark.parametrize("simt", [False, True], ids=["tc", "simt"])
 def test_classical_modp_exact(handle, p, shape, simt):
     m, k, n = shape
     A, B, C = modp_inputs(m, k, n, p)
