@@ -1,0 +1,346 @@
+#!/usr/bin/env python
+"""Benchmark of the memory-efficient Strassen-Winograd library on GB300.
+
+Default workload (the accumulate configuration): C <- A B + C over Z/65521,
+A, B, C 8192 x 8192 with entries uniform in [0, 65520], Table 9 (Acc,
+read-only inputs, two temporaries) at three Winograd levels, last level
+fused.  Metric: effective GOP/s = 2 m n k / t over the whole call.
+
+Printed JSON line (rank 0): value (device-resident inputs), e2e (host
+buffers, copies inside the timed region), the classical tcgen05 GEMM of the
+same library on the same inputs, the roofline of the leaf GEMM kernel
+(event-timed inside the timed region), peak extra device bytes against the
+paper's count, clocks sampled during the timed region, and a CPU baseline
+(the oracle on a bounded sample).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+       python bench.py --impl reference ...   (the CPU oracle on samples)
+Under torchrun every rank runs an independent replica (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synth  # noqa: E402
+
+MODP, FP32 = 0, 1
+CLASSICAL, T1, T2, IP, T9, IPMM = 0, 1, 2, 3, 9, 10
+
+WORKLOADS = {
+    # configs[1]: the accumulate schedule at 8192 (default)
+    "t9_8192_p65521": dict(desc="C<-AB+C over Z/65521, 8192^2, Table 9 (Acc) depth 3, fused last level",
+                           m=8192, k=8192, n=8192, mode=MODP, p=65521, sched=T9, depth=3, entry="muladd"),
+    "t9_16384_p65521": dict(desc="C<-AB+C over Z/65521, 16384^2, Table 9 (Acc) depth 2, fused last level",
+                            m=16384, k=16384, n=16384, mode=MODP, p=65521, sched=T9, depth=2, entry="muladd"),
+    "t9_16384_p65521_d1": dict(desc="C<-AB+C over Z/65521, 16384^2, Table 9 (Acc) depth 1 (fused level)",
+                               m=16384, k=16384, n=16384, mode=MODP, p=65521, sched=T9, depth=1, entry="muladd"),
+    "t1_512_p251": dict(desc="C<-AB over Z/251, 512^2, Table 1 depth 1", m=512, k=512, n=512, mode=MODP, p=251,
+                        sched=T1, depth=1, entry="mul"),
+    "ip_16384_p251": dict(desc="C<-AB over Z/251, 16384^2, Table 3 (IP) depth 2", m=16384, k=16384, n=16384,
+                          mode=MODP, p=251, sched=IP, depth=2, entry="inplace"),
+    "ipmm_16384_p251": dict(desc="C<-AB over Z/251, 16384^2, Algorithm 2 (IPMM), depth 2", m=16384, k=16384,
+                            n=16384, mode=MODP, p=251, sched=IPMM, depth=2, entry="mul"),
+    "t1_16384_p251": dict(desc="C<-AB over Z/251, 16384^2, Table 1 depth 2", m=16384, k=16384, n=16384, mode=MODP,
+                          p=251, sched=T1, depth=2, entry="mul"),
+    "fp32_t9_8192": dict(desc="C<-AB+C FP32 mode (3xbf16), 8192^2, Table 9 depth 2", m=8192, k=8192, n=8192,
+                         mode=FP32, p=0, sched=T9, depth=2, entry="muladd"),
+}
+DEFAULT = "t9_8192_p65521"
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return d["bf16_tflops"], d["bf16_tflops_sustained"], d["hbm_gbs"], "measured"
+    except Exception:
+        return 1900.0, 1700.0, 6800.0, "fallback"
+
+
+def make_inputs(w):
+    m, k, n = w["m"], w["k"], w["n"]
+    if w["mode"] == MODP:
+        p = w["p"]
+        return (synth.modp_matrix(synth.SEED_A, m, k, p), synth.modp_matrix(synth.SEED_B, k, n, p),
+                synth.modp_matrix(synth.SEED_C, m, n, p))
+    return (synth.normal_matrix(synth.SEED_A, m, k), synth.normal_matrix(synth.SEED_B, k, n),
+            synth.normal_matrix(synth.SEED_C, m, n))
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons while timing."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc is not None:
+            time.sleep(0.2)
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = max(mx, float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        loaded = [s for s in sm if s > 0.5 * mx] or sm
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(w, A, B, C, budget_s: float = 12.0):
+    """The oracle's classical product on a bounded sample of rows."""
+    from oracle import classical
+    m, k, n = w["m"], w["k"], w["n"]
+    rng = np.random.default_rng(5)
+    rows = 2
+    while True:
+        sel = rng.choice(m, rows, replace=False)
+        t0 = time.perf_counter()
+        if w["mode"] == MODP:
+            classical.rows_muladd_modp(sel, 1, A, B, 1, C, w["p"])
+        else:
+            classical.rows_muladd_f64(sel, 1.0, A, B, 1.0, C)
+        dt = time.perf_counter() - t0
+        if dt > budget_s / 4 or rows >= m:
+            break
+        rows = min(m, max(rows * 2, int(rows * budget_s / 4 / max(dt, 1e-3))))
+    gops = 2.0 * rows * n * k / dt / 1e9
+    return {"value": round(gops, 4), "unit": "GOP/s", "cores": 1, "kind": "oracle",
+            "sample": f"{rows} of {m} rows of the same product (numpy int64 matmul mod p, one core), {dt:.1f} s"}
+
+
+def run_reference(args, w, rank, world):
+    if rank != 0:
+        return
+    A, B, C = make_inputs(w)
+    from oracle import classical
+    m, k, n = w["m"], w["k"], w["n"]
+    rng = np.random.default_rng(6)
+    rows = max(1, min(m, 8))
+    ts = []
+    for step in range(args.warmup + args.steps):
+        sel = rng.choice(m, rows, replace=False)
+        t0 = time.perf_counter()
+        if w["mode"] == MODP:
+            classical.rows_muladd_modp(sel, 1, A, B, 1, C, w["p"])
+        else:
+            classical.rows_muladd_f64(sel, 1.0, A, B, 1.0, C)
+        if step >= args.warmup:
+            ts.append(time.perf_counter() - t0)
+    t = sum(ts) / len(ts)
+    value = 2.0 * rows * n * k / t / 1e9
+    line = {
+        "impl": "reference", "metric": "effective GOP/s (2mnk/t)", "value": round(value, 4), "unit": "GOP/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t * 1e3, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "int64 mod p" if w["mode"] == MODP else "f64", "data": "synthetic",
+        "config": {"workload": w["desc"], "m": m, "k": k, "n": n, "p": w["p"]},
+        "cpu_baseline": {"value": round(value, 4), "unit": "GOP/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{rows} rows of the {m}x{n} product per step"},
+        "e2e": {"value": round(value, 4), "unit": "GOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="swmm", choices=["swmm", "reference"])
+    ap.add_argument("--workload", default=DEFAULT, choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-classical", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    w = WORKLOADS[args.workload]
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, w, rank, world)
+        return
+
+    import torch
+    import __graft_entry__ as g
+    g.build()
+    from paper_0707_2347_gb300 import swmm as S
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    h = S.Handle(local)
+    m, k, n = w["m"], w["k"], w["n"]
+    A, B, C = make_inputs(w)
+    dA, dB = torch.from_numpy(A).to(dev), torch.from_numpy(B).to(dev)
+    dC0 = torch.from_numpy(C).to(dev)
+    dC = dC0.clone()
+    mode, p = w["mode"], w["p"]
+
+    def call(opts, Cdev, Adev=dA, Bdev=dB):
+        if w["entry"] == "muladd":
+            h.muladd(1, Adev, Bdev, 1, Cdev, opts)
+        elif w["entry"] == "mul":
+            h.mul(Adev, Bdev, Cdev, opts)
+        else:
+            h.mul_inplace(Adev, Bdev, Cdev, opts)
+
+    # the in-place schedules overwrite A and B: give them scratch copies
+    inplace = w["entry"] == "inplace"
+    sA = dA.clone() if inplace else dA
+    sB = dB.clone() if inplace else dB
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def timed(opts, steps, warmup, a=sA, b=sB):
+        for _ in range(warmup):
+            call(opts, dC, a, b)
+        h.sync()
+        h.leaf_timing(reset=True)
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            call(opts, dC, a, b)
+        e1.record()
+        barrier()
+        ms = e0.elapsed_time(e1) / steps
+        h.sync()
+        if dist is not None:
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms
+
+    opts = S.Opts(mode=mode, p=p or 65521, sched=w["sched"], depth=w["depth"], flags=S.FLAG_TIMING)
+    with Clocks(local) as clk:
+        ms = timed(opts, args.steps, args.warmup)
+    gemm_ms, gemm_launches, tensor_flops = h.leaf_timing(reset=True)
+    st = h.stats()
+    flops = 2.0 * m * n * k
+    value = world * flops / (ms * 1e-3) / 1e9
+    burst, sustained, hbm, peak_kind = peaks()
+    achieved = (tensor_flops / gemm_launches) / (gemm_ms / gemm_launches * 1e-3) / 1e12 if gemm_launches else 0.0
+
+    line = {
+        "metric": "effective GOP/s (2mnk/t)", "value": round(value, 2), "unit": "GOP/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "i32 mod p (fp16 limbs, fp32 accum)" if mode == MODP else "f32 (3xbf16)",
+        "data": "synthetic",
+        "config": {"workload": w["desc"], "m": m, "k": k, "n": n, "p": p, "schedule": S.SCHED_NAMES[w["sched"]],
+                   "depth": w["depth"], "l2": f"inputs {3 * m * n * 4 / 1e6:.0f} MB > 129 MB L2, no flush",
+                   "parallelism": f"replicas x{world}"},
+        "gpu_launches": int((st["leaf_launches"] + st["ew_launches"]) * args.steps),
+        "memory": {"workspace_bytes": st["workspace_bytes"], "plan_extra_elems": st["plan_extra_elems"],
+                   "paper_extra_elems_same_levels": st["paper_extra_elems"], "staging_bytes": st["staging_bytes"]},
+        "roofline": {"bound": "tensor", "achieved": round(achieved, 1), "peak": sustained, "unit": "TFLOP/s",
+                     "frac": round(achieved / sustained, 4), "traffic": None,
+                     "kernel": "gemm_kernel (leaf products, fp16 limb MMAs counted)",
+                     "peak_kind": f"{peak_kind} bf16 sustained", "launches_per_step": gemm_launches // max(args.steps, 1),
+                     "gemm_ms_per_step": round(gemm_ms / max(args.steps, 1), 4)},
+    }
+    line["clocks"] = clk.summary()
+
+    if not args.no_classical and w["sched"] != CLASSICAL:
+        dC.copy_(dC0)
+        copts = S.Opts(mode=mode, p=p or 65521, sched=CLASSICAL, depth=0, flags=S.FLAG_TIMING)
+        cms = timed(copts, args.steps, args.warmup)
+        cg_ms, cg_n, cg_fl = h.leaf_timing(reset=True)
+        cval = world * flops / (cms * 1e-3) / 1e9
+        line["classical"] = {"value": round(cval, 2), "ms_per_step": round(cms, 4),
+                             "gemm_tflops": round(cg_fl / (cg_ms * 1e-3) / 1e12, 1) if cg_ms else None}
+        line["speedup_vs_classical"] = round(value / cval, 4)
+
+    if not args.no_e2e:
+        pin = [torch.from_numpy(x).pin_memory() for x in (A, B, C)]
+        out = torch.empty_like(pin[2]).pin_memory()
+        opts_e = S.Opts(mode=mode, p=p or 65521, sched=w["sched"], depth=w["depth"])
+
+        def e2e_step():
+            dA.copy_(pin[0], non_blocking=True)
+            dB.copy_(pin[1], non_blocking=True)
+            dC.copy_(pin[2], non_blocking=True)
+            call(opts_e, dC, dA, dB)
+            out.copy_(dC, non_blocking=True)
+
+        for _ in range(args.warmup):
+            e2e_step()
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            e2e_step()
+        e1.record()
+        barrier()
+        ems = e0.elapsed_time(e1) / args.steps
+        h.sync()
+        line["e2e"] = {"value": round(world * flops / (ems * 1e-3) / 1e9, 2), "unit": "GOP/s",
+                       "h2d_bytes_per_step": int(A.nbytes + B.nbytes + C.nbytes), "d2h_bytes_per_step": int(C.nbytes),
+                       "ms_per_step": round(ems, 4)}
+    if rank == 0 and world == 1 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(w, A, B, C)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    h.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -80,6 +80,8 @@ extern "C" {
                                   into one grouped leaf launch */
 #define SWMM_FLAG_SIMT_LEAF 2u /* leaves on a plain CUDA-core kernel instead
                                   of the tcgen05 kernel (diagnostics) */
+#define SWMM_FLAG_TIMING 4u    /* record a CUDA event pair around every leaf
+                                  GEMM launch (read with swmm_leaf_timing) */
 
 typedef struct swmm_ctx *swmm_t;
 
@@ -151,6 +153,16 @@ int swmm_mul_inplace(swmm_t h, int64_t m, int64_t k, int64_t n,
 int swmm_workspace_elems(swmm_t h, int64_t m, int64_t k, int64_t n,
                          const swmm_opts *opts, int64_t *paper_elems,
                          int64_t *plan_elems);
+
+/* Leaf GEMM timing recorded by calls made with SWMM_FLAG_TIMING since the
+ * last reset.  Waits for the handle's stream, then returns the summed
+ * event-measured duration of those launches (*gemm_ms), their number
+ * (*launches) and the tensor-pipe flops they executed (*tensor_flops:
+ * 2 m n k per product times the limb products per product: 1 for p <= 256,
+ * 4 for larger p, 3 in SWMM_FP32 mode).  reset != 0 clears the record
+ * afterwards.  Any output pointer may be NULL. */
+int swmm_leaf_timing(swmm_t h, int reset, double *gemm_ms, int64_t *launches,
+                     double *tensor_flops);
 
 /* Statistics of the last completed call on this handle. */
 int swmm_get_stats(swmm_t h, swmm_stats *out);

@@ -48,6 +48,33 @@ bool make_tmap(CUtensorMap *map, const void *base, int64_t rows, int64_t kpad, i
 
 using namespace swmm;
 
+#include <vector>
+
+struct EventTimer : swmm::TimingHook {
+  std::vector<cudaEvent_t> ev;  // pairs: 2i = begin, 2i + 1 = end
+  std::vector<double> flops;
+  size_t used = 0;  // pairs recorded since the last reset
+  void begin(cudaStream_t s) override {
+    if (2 * used + 2 > ev.size()) {
+      cudaEvent_t a, b;
+      cudaEventCreate(&a);
+      cudaEventCreate(&b);
+      ev.push_back(a);
+      ev.push_back(b);
+      flops.push_back(0.0);
+    }
+    cudaEventRecord(ev[2 * used], s);
+  }
+  void end(cudaStream_t s, double f) override {
+    cudaEventRecord(ev[2 * used + 1], s);
+    flops[used] = f;
+    ++used;
+  }
+  ~EventTimer() override {
+    for (cudaEvent_t e : ev) cudaEventDestroy(e);
+  }
+};
+
 struct swmm_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
@@ -55,6 +82,7 @@ struct swmm_ctx {
   int *d_err = nullptr;
   swmm_stats stats;
   std::string last_error;
+  EventTimer timer;
 };
 
 namespace {
@@ -184,6 +212,7 @@ int run(swmm_t h, const Req &q, const swmm_opts *o, bool dry_only, int64_t *pape
   x.stream = h->stream;
   x.num_sms = h->num_sms;
   x.err = h->d_err;
+  x.timing = (o->flags & SWMM_FLAG_TIMING) ? &h->timer : nullptr;
   Scalar alpha, beta;
   if (x.fp32) {
     alpha.f = q.alpha ? *(const float *)q.alpha : 1.f;
@@ -338,6 +367,25 @@ int swmm_workspace_elems(swmm_t h, int64_t m, int64_t k, int64_t n, const swmm_o
   static const uint32_t one = 1;
   Req q{entry, m, k, n, nullptr, nullptr, nullptr, k, n, n, &one, acc_inplace || entry == 1 ? &one : nullptr};
   return run(h, q, opts, true, paper_elems, plan_elems);
+}
+
+int swmm_leaf_timing(swmm_t h, int reset, double *gemm_ms, int64_t *launches, double *tensor_flops) {
+  if (!h) return SWMM_EINVAL;
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return fail(h, SWMM_ECUDA, cudaGetErrorString(e));
+  double ms = 0.0, fl = 0.0;
+  for (size_t i = 0; i < h->timer.used; ++i) {
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, h->timer.ev[2 * i], h->timer.ev[2 * i + 1]) != cudaSuccess)
+      return fail(h, SWMM_ECUDA, "event timing failed");
+    ms += t;
+    fl += h->timer.flops[i];
+  }
+  if (gemm_ms) *gemm_ms = ms;
+  if (launches) *launches = (int64_t)h->timer.used;
+  if (tensor_flops) *tensor_flops = fl;
+  if (reset) h->timer.used = 0;
+  return SWMM_OK;
 }
 
 int swmm_get_stats(swmm_t h, swmm_stats *out) {

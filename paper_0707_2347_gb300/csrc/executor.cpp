@@ -24,6 +24,10 @@ int64_t rup(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 bool aligned16(const void *p, int64_t ld) { return ((uintptr_t)p % 16 == 0) && (ld % 4 == 0); }
 }  // namespace
 
+// tensor-core products per leaf product: 1 limb (p <= 256), 2 x 2 limbs,
+// or hi*hi + hi*lo + lo*hi in FP32 mode
+int Exec::limb_products() const { return mode == MODE_MODP1 ? 1 : (mode == MODE_MODP2 ? 4 : 3); }
+
 Scalar Exec::one() const {
   Scalar s;
   s.u = 1;
@@ -177,7 +181,9 @@ void Exec::leaf(Scalar alpha, bool acc, Scalar beta, View L, View R, View D) {
   pr.tile_begin = 0;
   P.nprod = 1;
   P.total_tiles = pr.tiles_m * pr.tiles_n;
+  if (timing) timing->begin(stream);
   check(launch_gemm_tc(P, mode, num_sms, stream), "leaf gemm");
+  if (timing) timing->end(stream, 2.0 * m * n * k * limb_products());
 }
 
 // One whole Winograd level (Section 2) with fused pre- and post-additions.
@@ -326,7 +332,9 @@ void Exec::fused_level(Scalar alpha, bool acc, Scalar beta, View L, View R, View
       }
       P.nprod = 7;
       P.total_tiles = tiles;
+      if (timing) timing->begin(stream);
       check(launch_gemm_tc(P, mode, num_sms, stream), "fused gemm");
+      if (timing) timing->end(stream, 7 * 2.0 * hm * hn * hk * limb_products());
     }
   }
   ++ew_launches;

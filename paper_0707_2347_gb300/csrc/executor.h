@@ -21,6 +21,13 @@ struct Arena {
   View region;
 };
 
+// Event pair around leaf GEMM launches (SWMM_FLAG_TIMING).
+struct TimingHook {
+  virtual void begin(cudaStream_t s) = 0;
+  virtual void end(cudaStream_t s, double tensor_flops) = 0;
+  virtual ~TimingHook() {}
+};
+
 struct Exec {
   // configuration
   int mode = MODE_MODP2;
@@ -32,6 +39,7 @@ struct Exec {
   cudaStream_t stream = nullptr;
   int num_sms = 152;
   int *err = nullptr;
+  TimingHook *timing = nullptr;
 
   // workspace for temporaries (bump allocator, bytes)
   char *ws = nullptr;
@@ -64,6 +72,7 @@ struct Exec {
   void check(cudaError_t e, const char *what);
   View alloc_tmp(int64_t rows, int64_t cols);
   Scalar one() const;
+  int limb_products() const;
   Scalar neg(Scalar s) const;
 };
 

@@ -25,7 +25,7 @@ SCHED_NAMES = {CLASSICAL: "classical", T1_DHSS: "T1", T2_HLJJTT: "T2", T3_IP: "I
                T5_OVR: "OvR", T6_ACLR: "AcLR", T7_ACCR: "AccR", T8_ACR: "AcR", T9_ACC: "Acc",
                IPMM: "IPMM", T4M_OVL: "OvLM"}
 # flags
-FLAG_UNFUSED, FLAG_SIMT_LEAF = 1, 2
+FLAG_UNFUSED, FLAG_SIMT_LEAF, FLAG_TIMING = 1, 2, 4
 
 
 class SwmmError(RuntimeError):
@@ -50,7 +50,8 @@ class _Stats(ctypes.Structure):
 
 # every symbol include/swmm.h declares
 EXPORTS = ["swmm_create", "swmm_destroy", "swmm_set_stream", "swmm_mul", "swmm_muladd", "swmm_mul_inplace",
-           "swmm_workspace_elems", "swmm_get_stats", "swmm_sync", "swmm_strerror", "swmm_last_error"]
+           "swmm_workspace_elems", "swmm_leaf_timing", "swmm_get_stats", "swmm_sync", "swmm_strerror",
+           "swmm_last_error"]
 
 _lib = None
 
@@ -75,6 +76,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.swmm_workspace_elems.argtypes = [vp, i64, i64, i64, ctypes.POINTER(_Opts), ctypes.POINTER(i64),
                                          ctypes.POINTER(i64)]
     lib.swmm_get_stats.argtypes = [vp, ctypes.POINTER(_Stats)]
+    lib.swmm_leaf_timing.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64),
+                                     ctypes.POINTER(ctypes.c_double)]
     lib.swmm_sync.argtypes = [vp]
     lib.swmm_strerror.argtypes = [ctypes.c_int]
     lib.swmm_strerror.restype = ctypes.c_char_p
@@ -198,6 +201,14 @@ class Handle:
         s = _Stats()
         self._check(self.lib.swmm_get_stats(self.h, ctypes.byref(s)))
         return {f: getattr(s, f) for f, _ in _Stats._fields_ if f != "reserved"}
+
+    def leaf_timing(self, reset: bool = True):
+        """(gemm_ms, launches, tensor_flops) of leaf GEMM launches made with
+        FLAG_TIMING since the last reset (waits for the stream)."""
+        ms, n, fl = ctypes.c_double(), ctypes.c_int64(), ctypes.c_double()
+        self._check(self.lib.swmm_leaf_timing(self.h, 1 if reset else 0, ctypes.byref(ms), ctypes.byref(n),
+                                              ctypes.byref(fl)))
+        return ms.value, n.value, fl.value
 
     def sync(self):
         self._check(self.lib.swmm_sync(self.h))
