@@ -45,6 +45,11 @@ WORKLOADS = {
                             m=16384, k=16384, n=16384, mode=MODP, p=65521, sched=T9, depth=2, entry="muladd"),
     "t9_16384_p65521_d1": dict(desc="C<-AB+C over Z/65521, 16384^2, Table 9 (Acc) depth 1 (fused level)",
                                m=16384, k=16384, n=16384, mode=MODP, p=65521, sched=T9, depth=1, entry="muladd"),
+    "t9_4096_p65521_d2": dict(desc="C<-AB+C over Z/65521, 4096^2, Table 9 (Acc) depth 2, fused last level",
+                              m=4096, k=4096, n=4096, mode=MODP, p=65521, sched=T9, depth=2, entry="muladd"),
+    "classical_4096_p65521": dict(desc="C<-AB+C over Z/65521, 4096^2, classical tcgen05 product",
+                                  m=4096, k=4096, n=4096, mode=MODP, p=65521, sched=CLASSICAL, depth=0,
+                                  entry="muladd"),
     "t1_512_p251": dict(desc="C<-AB over Z/251, 512^2, Table 1 depth 1", m=512, k=512, n=512, mode=MODP, p=251,
                         sched=T1, depth=1, entry="mul"),
     "ip_16384_p251": dict(desc="C<-AB over Z/251, 16384^2, Table 3 (IP) depth 2", m=16384, k=16384, n=16384,
