@@ -171,6 +171,7 @@ void Exec::leaf(Scalar alpha, bool acc, Scalar beta, View L, View R, View D) {
   pr.t[0].sign = 1;
   pr.t[0].vec_ok = aligned16(D.ptr, D.ld);
   pr.ntargets = 1;
+  pr.tma_epi = make_target_tmap(&pr.tmap[0], D.ptr, m, n, D.ld) ? 1 : 0;
   pr.M = (int)m;
   pr.N = (int)n;
   pr.Kpad = (int)Kp;
@@ -320,6 +321,9 @@ void Exec::fused_level(Scalar alpha, bool acc, Scalar beta, View L, View R, View
           T.sign = tgt[i][q];
           T.vec_ok = aligned16(Dq[q].ptr, Dq[q].ld);
         }
+        pr.tma_epi = 1;
+        for (int t = 0; t < pr.ntargets; ++t)
+          if (!make_target_tmap(&pr.tmap[t], pr.t[t].ptr, hm, hn, pr.t[t].ld)) pr.tma_epi = 0;
         pr.M = (int)hm;
         pr.N = (int)hn;
         pr.Kpad = (int)Kp;

@@ -222,25 +222,27 @@ __global__ void __launch_bounds__(256) pack_cols_kernel(const __grid_constant__ 
 }
 
 // ------------------------------------------------------------ GEMM glue
-constexpr int kThreads = 192;
+constexpr int kThreads = 320;                 // producer, MMA, 8 epilogue warps
+constexpr int kEpiThreads = 256;
 constexpr int kChunkKB = 15;                  // k-blocks between in-place reductions
 constexpr uint64_t kWaitNs = 4000000000ull;  // bounded wait: 4 s
 constexpr int kPlaneBytes = kBM * kBK * 2;    // 16 KB
 constexpr int kBBytes = 256 * kBK * 2;        // 32 KB
+constexpr int kEpiBytes = 4 * kBM * 32 * 4;   // 64 KB: 128 rows x 128 fp32 columns, 4 boxes
 
 template <int MODE>
 struct Cfg;
 template <>
 struct Cfg<MODE_MODP1> {
-  static constexpr int BN = 256, A_PLANES = 1, STAGES = 4, ACC_BUFS = 2, BUF_COLS = 256;
+  static constexpr int BN = 256, A_PLANES = 1, STAGES = 3, ACC_BUFS = 2, BUF_COLS = 256;
 };
 template <>
 struct Cfg<MODE_MODP2> {
-  static constexpr int BN = 128, A_PLANES = 2, STAGES = 3, ACC_BUFS = 1, BUF_COLS = 512;
+  static constexpr int BN = 128, A_PLANES = 2, STAGES = 2, ACC_BUFS = 1, BUF_COLS = 512;
 };
 template <>
 struct Cfg<MODE_FP32> {
-  static constexpr int BN = 128, A_PLANES = 2, STAGES = 3, ACC_BUFS = 2, BUF_COLS = 256;
+  static constexpr int BN = 128, A_PLANES = 2, STAGES = 2, ACC_BUFS = 2, BUF_COLS = 256;
 };
 template <int MODE>
 __host__ __device__ constexpr int stage_bytes() {
@@ -248,7 +250,7 @@ __host__ __device__ constexpr int stage_bytes() {
 }
 template <int MODE>
 __host__ __device__ constexpr int smem_bytes() {
-  return Cfg<MODE>::STAGES * stage_bytes<MODE>() + 1024 + 256;
+  return Cfg<MODE>::STAGES * stage_bytes<MODE>() + kEpiBytes + 1024 + 256;
 }
 
 __device__ __forceinline__ void mbar_init(uint64_t *b, uint32_t count) {
@@ -296,6 +298,8 @@ __device__ __forceinline__ bool wait_bar(uint64_t *b, uint32_t parity, Ctl *ctl,
   }
 }
 
+__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kEpiThreads) : "memory"); }
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_commit(uint64_t *b) {
@@ -316,6 +320,21 @@ __device__ __forceinline__ void tma_load(uint32_t dst, const CUtensorMap *map, i
       "l"(map), "r"(x), "r"(y), "r"(smem_u32(bar))
       : "memory");
 }
+__device__ __forceinline__ void tma_store(const CUtensorMap *map, int x, int y, uint32_t src) {
+  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.tile.bulk_group [%0, {%1, %2}], [%3];" ::"l"(map), "r"(x),
+               "r"(y), "r"(src)
+               : "memory");
+}
+__device__ __forceinline__ void tma_reduce_add(const CUtensorMap *map, int x, int y, uint32_t src) {
+  asm volatile("cp.reduce.async.bulk.tensor.2d.global.shared::cta.add.tile.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
+                   map),
+               "r"(x), "r"(y), "r"(src)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait0() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
 __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float *v) {
   uint32_t r[8];
   asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
@@ -333,6 +352,14 @@ __device__ __forceinline__ void tmem_st8(uint32_t taddr, const float *v) {
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ uint4 lds128(uint32_t a) {
+  uint4 v;
+  asm volatile("ld.shared.v4.b32 {%0,%1,%2,%3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(a));
+  return v;
+}
+__device__ __forceinline__ void sts128(uint32_t a, uint4 v) {
+  asm volatile("st.shared.v4.b32 [%0], {%1,%2,%3,%4};" ::"r"(a), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w) : "memory");
+}
 
 // Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row
 // core groups 1024 bytes apart (stride byte offset), descriptor version 1.
@@ -394,62 +421,64 @@ struct Epi {
   }
 };
 
-// write 4 consecutive mod p results (or 4 floats in FP32 mode) of one row
-template <bool FP>
-__device__ __forceinline__ void emit4(const GemmParams &P, const Product &pr, const Epi &E, int gr, int gc,
-                                      uint32_t (&v)[4]) {
-  if (P.epilogue == EPI_STORE) {
-    const Target &T = pr.t[0];
-    char *base = (char *)T.ptr + 4 * ((int64_t)gr * T.ld + gc);
-    const bool vec = T.vec_ok && gc + 4 <= pr.N;
-    if (P.use_beta) {
-      uint32_t s[4];
-      if (vec) {
-        uint4 q = *reinterpret_cast<const uint4 *>(base);
-        s[0] = q.x; s[1] = q.y; s[2] = q.z; s[3] = q.w;
-      } else {
+// Results of 8 consecutive columns of one row, as the 32-bit words written
+// to the target: mod p values (STORE), float values (REDUCE, sign folded in)
+// or floats (FP32).  `c8` holds beta-source words when the epilogue adds
+// beta * T0 (STORE) and is ignored otherwise.
+template <int MODE>
+__device__ __forceinline__ void tile_values(const GemmParams &P, const Epi &E, uint32_t d, int col, int sign,
+                                            const uint32_t (&c8)[8], uint32_t (&v)[8]) {
+  if (MODE == MODE_MODP2) {
+    float hh[8], hl[8], lh[8], ll[8];
+    tmem_ld8(d + col, hh);
+    tmem_ld8(d + 128 + col, hl);
+    tmem_ld8(d + 256 + col, lh);
+    tmem_ld8(d + 384 + col, ll);
+    tmem_wait_ld();
 #pragma unroll
-        for (int e = 0; e < 4; ++e) s[e] = gc + e < pr.N ? reinterpret_cast<const uint32_t *>(base)[e] : 0u;
-      }
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        if (FP) {
-          v[e] = __float_as_uint(__uint_as_float(v[e]) + P.beta_f * __uint_as_float(s[e]));
-        } else {
-          uint32_t w = v[e] + E.mulmod(P.beta_u, s[e]);
-          v[e] = min(w, w - E.p);
-        }
-      }
+    for (int e = 0; e < 8; ++e) {
+      // 2^16 hh + 2^8 (hl + lh) + ll, every intermediate an exact fp32 integer
+      const float s = E.fr(E.fr(hl[e]) + E.fr(lh[e]));
+      const float t1 = E.fr(__fmaf_rn(256.f, E.fr(hh[e]), s));
+      v[e] = E.canon(E.fr(__fmaf_rn(256.f, t1, E.fr(ll[e]))));
     }
-    if (vec) {
-      *reinterpret_cast<uint4 *>(base) = make_uint4(v[0], v[1], v[2], v[3]);
-    } else {
+  } else if (MODE == MODE_MODP1) {
+    float a[8];
+    tmem_ld8(d + col, a);
+    tmem_wait_ld();
 #pragma unroll
-      for (int e = 0; e < 4; ++e)
-        if (gc + e < pr.N) reinterpret_cast<uint32_t *>(base)[e] = v[e];
-    }
+    for (int e = 0; e < 8; ++e) v[e] = E.canon(E.fr(a[e]));
   } else {
-    for (int t = 0; t < pr.ntargets; ++t) {
-      const Target &T = pr.t[t];
-      float f[4];
+    float a[8], b[8];
+    tmem_ld8(d + col, a);
+    tmem_ld8(d + 128 + col, b);
+    tmem_wait_ld();
 #pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        if (FP)
-          f[e] = T.sign > 0 ? __uint_as_float(v[e]) : -__uint_as_float(v[e]);
-        else
-          f[e] = (float)(T.sign > 0 ? v[e] : (v[e] == 0 ? 0u : E.p - v[e]));
+    for (int e = 0; e < 8; ++e) {
+      float f = P.alpha_f * (a[e] + b[e]);
+      if (P.epilogue == EPI_STORE) {
+        if (P.use_beta) f += P.beta_f * __uint_as_float(c8[e]);
+      } else if (sign < 0) {
+        f = -f;
       }
-      float *base = reinterpret_cast<float *>((char *)T.ptr + 4 * ((int64_t)gr * T.ld + gc));
-      if (T.vec_ok && gc + 4 <= pr.N) {
-        asm volatile("red.global.add.v4.f32 [%0], {%1,%2,%3,%4};" ::"l"(base), "f"(f[0]), "f"(f[1]), "f"(f[2]),
-                     "f"(f[3])
-                     : "memory");
-      } else {
-#pragma unroll
-        for (int e = 0; e < 4; ++e)
-          if (gc + e < pr.N) atomicAdd(base + e, f[e]);
-      }
+      v[e] = __float_as_uint(f);
     }
+    return;
+  }
+#pragma unroll
+  for (int e = 0; e < 8; ++e) {
+    uint32_t x = v[e];
+    if (P.alpha_u != 1) x = E.mulmod(P.alpha_u, x);
+    if (P.epilogue == EPI_STORE) {
+      if (P.use_beta) {
+        uint32_t w = x + E.mulmod(P.beta_u, c8[e]);
+        x = min(w, w - E.p);
+      }
+    } else {
+      if (sign < 0) x = x == 0 ? 0u : E.p - x;
+      x = __float_as_uint((float)x);
+    }
+    v[e] = x;
   }
 }
 
@@ -462,7 +491,8 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_kernel(const __grid_constant
   constexpr bool modp = MODE != MODE_FP32;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + C::STAGES * SB);
+  unsigned char *ebuf = smem + C::STAGES * SB;  // epilogue tile, 4 swizzled boxes
+  uint64_t *bars = reinterpret_cast<uint64_t *>(ebuf + kEpiBytes);
   uint64_t *full = bars;                      // [STAGES]
   uint64_t *empty = bars + C::STAGES;         // [STAGES]
   uint64_t *acc_full = bars + 2 * C::STAGES;  // [2]
@@ -470,7 +500,8 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_kernel(const __grid_constant
   uint64_t *drain_full = acc_empty + 2;
   uint64_t *drain_empty = drain_full + 1;
   uint64_t *final_bar = drain_empty + 1;
-  Ctl *ctl = reinterpret_cast<Ctl *>(final_bar + 1);
+  uint64_t *cbar = final_bar + 1;  // beta source tile loaded
+  Ctl *ctl = reinterpret_cast<Ctl *>(cbar + 1);
 
   const int tid = threadIdx.x;
   const int warp = tid >> 5;
@@ -483,11 +514,12 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_kernel(const __grid_constant
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&acc_full[b], 1);
-      mbar_init(&acc_empty[b], 128);
+      mbar_init(&acc_empty[b], kEpiThreads);
     }
     mbar_init(drain_full, 1);
-    mbar_init(drain_empty, 128);
+    mbar_init(drain_empty, kEpiThreads);
     mbar_init(final_bar, 1);
+    mbar_init(cbar, 1);
     ctl->abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -604,15 +636,21 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_kernel(const __grid_constant
     __syncwarp();
   } else {
     // ================================= epilogue =================================
-    const int q4 = warp & 3;  // tensor-memory lane quadrant this warp may access
+    // warp w in 2..9 reads tensor-memory lanes 32 (w % 4) .. +31 and the 64
+    // columns (w - 2) / 4 of each 128-column chunk of the tile.
+    const int et = tid - 64;
+    const int q4 = warp & 3;
+    const int hsel = (warp - 2) >> 2;
     const int row = q4 * 32 + lane;
+    const bool issuer = et == 0;
     const uint32_t lane_addr = (uint32_t)((q4 * 32) << 16);
+    const uint32_t eb = smem_u32(ebuf);
     Epi E;
     E.p = P.p;
     E.m = P.barrett;
     E.pf = (float)P.p;
     E.inv_p = P.inv_p;
-    uint32_t tcount = 0, dcount = 0;
+    uint32_t tcount = 0, dcount = 0, cphase = 0;
     for (int g = blockIdx.x; g < P.total_tiles; g += gridDim.x, ++tcount) {
       const TileInfo ti = decode<BN>(P, g);
       const Product &pr = P.prod[ti.pi];
@@ -620,103 +658,127 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_kernel(const __grid_constant
       const int buf = C::ACC_BUFS == 2 ? (int)(tcount & 1) : 0;
       const uint32_t use = C::ACC_BUFS == 2 ? (tcount >> 1) : tcount;
       const uint32_t d = tmem + lane_addr + (uint32_t)(buf * C::BUF_COLS);
-      if (modp && nkb > 16) {
-        const int ndrain = (nkb - 1) / kChunkKB;
-        bool bad = false;
-        for (int q = 0; q < ndrain; ++q, ++dcount) {
-          if (!wait_bar(drain_full, dcount & 1, ctl, P.err)) {
-            bad = true;
-            break;
-          }
-          tc_fence_after();
-          constexpr int cols = MODE == MODE_MODP2 ? 512 : 256;
-          for (int c = 0; c < cols; c += 8) {
-            float v[8];
-            tmem_ld8(d + c, v);
-            tmem_wait_ld();
-#pragma unroll
-            for (int e = 0; e < 8; ++e) v[e] = E.fr(v[e]);
-            tmem_st8(d + c, v);
-          }
-          tmem_wait_st();
-          tc_fence_before();
-          mbar_arrive(drain_empty);
-        }
-        if (bad) break;
-      }
-      if (!wait_bar(&acc_full[buf], use & 1, ctl, P.err)) break;
-      tc_fence_after();
+      const bool tma = pr.tma_epi != 0;
+      const bool load_c = tma && P.epilogue == EPI_STORE && P.use_beta;
+      const int sign = pr.t[0].sign;
       const int gr = ti.m0 + row;
-      const bool row_ok = gr < pr.M;
-      if (MODE == MODE_MODP2) {
-        uint32_t res[BN];
-#pragma unroll
-        for (int c = 0; c < BN; c += 8) {
-          float hh[8], hl[8], lh[8], ll[8];
-          tmem_ld8(d + c, hh);
-          tmem_ld8(d + 128 + c, hl);
-          tmem_ld8(d + 256 + c, lh);
-          tmem_ld8(d + 384 + c, ll);
-          tmem_wait_ld();
-#pragma unroll
-          for (int e = 0; e < 8; ++e) {
-            // 2^16 hh + 2^8 (hl + lh) + ll, every intermediate an exact fp32 integer
-            const float s = E.fr(E.fr(hl[e]) + E.fr(lh[e]));
-            const float t1 = E.fr(__fmaf_rn(256.f, E.fr(hh[e]), s));
-            const float t2 = E.fr(__fmaf_rn(256.f, t1, E.fr(ll[e])));
-            res[c + e] = E.canon(t2);
-          }
-        }
-        tc_fence_before();
-        mbar_arrive(&acc_empty[buf]);  // tensor memory free: the next tile's MMAs may start
-        if (row_ok) {
-#pragma unroll
-          for (int c = 0; c < BN; c += 4) {
-            const int gc = ti.n0 + c;
-            if (gc < pr.N) {
-              uint32_t v[4] = {res[c], res[c + 1], res[c + 2], res[c + 3]};
-              if (P.alpha_u != 1) {
-#pragma unroll
-                for (int e = 0; e < 4; ++e) v[e] = E.mulmod(P.alpha_u, v[e]);
-              }
-              emit4<false>(P, pr, E, gr, gc, v);
+      bool bad = false;
+      for (int ch = 0; ch < BN / 128 && !bad; ++ch) {
+        const int cbase = ti.n0 + ch * 128;  // first global column of the chunk
+        if (tma) {
+          // the previous chunk's TMA must have read the staging buffer
+          if (issuer) {
+            bulk_wait_read0();
+            if (load_c) {
+              int boxes = 0;
+              for (int b = 0; b < 4; ++b) boxes += cbase + 32 * b < pr.N;
+              mbar_expect_tx(cbar, boxes * 16384);
+              for (int b = 0; b < 4; ++b)
+                if (cbase + 32 * b < pr.N) tma_load(eb + b * 16384, &pr.tmap[0], cbase + 32 * b, ti.m0, cbar);
             }
           }
+          epi_sync();
         }
-      } else {
-        // MODP1 / FP32: 8-column slices straight from tensor memory
-        constexpr int NC = MODE == MODE_FP32 ? 128 : BN;
-        for (int c = 0; c < NC; c += 8) {
-          float a8[8], b8[8];
-          tmem_ld8(d + c, a8);
-          if (MODE == MODE_FP32) tmem_ld8(d + 128 + c, b8);
-          tmem_wait_ld();
-          const int gc = ti.n0 + c;
-          if (!row_ok || gc >= pr.N) continue;
+        if (ch == 0) {
+          if (modp && nkb > 16) {
+            const int ndrain = (nkb - 1) / kChunkKB;
+            for (int q = 0; q < ndrain; ++q, ++dcount) {
+              wait_bar(drain_full, dcount & 1, ctl, P.err);
+              epi_sync();  // every epilogue thread takes the same exit on a timeout
+              if (ctl->abort) {
+                bad = true;
+                break;
+              }
+              tc_fence_after();
+              constexpr int cols = MODE == MODE_MODP2 ? 512 : 256;
+              // each of the 8 warps reduces its lane quadrant, half the columns
+              for (int c = hsel * (cols / 2); c < (hsel + 1) * (cols / 2); c += 8) {
+                float v[8];
+                tmem_ld8(d + c, v);
+                tmem_wait_ld();
 #pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            const int gc4 = gc + 4 * h;
-            if (gc4 < pr.N) {
-              uint32_t v[4];
-              if (MODE == MODE_MODP1) {
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                  v[e] = E.canon(E.fr(a8[4 * h + e]));
-                  if (P.alpha_u != 1) v[e] = E.mulmod(P.alpha_u, v[e]);
-                }
-                emit4<false>(P, pr, E, gr, gc4, v);
+                for (int e = 0; e < 8; ++e) v[e] = E.fr(v[e]);
+                tmem_st8(d + c, v);
+              }
+              tmem_wait_st();
+              tc_fence_before();
+              mbar_arrive(drain_empty);
+            }
+            if (bad) break;
+          }
+          wait_bar(&acc_full[buf], use & 1, ctl, P.err);
+        }
+        if (load_c) {
+          wait_bar(cbar, cphase, ctl, P.err);
+          cphase ^= 1;
+        }
+        epi_sync();
+        if (ctl->abort) {
+          bad = true;
+          break;
+        }
+        tc_fence_after();
+#pragma unroll 1
+        for (int s = 0; s < 8; ++s) {
+          const int cc = hsel * 64 + 8 * s;  // column within the chunk
+          const int box = cc >> 5, j = (cc & 31) >> 2;
+          const uint32_t a0 = eb + box * 16384 + row * 128 + ((j ^ (row & 7)) << 4);
+          const uint32_t a1 = eb + box * 16384 + row * 128 + (((j + 1) ^ (row & 7)) << 4);
+          uint32_t c8[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+          const int gc = cbase + cc;
+          if (P.epilogue == EPI_STORE && P.use_beta) {
+            if (load_c) {
+              uint4 x0 = lds128(a0), x1 = lds128(a1);
+              c8[0] = x0.x; c8[1] = x0.y; c8[2] = x0.z; c8[3] = x0.w;
+              c8[4] = x1.x; c8[5] = x1.y; c8[6] = x1.z; c8[7] = x1.w;
+            } else if (gr < pr.M) {
+              const uint32_t *src = reinterpret_cast<const uint32_t *>((const char *)pr.t[0].ptr) + (int64_t)gr * pr.t[0].ld;
+              for (int e = 0; e < 8; ++e) c8[e] = gc + e < pr.N ? src[gc + e] : 0u;
+            }
+          }
+          uint32_t v[8];
+          tile_values<MODE>(P, E, d, ch * 128 + cc, sign, c8, v);
+          if (tma) {
+            sts128(a0, make_uint4(v[0], v[1], v[2], v[3]));
+            sts128(a1, make_uint4(v[4], v[5], v[6], v[7]));
+          } else if (gr < pr.M) {
+            // direct path for targets TMA cannot address (odd leading dimension)
+            for (int e = 0; e < 8; ++e) {
+              if (gc + e >= pr.N) break;
+              if (P.epilogue == EPI_STORE) {
+                reinterpret_cast<uint32_t *>((char *)pr.t[0].ptr)[(int64_t)gr * pr.t[0].ld + gc + e] = v[e];
               } else {
-#pragma unroll
-                for (int e = 0; e < 4; ++e) v[e] = __float_as_uint(P.alpha_f * (a8[4 * h + e] + b8[4 * h + e]));
-                emit4<true>(P, pr, E, gr, gc4, v);
+                for (int t = 0; t < pr.ntargets; ++t)
+                  atomicAdd(reinterpret_cast<float *>((char *)pr.t[t].ptr) + (int64_t)gr * pr.t[t].ld + gc + e,
+                            __uint_as_float(v[e]));
               }
             }
           }
         }
-        tc_fence_before();
-        mbar_arrive(&acc_empty[buf]);
+        if (ch == BN / 128 - 1) {
+          tc_fence_before();
+          mbar_arrive(&acc_empty[buf]);  // accumulators free for the next tile
+        }
+        if (tma) {
+          fence_proxy_async();
+          epi_sync();
+          if (issuer) {
+            for (int b = 0; b < 4; ++b) {
+              const int x = cbase + 32 * b;
+              if (x >= pr.N) break;
+              if (P.epilogue == EPI_STORE) {
+                tma_store(&pr.tmap[0], x, ti.m0, eb + b * 16384);
+              } else {
+                for (int t = 0; t < pr.ntargets; ++t) tma_reduce_add(&pr.tmap[t], x, ti.m0, eb + b * 16384);
+              }
+            }
+            bulk_commit();
+          }
+        }
       }
+      if (bad) break;
     }
+    if (issuer) bulk_wait0();
   }
 
   tc_fence_before();

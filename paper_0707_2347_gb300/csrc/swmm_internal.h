@@ -76,6 +76,8 @@ struct Target {
 struct Product {
   CUtensorMap ta;  // packed A': 2-D (K_pad halves) x (planes * M_pad rows)
   CUtensorMap tb;  // packed B': 2-D (K_pad halves) x (planes * N_pad rows)
+  CUtensorMap tmap[kMaxTargets];  // targets (fp32 words, 32 x 128 boxes, 128-byte swizzle)
+  int32_t tma_epi;                // every target addressable by TMA: staged epilogue
   Target t[kMaxTargets];
   int32_t ntargets;
   int32_t M, N, Kpad;
@@ -103,6 +105,9 @@ struct GemmParams {
 
 // Encode a 2-D tensor map over a packed buffer (rows x kpad halves).
 bool make_tmap(CUtensorMap *map, const void *base, int64_t rows, int64_t kpad, int box_rows);
+// Encode a 2-D tensor map over a target block of 32-bit words (rows x cols,
+// leading dimension ld); false when TMA cannot address it (alignment).
+bool make_target_tmap(CUtensorMap *map, const void *base, int64_t rows, int64_t cols, int64_t ld);
 
 cudaError_t launch_gemm_tc(const GemmParams &P, int mode, int num_sms, cudaStream_t s);
 
