@@ -135,6 +135,26 @@ int swmm_muladd(swmm_t h, int64_t m, int64_t k, int64_t n, const void *alpha,
                 const void *A, int64_t lda, const void *B, int64_t ldb,
                 const void *beta, void *C, int64_t ldc, const swmm_opts *opts);
 
+/* The same operation as swmm_muladd for callers that cannot allocate device
+ * memory (the paper has no counterpart: it is a deployment variant).  Code
+ * running where cudaMalloc/cudaMallocAsync are unavailable or forbidden --
+ * inside a memory budget owned by another allocator, in a real-time path
+ * that must not reach the driver's allocator, or in a process whose pools
+ * are reserved -- gets the schedule's temporaries and the tensor-core
+ * operand staging from one static device array of
+ * SWMM_NOALLOC_SCRATCH_BYTES bytes that every GPU which loads the library
+ * holds until the process exits.  Plans that need more scratch fail with
+ * SWMM_EINVAL (swmm_last_error gives the sizes).  Nothing is allocated and
+ * no scratch content needs to start at zero.  The first call on a device
+ * looks the array's device address up (cudaGetSymbolAddress); make that
+ * first call before any stream capture.  All calls share the array: calls
+ * whose work overlaps on the GPU (different streams, or several handles)
+ * race on it and must be serialised by the caller. */
+#define SWMM_NOALLOC_SCRATCH_BYTES (32ll << 20)
+int swmm_muladd_noalloc(swmm_t h, int64_t m, int64_t k, int64_t n, const void *alpha,
+                        const void *A, int64_t lda, const void *B, int64_t ldb,
+                        const void *beta, void *C, int64_t ldc, const swmm_opts *opts);
+
 /* Schedules that may overwrite their inputs (Sections 5.1-5.3).
  * beta == NULL: C <- alpha A B with SWMM_T3_IP (k = n <= m), SWMM_T4_OVL,
  * SWMM_T4M_OVL, SWMM_T5_OVR (square).  beta != NULL: C <- alpha A B + beta C

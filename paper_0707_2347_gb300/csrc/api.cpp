@@ -174,7 +174,13 @@ bool overlaps(const void *a, int64_t ar, int64_t ac, int64_t lda, const void *b,
   return a0 < b1 && b0 < a1;
 }
 
-int run(swmm_t h, const Req &q, const swmm_opts *o, bool dry_only, int64_t *paper_out, int64_t *plan_out) {
+struct Scratch {
+  char *base;
+  int64_t bytes;
+};
+
+int run(swmm_t h, const Req &q, const swmm_opts *o, bool dry_only, int64_t *paper_out, int64_t *plan_out,
+        const Scratch *ext = nullptr) {
   if (!h) return SWMM_EINVAL;
   h->last_error.clear();
   if (!o) return fail(h, SWMM_EINVAL, "opts is NULL");
@@ -225,7 +231,7 @@ int run(swmm_t h, const Req &q, const swmm_opts *o, bool dry_only, int64_t *pape
   x.stream = h->stream;
   x.num_sms = h->num_sms;
   x.err = h->d_err;
-  x.timing = (o->flags & SWMM_FLAG_TIMING) ? &h->timer : nullptr;
+  x.timing = (o->flags & SWMM_FLAG_TIMING) && !ext ? &h->timer : nullptr;
   Scalar alpha, beta;
   if (x.fp32) {
     alpha.f = q.alpha ? *(const float *)q.alpha : 1.f;
@@ -276,13 +282,22 @@ int run(swmm_t h, const Req &q, const swmm_opts *o, bool dry_only, int64_t *pape
   r.tmp_elems = r.tmp_peak_elems = 0;
   r.add_elems = r.leaf_flops = r.leaf_launches = r.ew_launches = r.leaf_products = 0;
   r.stage_need = x.stage_need;
-  if (x.ws_peak > 0) {
+  if (ext) {
+    // caller-provided scratch: carve, never allocate
+    const int64_t ws_bytes = (x.ws_peak + 1023) / 1024 * 1024;
+    if (ws_bytes + x.stage_need > ext->bytes)
+      return fail(h, SWMM_EINVAL,
+                  "plan needs " + std::to_string(ws_bytes + x.stage_need) + " bytes of scratch, more than the " +
+                      std::to_string(ext->bytes) + "-byte static scratch");
+    r.ws = x.ws_peak > 0 ? ext->base : nullptr;
+    r.stage = x.stage_need > 0 ? ext->base + ws_bytes : nullptr;
+  } else if (x.ws_peak > 0) {
     if (cudaMallocAsync((void **)&r.ws, x.ws_peak, h->stream) != cudaSuccess) {
       cudaGetLastError();
       return fail(h, SWMM_ENOMEM, "workspace allocation failed");
     }
   }
-  if (x.stage_need > 0) {
+  if (!ext && x.stage_need > 0) {
     if (cudaMallocAsync((void **)&r.stage, x.stage_need, h->stream) != cudaSuccess) {
       cudaGetLastError();
       if (r.ws) cudaFreeAsync(r.ws, h->stream);
@@ -290,8 +305,8 @@ int run(swmm_t h, const Req &q, const swmm_opts *o, bool dry_only, int64_t *pape
     }
   }
   execute(r);
-  if (r.ws) cudaFreeAsync(r.ws, h->stream);
-  if (r.stage) cudaFreeAsync(r.stage, h->stream);
+  if (!ext && r.ws) cudaFreeAsync(r.ws, h->stream);
+  if (!ext && r.stage) cudaFreeAsync(r.stage, h->stream);
   std::memset(&h->stats, 0, sizeof(h->stats));
   h->stats.workspace_bytes = x.ws_peak;
   h->stats.plan_extra_elems = x.tmp_peak_elems;
@@ -308,6 +323,19 @@ int run(swmm_t h, const Req &q, const swmm_opts *o, bool dry_only, int64_t *pape
 }
 
 }  // namespace
+
+namespace swmm {
+int handle_device(swmm_t h) { return h ? h->device : -1; }
+
+int muladd_with_scratch(swmm_t h, int64_t m, int64_t k, int64_t n, const void *alpha, const void *A, int64_t lda,
+                        const void *B, int64_t ldb, const void *beta, void *C, int64_t ldc, const swmm_opts *opts,
+                        void *scratch, int64_t scratch_bytes) {
+  if (!alpha || !beta) return fail(h, SWMM_EINVAL, "alpha and beta are required");
+  Req q{1, m, k, n, A, B, C, lda, ldb, ldc, alpha, beta};
+  Scratch s{(char *)scratch, scratch_bytes};
+  return run(h, q, opts, false, nullptr, nullptr, &s);
+}
+}  // namespace swmm
 
 extern "C" {
 

@@ -49,7 +49,8 @@ class _Stats(ctypes.Structure):
 
 
 # every symbol include/swmm.h declares
-EXPORTS = ["swmm_create", "swmm_destroy", "swmm_set_stream", "swmm_mul", "swmm_muladd", "swmm_mul_inplace",
+EXPORTS = ["swmm_create", "swmm_destroy", "swmm_set_stream", "swmm_mul", "swmm_muladd", "swmm_muladd_noalloc",
+           "swmm_mul_inplace",
            "swmm_workspace_elems", "swmm_leaf_timing", "swmm_get_stats", "swmm_sync", "swmm_strerror",
            "swmm_last_error"]
 
@@ -71,6 +72,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.swmm_set_stream.argtypes = [vp, vp]
     lib.swmm_mul.argtypes = [vp, i64, i64, i64, cvp, i64, cvp, i64, vp, i64, ctypes.POINTER(_Opts)]
     lib.swmm_muladd.argtypes = [vp, i64, i64, i64, cvp, cvp, i64, cvp, i64, cvp, vp, i64, ctypes.POINTER(_Opts)]
+    lib.swmm_muladd_noalloc.argtypes = [vp, i64, i64, i64, cvp, cvp, i64, cvp, i64, cvp, vp, i64,
+                                        ctypes.POINTER(_Opts)]
     lib.swmm_mul_inplace.argtypes = [vp, i64, i64, i64, vp, i64, vp, i64, vp, i64, cvp, cvp,
                                      ctypes.POINTER(_Opts)]
     lib.swmm_workspace_elems.argtypes = [vp, i64, i64, i64, ctypes.POINTER(_Opts), ctypes.POINTER(i64),
@@ -176,6 +179,19 @@ class Handle:
         n = B.shape[1]
         self._check(self.lib.swmm_muladd(self.h, m, k, n, _scalar(opts.mode, alpha), a, lda, b, ldb,
                                          _scalar(opts.mode, beta), c, ldc, ctypes.byref(opts.c())))
+        return C
+
+    def muladd_noalloc(self, alpha, A, B, beta, C, opts: Opts):
+        """swmm_muladd_noalloc: like muladd, scratch from the library's static
+        device array (no allocation)."""
+        self._stream()
+        a, lda = _mat(A, "A")
+        b, ldb = _mat(B, "B")
+        c, ldc = _mat(C, "C")
+        m, k = A.shape
+        n = B.shape[1]
+        self._check(self.lib.swmm_muladd_noalloc(self.h, m, k, n, _scalar(opts.mode, alpha), a, lda, b, ldb,
+                                                 _scalar(opts.mode, beta), c, ldc, ctypes.byref(opts.c())))
         return C
 
     def mul_inplace(self, A, B, C, opts: Opts, alpha=1, beta=None):
