@@ -44,14 +44,17 @@ bool make_tmap(CUtensorMap *map, const void *base, int64_t rows, int64_t kpad, i
   return r == CUDA_SUCCESS;
 }
 
-bool make_target_tmap(CUtensorMap *map, const void *base, int64_t rows, int64_t cols, int64_t ld) {
+bool make_target_tmap(CUtensorMap *map, const void *base, int64_t rows, int64_t cols, int64_t ld, bool fp32) {
   EncodeTiledFn fn = encode_fn();
   if (!fn || ((uintptr_t)base % 16) != 0 || (ld % 4) != 0 || rows <= 0 || cols <= 0) return false;
   cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
   cuuint64_t strides[1] = {(cuuint64_t)ld * 4};
   cuuint32_t box[2] = {32, (cuuint32_t)kBM};
   cuuint32_t estr[2] = {1, 1};
-  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void *>(base), dims, strides, box, estr,
+  // the element type matters for TMA reduce-add: float sums or unsigned
+  // integer sums of mod p contributions
+  CUresult r = fn(map, fp32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_UINT32, 2,
+                  const_cast<void *>(base), dims, strides, box, estr,
                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
@@ -278,6 +281,7 @@ int run(swmm_t h, const Req &q, const swmm_opts *o, bool dry_only, int64_t *pape
 
   Exec r = x;
   r.dry = false;
+  r.lazy = false;
   r.ws_top = r.ws_peak = 0;
   r.tmp_elems = r.tmp_peak_elems = 0;
   r.add_elems = r.leaf_flops = r.leaf_launches = r.ew_launches = r.leaf_products = 0;
@@ -305,6 +309,15 @@ int run(swmm_t h, const Req &q, const swmm_opts *o, bool dry_only, int64_t *pape
     }
   }
   execute(r);
+  if (r.lazy && r.ok()) {
+    // fused levels leave unreduced representatives: one canonicalising pass
+    ++r.ew_launches;
+    cudaError_t e = launch_canon_modp(D, r.p, h->stream);
+    if (e != cudaSuccess) {
+      r.cuda_err = e;
+      r.fail = std::string("canonical pass: ") + cudaGetErrorString(e);
+    }
+  }
   if (!ext && r.ws) cudaFreeAsync(r.ws, h->stream);
   if (!ext && r.stage) cudaFreeAsync(r.stage, h->stream);
   std::memset(&h->stats, 0, sizeof(h->stats));

@@ -6,9 +6,10 @@
 // All are HBM-bound streams over strided 2-D blocks: one thread handles four
 // consecutive elements with 16-byte loads/stores when the views allow it
 // (base 16-byte aligned, ld and cols multiples of 4), else one element.
-// Values mod p are canonical in [0, p); a + b and a - b + p are brought back
-// with one unsigned min (r < 2p), products u * x (< 2^32) with a Barrett
-// step using m = floor(2^32 / p).
+// Inputs mod p may be any representative below 2^32 (a fused Winograd level
+// leaves unreduced sums in its destination): every input is first reduced
+// with a Barrett step using m = floor(2^32 / p); outputs are canonical in
+// [0, p).
 #include <cstdint>
 
 #include "swmm_internal.h"
@@ -32,10 +33,18 @@ __device__ __forceinline__ uint32_t mulmod(uint32_t u, uint32_t x, uint32_t p, u
   return red2p(prod - q * p, p);
 }
 
+// any 32-bit representative -> [0, p)
+__device__ __forceinline__ uint32_t bred(uint32_t x, uint32_t p, uint32_t m) {
+  uint32_t q = __umulhi(x, m);
+  return red2p(x - q * p, p);
+}
+
 // coefficient classes: 0 = +1, 1 = -1, 2 = general u
 template <int K1, int K2>
 __device__ __forceinline__ uint32_t comb(uint32_t a, uint32_t b, uint32_t u1, uint32_t u2, uint32_t p,
                                          uint32_t m) {
+  a = bred(a, p, m);
+  b = bred(b, p, m);
   uint32_t x = (K1 == 0) ? a : (K1 == 1 ? (p - a) : mulmod(u1, a, p, m));
   uint32_t y = (K2 == 0) ? b : (K2 == 1 ? (p - b) : mulmod(u2, b, p, m));
   // x in [0, p], y in [0, p]: x + y < 2p + 1; p - 0 = p is reduced too
@@ -93,25 +102,20 @@ __global__ void add_f32_kernel(V d, V s1, V s2, int64_t rows, int64_t cols, floa
   }
 }
 
-// mode 0: int mod p -> float(coef * x mod p); mode 1: float -> int mod p;
-// mode 2: float *= coef (coef 0 writes 0); mode 3: int mod p *= coef
+// mode 2: float *= coef (coef 0 writes 0); mode 3: int mod p *= coef;
+// mode 4: int mod p reduced to [0, p)
 template <int MODE, bool VEC>
 __global__ void convert_kernel(V d, int64_t rows, int64_t cols, uint32_t coef, float fcoef, uint32_t p,
                                uint32_t m) {
   const int64_t cw = VEC ? cols / 4 : cols;
   const int64_t total = rows * cw;
   auto f = [&](uint32_t x) -> uint32_t {
-    if (MODE == 0) {
-      uint32_t v = coef == 0 ? 0u : mulmod(coef, x, p, m);
-      return __float_as_uint((float)v);
-    } else if (MODE == 1) {
-      uint32_t v = __float2uint_rn(__uint_as_float(x));  // exact integer < 2^24
-      uint32_t q = __umulhi(v, m);
-      return red2p(v - q * p, p);
-    } else if (MODE == 2) {
+    if (MODE == 2) {
       return __float_as_uint(fcoef == 0.f ? 0.f : fcoef * __uint_as_float(x));
+    } else if (MODE == 3) {
+      return coef == 0 ? 0u : mulmod(coef, bred(x, p, m), p, m);
     } else {
-      return coef == 0 ? 0u : mulmod(coef, x, p, m);
+      return bred(x, p, m);
     }
   };
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
@@ -211,13 +215,14 @@ static cudaError_t conv(View d, uint32_t coef, float fcoef, uint32_t p, cudaStre
   return cudaGetLastError();
 }
 
-cudaError_t launch_to_float_scaled(View d, uint32_t coef, uint32_t p, cudaStream_t s) {
-  return conv<0>(d, coef % p, 0.f, p, s);
-}
-cudaError_t launch_from_float_mod(View d, uint32_t p, cudaStream_t s) { return conv<1>(d, 0, 0.f, p, s); }
 cudaError_t launch_scale_f(View d, float coef, cudaStream_t s) { return conv<2>(d, 0, coef, 0, s); }
 cudaError_t launch_scale_modp(View d, uint32_t coef, uint32_t p, cudaStream_t s) {
   return conv<3>(d, coef % p, 0.f, p, s);
+}
+cudaError_t launch_canon_modp(View d, uint32_t p, cudaStream_t s) { return conv<4>(d, 0, 0.f, p, s); }
+cudaError_t launch_zero(View d, cudaStream_t s) {
+  if (d.rows == 0 || d.cols == 0) return cudaSuccess;
+  return cudaMemset2DAsync(d.ptr, d.ld * 4, 0, d.cols * 4, d.rows, s);
 }
 
 cudaError_t launch_copy(View d, View src, cudaStream_t s) {

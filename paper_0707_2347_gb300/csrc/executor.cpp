@@ -151,6 +151,7 @@ void Exec::leaf(Scalar alpha, bool acc, Scalar beta, View L, View R, View D) {
   pa.pcol_pad = (int)Kp;
   pa.transpose = 0;
   pa.p = p;
+  pa.barrett = p ? (uint32_t)(0x100000000ull / p) : 0;
   check(launch_pack(pa, mode, stream), "pack A");
   pa.src[0] = R.ptr;
   pa.ld[0] = R.ld;
@@ -171,7 +172,7 @@ void Exec::leaf(Scalar alpha, bool acc, Scalar beta, View L, View R, View D) {
   pr.t[0].sign = 1;
   pr.t[0].vec_ok = aligned16(D.ptr, D.ld);
   pr.ntargets = 1;
-  pr.tma_epi = make_target_tmap(&pr.tmap[0], D.ptr, m, n, D.ld) ? 1 : 0;
+  pr.tma_epi = make_target_tmap(&pr.tmap[0], D.ptr, m, n, D.ld, fp32) ? 1 : 0;
   pr.M = (int)m;
   pr.N = (int)n;
   pr.Kpad = (int)Kp;
@@ -227,13 +228,21 @@ void Exec::fused_level(Scalar alpha, bool acc, Scalar beta, View L, View R, View
   leaf_flops += 7 * 2 * hm * hn * hk;
   leaf_products += 7;
   ++leaf_launches;
-  // D <- beta D (or 0), as float32 for the reductions
-  ++ew_launches;
-  if (!dry) {
-    if (fp32)
-      check(launch_scale_f(D, acc ? beta.f : 0.f, stream), "fused prologue");
-    else
-      check(launch_to_float_scaled(D, acc ? beta.u : 0u, p, stream), "fused prologue");
+  // prologue: D <- beta D; nothing when beta = 1, zeros for C <- alpha AB.
+  // The products are then added as unreduced representatives (mod p), so D
+  // stays lazy until a consumer or the final pass reduces it.
+  lazy = lazy || !fp32;
+  const bool keep = acc && (fp32 ? beta.f == 1.f : beta.u == 1u);
+  if (!keep) {
+    ++ew_launches;
+    if (!dry) {
+      if (!acc)
+        check(launch_zero(D, stream), "fused prologue");
+      else if (fp32)
+        check(launch_scale_f(D, beta.f, stream), "fused prologue");
+      else
+        check(launch_scale_modp(D, beta.u, p, stream), "fused prologue");
+    }
   }
   GemmParams P;
   fill_common(P, *this, alpha, false, beta, EPI_REDUCE);
@@ -297,6 +306,8 @@ void Exec::fused_level(Scalar alpha, bool acc, Scalar beta, View L, View R, View
       pa.pcol_pad = (int)Kp;
       pa.transpose = 0;
       pa.p = p;
+      pa.barrett = p ? (uint32_t)(0x100000000ull / p) : 0;
+      pb.barrett = pa.barrett;
       pb.rows = (int)hk;
       pb.cols = (int)hn;
       pb.prow_pad = (int)Np;
@@ -323,7 +334,7 @@ void Exec::fused_level(Scalar alpha, bool acc, Scalar beta, View L, View R, View
         }
         pr.tma_epi = 1;
         for (int t = 0; t < pr.ntargets; ++t)
-          if (!make_target_tmap(&pr.tmap[t], pr.t[t].ptr, hm, hn, pr.t[t].ld)) pr.tma_epi = 0;
+          if (!make_target_tmap(&pr.tmap[t], pr.t[t].ptr, hm, hn, pr.t[t].ld, fp32)) pr.tma_epi = 0;
         pr.M = (int)hm;
         pr.N = (int)hn;
         pr.Kpad = (int)Kp;
@@ -341,8 +352,6 @@ void Exec::fused_level(Scalar alpha, bool acc, Scalar beta, View L, View R, View
       if (timing) timing->end(stream, 7 * 2.0 * hm * hn * hk * limb_products());
     }
   }
-  ++ew_launches;
-  if (!dry && !fp32) check(launch_from_float_mod(D, p, stream), "fused epilogue");
 }
 
 // ------------------------------------------------------------- recursion

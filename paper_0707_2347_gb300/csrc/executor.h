@@ -52,6 +52,8 @@ struct Exec {
   int64_t tmp_elems = 0, tmp_peak_elems = 0;
   int64_t add_elems = 0, leaf_flops = 0, leaf_launches = 0, ew_launches = 0, leaf_products = 0;
 
+  bool lazy = false;  // some destination holds unreduced representatives (mod p)
+
   cudaError_t cuda_err = cudaSuccess;
   std::string fail;  // first failure description
 

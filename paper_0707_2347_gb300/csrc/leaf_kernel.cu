@@ -109,12 +109,17 @@ __device__ __forceinline__ uint32_t combine(const PackArgs &a, int o, const uint
     }
     return __float_as_uint(s);
   } else {
+    // sources hold any representative below 2^31: Barrett-reduce each first
+    const uint32_t m = a.barrett;
     uint32_t s = 0;
 #pragma unroll
     for (int q = 0; q < kMaxSrc; ++q) {
       const int c = a.coef[o][q];
-      if (c > 0) s += v[q];
-      if (c < 0) s += p - v[q];
+      if (c != 0) {
+        uint32_t r = v[q] - __umulhi(v[q], m) * p;
+        r = min(r, r - p);
+        s += c > 0 ? r : p - r;
+      }
     }
     return red4p(s, p);
   }
@@ -228,21 +233,21 @@ constexpr int kChunkKB = 15;                  // k-blocks between in-place reduc
 constexpr uint64_t kWaitNs = 4000000000ull;  // bounded wait: 4 s
 constexpr int kPlaneBytes = kBM * kBK * 2;    // 16 KB
 constexpr int kBBytes = 256 * kBK * 2;        // 32 KB
-constexpr int kEpiBytes = 4 * kBM * 32 * 4;   // 64 KB: 128 rows x 128 fp32 columns, 4 boxes
+constexpr int kEpiBytes = 2 * kBM * 32 * 4;   // 32 KB: 128 rows x 64 columns, 2 boxes of 32
 
 template <int MODE>
 struct Cfg;
 template <>
 struct Cfg<MODE_MODP1> {
-  static constexpr int BN = 256, A_PLANES = 1, STAGES = 3, ACC_BUFS = 2, BUF_COLS = 256;
+  static constexpr int BN = 256, A_PLANES = 1, STAGES = 4, ACC_BUFS = 2, BUF_COLS = 256;
 };
 template <>
 struct Cfg<MODE_MODP2> {
-  static constexpr int BN = 128, A_PLANES = 2, STAGES = 2, ACC_BUFS = 1, BUF_COLS = 512;
+  static constexpr int BN = 128, A_PLANES = 2, STAGES = 3, ACC_BUFS = 1, BUF_COLS = 512;
 };
 template <>
 struct Cfg<MODE_FP32> {
-  static constexpr int BN = 128, A_PLANES = 2, STAGES = 2, ACC_BUFS = 2, BUF_COLS = 256;
+  static constexpr int BN = 128, A_PLANES = 2, STAGES = 3, ACC_BUFS = 2, BUF_COLS = 256;
 };
 template <int MODE>
 __host__ __device__ constexpr int stage_bytes() {
@@ -413,21 +418,25 @@ struct Epi {
     r = r < 0.f ? r + pf : r;
     return __float_as_uint(r + 12582912.0f) - 0x4B400000u;
   }
-  __device__ __forceinline__ uint32_t mulmod(uint32_t u, uint32_t x) const {
+  __device__ __forceinline__ uint32_t mulmod(uint32_t u, uint32_t x) const {  // u, x < p
     uint32_t prod = u * x;
     uint32_t q = __umulhi(prod, m);
     uint32_t r = prod - q * p;
     return min(r, r - p);
   }
+  __device__ __forceinline__ uint32_t red(uint32_t x) const {  // any x -> [0, p)
+    uint32_t q = __umulhi(x, m);
+    uint32_t r = x - q * p;
+    return min(r, r - p);
+  }
 };
 
-// Results of 8 consecutive columns of one row, as the 32-bit words written
-// to the target: mod p values (STORE), float values (REDUCE, sign folded in)
-// or floats (FP32).  `c8` holds beta-source words when the epilogue adds
-// beta * T0 (STORE) and is ignored otherwise.
+// Values of 8 consecutive columns of one row before any beta term: mod p
+// results (alpha applied; REDUCE: the signed contribution p - v for a
+// negative target) or floats (FP32: alpha applied, sign folded for REDUCE).
 template <int MODE>
 __device__ __forceinline__ void tile_values(const GemmParams &P, const Epi &E, uint32_t d, int col, int sign,
-                                            const uint32_t (&c8)[8], uint32_t (&v)[8]) {
+                                            uint32_t *v) {
   if (MODE == MODE_MODP2) {
     float hh[8], hl[8], lh[8], ll[8];
     tmem_ld8(d + col, hh);
@@ -456,11 +465,7 @@ __device__ __forceinline__ void tile_values(const GemmParams &P, const Epi &E, u
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
       float f = P.alpha_f * (a[e] + b[e]);
-      if (P.epilogue == EPI_STORE) {
-        if (P.use_beta) f += P.beta_f * __uint_as_float(c8[e]);
-      } else if (sign < 0) {
-        f = -f;
-      }
+      if (P.epilogue == EPI_REDUCE && sign < 0) f = -f;
       v[e] = __float_as_uint(f);
     }
     return;
@@ -469,17 +474,17 @@ __device__ __forceinline__ void tile_values(const GemmParams &P, const Epi &E, u
   for (int e = 0; e < 8; ++e) {
     uint32_t x = v[e];
     if (P.alpha_u != 1) x = E.mulmod(P.alpha_u, x);
-    if (P.epilogue == EPI_STORE) {
-      if (P.use_beta) {
-        uint32_t w = x + E.mulmod(P.beta_u, c8[e]);
-        x = min(w, w - E.p);
-      }
-    } else {
-      if (sign < 0) x = x == 0 ? 0u : E.p - x;
-      x = __float_as_uint((float)x);
-    }
+    if (P.epilogue == EPI_REDUCE && sign < 0) x = x == 0 ? 0u : E.p - x;
     v[e] = x;
   }
+}
+
+// value + beta * c for a STORE with beta (c may be any representative mod p)
+template <int MODE>
+__device__ __forceinline__ uint32_t add_beta(const GemmParams &P, const Epi &E, uint32_t v, uint32_t c) {
+  if (MODE == MODE_FP32) return __float_as_uint(__uint_as_float(v) + P.beta_f * __uint_as_float(c));
+  const uint32_t w = v + E.mulmod(P.beta_u, E.red(c));
+  return min(w, w - E.p);
 }
 
 // ------------------------------------------------------------- the GEMM
@@ -636,8 +641,9 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_kernel(const __grid_constant
     __syncwarp();
   } else {
     // ================================= epilogue =================================
-    // warp w in 2..9 reads tensor-memory lanes 32 (w % 4) .. +31 and the 64
-    // columns (w - 2) / 4 of each 128-column chunk of the tile.
+    // Warp w in 2..9 reads tensor-memory lanes 32 (w % 4) .. +31.  The tile is
+    // written in 64-column chunks through a 32 KB staging buffer (two boxes of
+    // 32 columns); in each chunk warp w owns box (w - 2) / 4.
     const int et = tid - 64;
     const int q4 = warp & 3;
     const int hsel = (warp - 2) >> 2;
@@ -659,112 +665,90 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_kernel(const __grid_constant
       const uint32_t use = C::ACC_BUFS == 2 ? (tcount >> 1) : tcount;
       const uint32_t d = tmem + lane_addr + (uint32_t)(buf * C::BUF_COLS);
       const bool tma = pr.tma_epi != 0;
-      const bool load_c = tma && P.epilogue == EPI_STORE && P.use_beta;
+      const bool with_beta = P.epilogue == EPI_STORE && P.use_beta;
       const int sign = pr.t[0].sign;
       const int gr = ti.m0 + row;
       bool bad = false;
-      for (int ch = 0; ch < BN / 128 && !bad; ++ch) {
-        const int cbase = ti.n0 + ch * 128;  // first global column of the chunk
-        if (tma) {
-          // the previous chunk's TMA must have read the staging buffer
-          if (issuer) {
-            bulk_wait_read0();
-            if (load_c) {
-              int boxes = 0;
-              for (int b = 0; b < 4; ++b) boxes += cbase + 32 * b < pr.N;
-              mbar_expect_tx(cbar, boxes * 16384);
-              for (int b = 0; b < 4; ++b)
-                if (cbase + 32 * b < pr.N) tma_load(eb + b * 16384, &pr.tmap[0], cbase + 32 * b, ti.m0, cbar);
-            }
+      if (modp && nkb > 16) {
+        const int ndrain = (nkb - 1) / kChunkKB;
+        for (int q = 0; q < ndrain; ++q, ++dcount) {
+          wait_bar(drain_full, dcount & 1, ctl, P.err);
+          epi_sync();  // every epilogue thread takes the same exit on a timeout
+          if (ctl->abort) {
+            bad = true;
+            break;
           }
-          epi_sync();
-        }
-        if (ch == 0) {
-          if (modp && nkb > 16) {
-            const int ndrain = (nkb - 1) / kChunkKB;
-            for (int q = 0; q < ndrain; ++q, ++dcount) {
-              wait_bar(drain_full, dcount & 1, ctl, P.err);
-              epi_sync();  // every epilogue thread takes the same exit on a timeout
-              if (ctl->abort) {
-                bad = true;
-                break;
-              }
-              tc_fence_after();
-              constexpr int cols = MODE == MODE_MODP2 ? 512 : 256;
-              // each of the 8 warps reduces its lane quadrant, half the columns
-              for (int c = hsel * (cols / 2); c < (hsel + 1) * (cols / 2); c += 8) {
-                float v[8];
-                tmem_ld8(d + c, v);
-                tmem_wait_ld();
+          tc_fence_after();
+          constexpr int cols = MODE == MODE_MODP2 ? 512 : 256;
+          for (int c = hsel * (cols / 2); c < (hsel + 1) * (cols / 2); c += 8) {
+            float v[8];
+            tmem_ld8(d + c, v);
+            tmem_wait_ld();
 #pragma unroll
-                for (int e = 0; e < 8; ++e) v[e] = E.fr(v[e]);
-                tmem_st8(d + c, v);
-              }
-              tmem_wait_st();
-              tc_fence_before();
-              mbar_arrive(drain_empty);
-            }
-            if (bad) break;
+            for (int e = 0; e < 8; ++e) v[e] = E.fr(v[e]);
+            tmem_st8(d + c, v);
           }
-          wait_bar(&acc_full[buf], use & 1, ctl, P.err);
+          tmem_wait_st();
+          tc_fence_before();
+          mbar_arrive(drain_empty);
         }
-        if (load_c) {
-          wait_bar(cbar, cphase, ctl, P.err);
-          cphase ^= 1;
-        }
-        epi_sync();
-        if (ctl->abort) {
-          bad = true;
-          break;
-        }
-        tc_fence_after();
-#pragma unroll 1
-        for (int s = 0; s < 8; ++s) {
-          const int cc = hsel * 64 + 8 * s;  // column within the chunk
-          const int box = cc >> 5, j = (cc & 31) >> 2;
-          const uint32_t a0 = eb + box * 16384 + row * 128 + ((j ^ (row & 7)) << 4);
-          const uint32_t a1 = eb + box * 16384 + row * 128 + (((j + 1) ^ (row & 7)) << 4);
-          uint32_t c8[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-          const int gc = cbase + cc;
-          if (P.epilogue == EPI_STORE && P.use_beta) {
-            if (load_c) {
-              uint4 x0 = lds128(a0), x1 = lds128(a1);
-              c8[0] = x0.x; c8[1] = x0.y; c8[2] = x0.z; c8[3] = x0.w;
-              c8[4] = x1.x; c8[5] = x1.y; c8[6] = x1.z; c8[7] = x1.w;
-            } else if (gr < pr.M) {
-              const uint32_t *src = reinterpret_cast<const uint32_t *>((const char *)pr.t[0].ptr) + (int64_t)gr * pr.t[0].ld;
-              for (int e = 0; e < 8; ++e) c8[e] = gc + e < pr.N ? src[gc + e] : 0u;
-            }
-          }
-          uint32_t v[8];
-          tile_values<MODE>(P, E, d, ch * 128 + cc, sign, c8, v);
-          if (tma) {
-            sts128(a0, make_uint4(v[0], v[1], v[2], v[3]));
-            sts128(a1, make_uint4(v[4], v[5], v[6], v[7]));
-          } else if (gr < pr.M) {
-            // direct path for targets TMA cannot address (odd leading dimension)
-            for (int e = 0; e < 8; ++e) {
-              if (gc + e >= pr.N) break;
-              if (P.epilogue == EPI_STORE) {
-                reinterpret_cast<uint32_t *>((char *)pr.t[0].ptr)[(int64_t)gr * pr.t[0].ld + gc + e] = v[e];
-              } else {
-                for (int t = 0; t < pr.ntargets; ++t)
-                  atomicAdd(reinterpret_cast<float *>((char *)pr.t[t].ptr) + (int64_t)gr * pr.t[t].ld + gc + e,
-                            __uint_as_float(v[e]));
-              }
-            }
-          }
-        }
-        if (ch == BN / 128 - 1) {
+        if (bad) break;
+      }
+      wait_bar(&acc_full[buf], use & 1, ctl, P.err);
+      epi_sync();
+      if (ctl->abort) break;
+      tc_fence_after();
+      constexpr int NCH = BN / 64;
+      for (int ch = 0; ch < NCH; ++ch) {
+        const int tc0 = ch * 64 + hsel * 32;  // tile column of this thread's first value
+        uint32_t v[32];
+#pragma unroll
+        for (int s = 0; s < 4; ++s) tile_values<MODE>(P, E, d, tc0 + 8 * s, sign, v + 8 * s);
+        if (ch == NCH - 1) {
           tc_fence_before();
           mbar_arrive(&acc_empty[buf]);  // accumulators free for the next tile
         }
+        const int gc0 = ti.n0 + tc0;
         if (tma) {
+          if (issuer) {
+            bulk_wait_read0();  // the previous chunk's TMA has read the buffer
+            if (with_beta) {
+              int boxes = 0;
+              for (int b = 0; b < 2; ++b) boxes += ti.n0 + ch * 64 + 32 * b < pr.N;
+              mbar_expect_tx(cbar, boxes * 16384);
+              for (int b = 0; b < 2; ++b)
+                if (ti.n0 + ch * 64 + 32 * b < pr.N)
+                  tma_load(eb + b * 16384, &pr.tmap[0], ti.n0 + ch * 64 + 32 * b, ti.m0, cbar);
+            }
+          }
+          epi_sync();
+          if (with_beta) {
+            wait_bar(cbar, cphase, ctl, P.err);
+            cphase ^= 1;
+          }
+          const uint32_t rowbase = eb + hsel * 16384 + row * 128;
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const uint32_t a = rowbase + ((j ^ (row & 7)) << 4);
+            uint4 w = make_uint4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+            if (with_beta) {
+              const uint4 c = lds128(a);
+              w.x = add_beta<MODE>(P, E, w.x, c.x);
+              w.y = add_beta<MODE>(P, E, w.y, c.y);
+              w.z = add_beta<MODE>(P, E, w.z, c.z);
+              w.w = add_beta<MODE>(P, E, w.w, c.w);
+            }
+            sts128(a, w);
+          }
           fence_proxy_async();
           epi_sync();
+          if (ctl->abort) {
+            bad = true;
+            break;
+          }
           if (issuer) {
-            for (int b = 0; b < 4; ++b) {
-              const int x = cbase + 32 * b;
+            for (int b = 0; b < 2; ++b) {
+              const int x = ti.n0 + ch * 64 + 32 * b;
               if (x >= pr.N) break;
               if (P.epilogue == EPI_STORE) {
                 tma_store(&pr.tmap[0], x, ti.m0, eb + b * 16384);
@@ -773,6 +757,25 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_kernel(const __grid_constant
               }
             }
             bulk_commit();
+          }
+        } else if (gr < pr.M) {
+          // direct path for targets TMA cannot address (misaligned leading dimension)
+#pragma unroll
+          for (int e = 0; e < 32; ++e) {
+            const int gc = gc0 + e;
+            if (gc >= pr.N) continue;
+            if (P.epilogue == EPI_STORE) {
+              uint32_t *dst = reinterpret_cast<uint32_t *>((char *)pr.t[0].ptr) + (int64_t)gr * pr.t[0].ld + gc;
+              *dst = with_beta ? add_beta<MODE>(P, E, v[e], *dst) : v[e];
+            } else {
+              for (int t = 0; t < pr.ntargets; ++t) {
+                if (modp)
+                  atomicAdd(reinterpret_cast<unsigned int *>((char *)pr.t[t].ptr) + (int64_t)gr * pr.t[t].ld + gc, v[e]);
+                else
+                  atomicAdd(reinterpret_cast<float *>((char *)pr.t[t].ptr) + (int64_t)gr * pr.t[t].ld + gc,
+                            __uint_as_float(v[e]));
+              }
+            }
           }
         }
       }
@@ -828,13 +831,13 @@ __global__ void leaf_simt_kernel(const __grid_constant__ SimtArgs A, const __gri
     uint64_t v = (acc * P.alpha_u) % p;
     if (P.epilogue == EPI_STORE) {
       uint32_t *dst = (uint32_t *)A.t[0].ptr + (int64_t)r * A.t[0].ld + c;
-      if (P.use_beta) v = (v + (uint64_t)P.beta_u * (*dst)) % p;
+      if (P.use_beta) v = (v + (uint64_t)P.beta_u * ((*dst) % p)) % p;
       *dst = (uint32_t)v;
     } else {
       for (int t = 0; t < A.ntargets; ++t) {
-        float *dst = (float *)A.t[t].ptr + (int64_t)r * A.t[t].ld + c;
+        unsigned int *dst = (unsigned int *)A.t[t].ptr + (int64_t)r * A.t[t].ld + c;
         uint64_t w = A.t[t].sign > 0 ? v : (p - v) % p;
-        atomicAdd(dst, (float)w);
+        atomicAdd(dst, (unsigned int)w);
       }
     }
   } else {

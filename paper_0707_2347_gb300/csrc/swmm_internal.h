@@ -55,14 +55,16 @@ struct PackArgs {
   int32_t prow_pad, pcol_pad;  // packed extent (packed rows x packed cols)
   int32_t transpose;
   uint32_t p;
+  uint32_t barrett;  // floor(2^32 / p)
 };
 cudaError_t launch_pack(const PackArgs &a, int mode, cudaStream_t s);
 
 // ---------------------------------------------------------------- leaf GEMM
 // One product of a grouped leaf launch: P = A' x B' from packed operands.
 // Epilogue STORE: T0 <- alpha * P + beta * T0 (only target 0).
-// Epilogue REDUCE: for each target t, T_t += sign_t * alpha * P, where the
-// targets hold float32 values (mod p values are exact integers < 2^24).
+// Epilogue REDUCE: for each target t, T_t += sign_t * alpha * P (mod p: the
+// canonical contribution, p - v for a negative sign, added as an unsigned
+// integer, so targets hold representatives that are reduced later).
 constexpr int kMaxTargets = 4;
 constexpr int kMaxProducts = 7;
 
@@ -107,7 +109,7 @@ struct GemmParams {
 bool make_tmap(CUtensorMap *map, const void *base, int64_t rows, int64_t kpad, int box_rows);
 // Encode a 2-D tensor map over a target block of 32-bit words (rows x cols,
 // leading dimension ld); false when TMA cannot address it (alignment).
-bool make_target_tmap(CUtensorMap *map, const void *base, int64_t rows, int64_t cols, int64_t ld);
+bool make_target_tmap(CUtensorMap *map, const void *base, int64_t rows, int64_t cols, int64_t ld, bool fp32);
 
 cudaError_t launch_gemm_tc(const GemmParams &P, int mode, int num_sms, cudaStream_t s);
 
@@ -132,15 +134,14 @@ cudaError_t launch_leaf_simt(const SimtArgs &A, const GemmParams &P, int mode, c
 cudaError_t launch_add(View dst, View s1, View s2, int64_t c1, int64_t c2, uint32_t p, int fp32,
                        cudaStream_t s);
 cudaError_t launch_add_f(View dst, View s1, View s2, float c1, float c2, cudaStream_t s);
-// dst <- coef * dst (mod p) written as float32 (REDUCE prologue); coef 0
-// writes zeros.
-cudaError_t launch_to_float_scaled(View dst, uint32_t coef, uint32_t p, cudaStream_t s);
 // FP32: dst <- coef * dst (coef 0 writes zeros)
 cudaError_t launch_scale_f(View dst, float coef, cudaStream_t s);
-// dst(float, exact integer < 2^24) -> int32 mod p, canonical (REDUCE epilogue)
-cudaError_t launch_from_float_mod(View dst, uint32_t p, cudaStream_t s);
-// mod p: dst <- coef * dst mod p (int32 in place)
+// mod p: dst <- coef * dst mod p, canonical (int32 in place; coef 0 writes 0)
 cudaError_t launch_scale_modp(View dst, uint32_t coef, uint32_t p, cudaStream_t s);
+// mod p: dst <- dst mod p (any representative below 2^32 -> [0, p))
+cudaError_t launch_canon_modp(View dst, uint32_t p, cudaStream_t s);
+// dst <- 0
+cudaError_t launch_zero(View dst, cudaStream_t s);
 // dst <- src
 cudaError_t launch_copy(View dst, View src, cudaStream_t s);
 
