@@ -203,6 +203,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-classical", action="store_true")
+    ap.add_argument("--no-graph", action="store_true", help="launch kernels directly instead of a CUDA graph")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     w = WORKLOADS[args.workload]
@@ -272,7 +273,8 @@ def main():
             ms = float(t.item())
         return ms
 
-    opts = S.Opts(mode=mode, p=p or 65521, sched=w["sched"], depth=w["depth"], flags=S.FLAG_TIMING)
+    gflag = 0 if args.no_graph else S.FLAG_GRAPH
+    opts = S.Opts(mode=mode, p=p or 65521, sched=w["sched"], depth=w["depth"], flags=S.FLAG_TIMING | gflag)
     with Clocks(local) as clk:
         ms = timed(opts, args.steps, args.warmup)
     gemm_ms, gemm_launches, tensor_flops = h.leaf_timing(reset=True)
@@ -292,19 +294,20 @@ def main():
                    "depth": w["depth"], "l2": f"inputs {3 * m * n * 4 / 1e6:.0f} MB > 129 MB L2, no flush",
                    "parallelism": f"replicas x{world}"},
         "gpu_launches": int((st["leaf_launches"] + st["ew_launches"]) * args.steps),
+        "cuda_graph": not args.no_graph,
         "memory": {"workspace_bytes": st["workspace_bytes"], "plan_extra_elems": st["plan_extra_elems"],
                    "paper_extra_elems_same_levels": st["paper_extra_elems"], "staging_bytes": st["staging_bytes"]},
         "roofline": {"bound": "tensor", "achieved": round(achieved, 1), "peak": sustained, "unit": "TFLOP/s",
                      "frac": round(achieved / sustained, 4), "traffic": None,
                      "kernel": "gemm_kernel (leaf products, fp16 limb MMAs counted)",
-                     "peak_kind": f"{peak_kind} bf16 sustained", "launches_per_step": gemm_launches // max(args.steps, 1),
-                     "gemm_ms_per_step": round(gemm_ms / max(args.steps, 1), 4)},
+                     "peak_kind": f"{peak_kind} bf16 sustained", "launches_per_step": st["leaf_launches"],
+                     "gemm_ms_per_step": round(gemm_ms / max(gemm_launches, 1) * st["leaf_launches"], 4)},
     }
     line["clocks"] = clk.summary()
 
     if not args.no_classical and w["sched"] != CLASSICAL:
         dC.copy_(dC0)
-        copts = S.Opts(mode=mode, p=p or 65521, sched=CLASSICAL, depth=0, flags=S.FLAG_TIMING)
+        copts = S.Opts(mode=mode, p=p or 65521, sched=CLASSICAL, depth=0, flags=S.FLAG_TIMING | gflag)
         cms = timed(copts, args.steps, args.warmup)
         cg_ms, cg_n, cg_fl = h.leaf_timing(reset=True)
         cval = world * flops / (cms * 1e-3) / 1e9
@@ -315,7 +318,7 @@ def main():
     if not args.no_e2e:
         pin = [torch.from_numpy(x).pin_memory() for x in (A, B, C)]
         out = torch.empty_like(pin[2]).pin_memory()
-        opts_e = S.Opts(mode=mode, p=p or 65521, sched=w["sched"], depth=w["depth"])
+        opts_e = S.Opts(mode=mode, p=p or 65521, sched=w["sched"], depth=w["depth"], flags=gflag)
 
         def e2e_step():
             dA.copy_(pin[0], non_blocking=True)

@@ -72,6 +72,7 @@ extern "C" {
 #define SWMM_T9_ACC 9    /* Table 9, C <- aAB + bC, read-only inputs */
 #define SWMM_IPMM 10     /* Algorithm 2, C <- AB, read-only, no extra memory */
 #define SWMM_T4M_OVL 11  /* Section 5.1 variant of Table 4: overwrites A11, A21 */
+#define SWMM_AUTO (-1)   /* batched calls: the autotuner picks schedule and depth */
 
 /* flags */
 #define SWMM_FLAG_UNFUSED 1u   /* run the table at every level down to
@@ -82,6 +83,12 @@ extern "C" {
                                   of the tcgen05 kernel (diagnostics) */
 #define SWMM_FLAG_TIMING 4u    /* record a CUDA event pair around every leaf
                                   GEMM launch (read with swmm_leaf_timing) */
+#define SWMM_FLAG_GRAPH 8u     /* capture the call's launches in a CUDA graph
+                                  on first use and replay it for identical
+                                  calls (same sizes, pointers, options and
+                                  scalars); the graph runs on an internal
+                                  stream ordered after and before the handle's
+                                  stream by events */
 
 typedef struct swmm_ctx *swmm_t;
 
@@ -129,6 +136,25 @@ int swmm_mul(swmm_t h, int64_t m, int64_t k, int64_t n,
              const void *A, int64_t lda, const void *B, int64_t ldb,
              void *C, int64_t ldc, const swmm_opts *opts);
 
+/* One problem of a batched call (C <- alpha A B + beta C, read-only A, B). */
+typedef struct {
+  int64_t m, k, n;
+  const void *A;
+  int64_t lda;
+  const void *B;
+  int64_t ldb;
+  void *C;
+  int64_t ldc;
+  int32_t mode;          /* SWMM_MODP or SWMM_FP32 */
+  uint32_t p;            /* modulus (SWMM_MODP) */
+  uint32_t alpha_u, beta_u; /* scalars (SWMM_MODP) */
+  float alpha_f, beta_f;    /* scalars (SWMM_FP32) */
+  int32_t sched;         /* SWMM_AUTO, SWMM_CLASSICAL, SWMM_T2_HLJJTT or SWMM_T9_ACC */
+  int32_t depth;         /* used when sched != SWMM_AUTO */
+  int32_t chosen_sched;  /* out: the schedule that ran */
+  int32_t chosen_depth;  /* out: the depth that ran */
+} swmm_problem;
+
 /* C <- alpha A B + beta C with read-only A and B: SWMM_CLASSICAL,
  * SWMM_T2_HLJJTT (Table 2), SWMM_T9_ACC (Table 9, square). */
 int swmm_muladd(swmm_t h, int64_t m, int64_t k, int64_t n, const void *alpha,
@@ -166,6 +192,23 @@ int swmm_mul_inplace(swmm_t h, int64_t m, int64_t k, int64_t n,
                      void *A, int64_t lda, void *B, int64_t ldb,
                      void *C, int64_t ldc, const void *alpha, const void *beta,
                      const swmm_opts *opts);
+
+/* Many independent products of uneven shapes in one call.  Each problem
+ * runs the plan its `sched` names (SWMM_AUTO: the autotuner's choice, see
+ * swmm_autotune); odd dimensions are peeled at every Winograd level.  With
+ * SWMM_FLAG_GRAPH the whole batch is captured once into one CUDA graph and
+ * replayed by identical later calls.  The C blocks of different problems
+ * must not overlap. */
+int swmm_muladd_batched(swmm_t h, int count, swmm_problem *probs, uint32_t flags);
+
+/* The autotuner: for C <- A B + C of size (m, k, n) in `mode`, evaluate the
+ * classical product, Table 2 and (square) Table 9 at depths 1-3 with the
+ * planner and a cost model of this GPU (tensor rate by leaf size, HBM-bound
+ * passes, launch cost), and return the fastest (*sched, *depth), its
+ * modelled time (*est_us) and its peak temporary elements (*extra_elems).
+ * No device work; h may be NULL. */
+int swmm_autotune(swmm_t h, int64_t m, int64_t k, int64_t n, int32_t mode, uint32_t p,
+                  int32_t *sched, int32_t *depth, double *est_us, int64_t *extra_elems);
 
 /* Peak temporary elements the plan for (m, k, n, opts) uses
  * (*plan_elems) and the paper's count for the same levels (*paper_elems;

@@ -1,11 +1,13 @@
-// C ABI of the library (include/swmm.h): argument validation, workspace
-// management and dispatch to the schedule executor.
+// C ABI of the library (include/swmm.h): argument validation, planning,
+// workspace management, CUDA-graph capture and dispatch to the executor.
 #include "swmm.h"
 
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
+#include <memory>
 #include <string>
+#include <vector>
 
 #include "executor.h"
 
@@ -54,19 +56,13 @@ bool make_target_tmap(CUtensorMap *map, const void *base, int64_t rows, int64_t 
   // the element type matters for TMA reduce-add: float sums or unsigned
   // integer sums of mod p contributions
   CUresult r = fn(map, fp32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_UINT32, 2,
-                  const_cast<void *>(base), dims, strides, box, estr,
-                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                  const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
 }
 
-}  // namespace swmm
-
-using namespace swmm;
-
-#include <vector>
-
-struct EventTimer : swmm::TimingHook {
+// Event pairs around leaf GEMM launches (SWMM_FLAG_TIMING).
+struct EventTimer : TimingHook {
   std::vector<cudaEvent_t> ev;  // pairs: 2i = begin, 2i + 1 = end
   std::vector<double> flops;
   size_t used = 0;  // pairs recorded since the last reset
@@ -91,6 +87,23 @@ struct EventTimer : swmm::TimingHook {
   }
 };
 
+// A captured call: its instantiated graph, the statistics of the capture and
+// the leaf-timing events recorded in it (their times refresh on each replay).
+struct GraphEntry {
+  std::string key;
+  cudaGraphExec_t exec = nullptr;
+  swmm_stats stats;
+  EventTimer timer;
+  GraphEntry() { std::memset(&stats, 0, sizeof(stats)); }
+  ~GraphEntry() {
+    if (exec) cudaGraphExecDestroy(exec);
+  }
+};
+
+}  // namespace swmm
+
+using namespace swmm;
+
 struct swmm_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
@@ -99,6 +112,17 @@ struct swmm_ctx {
   swmm_stats stats;
   std::string last_error;
   EventTimer timer;
+  EventTimer *last_timer = &timer;
+  // CUDA graph cache (SWMM_FLAG_GRAPH)
+  std::vector<std::unique_ptr<GraphEntry>> graphs;
+  cudaStream_t cap = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  ~swmm_ctx() {
+    graphs.clear();
+    if (cap) cudaStreamDestroy(cap);
+    if (ev_in) cudaEventDestroy(ev_in);
+    if (ev_out) cudaEventDestroy(ev_out);
+  }
 };
 
 namespace {
@@ -142,25 +166,26 @@ int64_t paper_elems(int sched, int64_t m, int64_t k, int64_t n, int levels) {
     k /= 2;
     n /= 2;
     switch (sched) {
-      case SWMM_T1_DHSS: s += m * std::max(k, n) + k * n; break;        // Eq. (1)
-      case SWMM_T2_HLJJTT: s += m * k + k * n + m * n; break;          // Eq. (2)
+      case SWMM_T1_DHSS: s += m * std::max(k, n) + k * n; break;  // Eq. (1)
+      case SWMM_T2_HLJJTT: s += m * k + k * n + m * n; break;    // Eq. (2)
       case SWMM_T4_OVL:
       case SWMM_T4M_OVL:
-      case SWMM_T5_OVR: s += n * n; break;                             // Sec. 5.1
+      case SWMM_T5_OVR: s += n * n; break;  // Sec. 5.1
       case SWMM_T6_ACLR:
       case SWMM_T7_ACCR:
-      case SWMM_T9_ACC: s += 2 * n * n; break;                         // Eq. (3), Sec. 6
-      case SWMM_T8_ACR: s += std::max(m, k) * n + m * k; break;         // Sec. 5.3
-      default: break;                                                  // IP, IPMM, classical: 0
+      case SWMM_T9_ACC: s += 2 * n * n; break;                  // Eq. (3), Sec. 6
+      case SWMM_T8_ACR: s += std::max(m, k) * n + m * k; break;  // Sec. 5.3
+      default: break;                                           // IP, IPMM, classical: 0
     }
   }
   return s;
 }
 
-// number of Winograd levels the recursion actually performs
+// number of Winograd levels the recursion performs (odd dimensions are
+// peeled, so each level halves the even core)
 int levels_possible(int64_t m, int64_t k, int64_t n, int depth) {
   int d = 0;
-  while (d < depth && m >= 2 && k >= 2 && n >= 2 && m % 2 == 0 && k % 2 == 0 && n % 2 == 0) {
+  while (d < depth && m >= 2 && k >= 2 && n >= 2) {
     m /= 2;
     k /= 2;
     n /= 2;
@@ -182,10 +207,31 @@ struct Scratch {
   int64_t bytes;
 };
 
-int run(swmm_t h, const Req &q, const swmm_opts *o, bool dry_only, int64_t *paper_out, int64_t *plan_out,
-        const Scratch *ext = nullptr) {
-  if (!h) return SWMM_EINVAL;
-  h->last_error.clear();
+// A validated, planned call.
+struct Plan {
+  Req q;
+  swmm_opts o;
+  Exec x;  // the dry run: sizes and counts
+  View L, R, D;
+  Scalar alpha, beta;
+  bool accum = false, ne = false;
+  int sched = 0, depth = 0, lv = 0;
+  int64_t cutoff = 1024;
+  Kind ipmm_acc = K_T2;
+  int64_t paper = 0;
+};
+
+void execute(const Plan &P, Exec &e) {
+  if (!P.ne) return;
+  if (P.sched == SWMM_IPMM)
+    e.ipmm(P.L, P.R, P.D, P.depth, P.cutoff, P.ipmm_acc);
+  else if (P.sched == SWMM_CLASSICAL)
+    e.leaf(P.alpha, P.accum, P.beta, P.L, P.R, P.D);
+  else
+    e.call(kind_of(P.sched), P.alpha, P.accum, P.beta, P.L, P.R, P.D, P.depth, Arena{});
+}
+
+int make_plan(swmm_t h, const Req &q, const swmm_opts *o, bool check_ptrs, Plan &P) {
   if (!o) return fail(h, SWMM_EINVAL, "opts is NULL");
   if (o->mode != SWMM_MODP && o->mode != SWMM_FP32) return fail(h, SWMM_EINVAL, "unknown mode");
   if (o->mode == SWMM_MODP && (o->p <= 2 || o->p >= 65536)) return fail(h, SWMM_EINVAL, "p must satisfy 2 < p < 65536");
@@ -193,17 +239,17 @@ int run(swmm_t h, const Req &q, const swmm_opts *o, bool dry_only, int64_t *pape
   if (q.m > (1 << 30) || q.k > (1 << 30) || q.n > (1 << 30)) return fail(h, SWMM_EINVAL, "dimension too large");
   if (o->depth < 0 || o->depth > 30) return fail(h, SWMM_EINVAL, "depth out of range");
   const int sched = o->sched;
-  const bool accum_req = q.entry == 1 || (q.entry == 2 && q.beta != nullptr);
+  const bool accum = q.entry == 1 || (q.entry == 2 && q.beta != nullptr);
   // schedule / entry point consistency (overwrite contracts, Sections 3, 5)
   bool okk = false;
   if (q.entry == 0) okk = sched == SWMM_CLASSICAL || sched == SWMM_T1_DHSS || sched == SWMM_IPMM;
   if (q.entry == 1) okk = sched == SWMM_CLASSICAL || sched == SWMM_T2_HLJJTT || sched == SWMM_T9_ACC;
-  if (q.entry == 2 && !accum_req)
+  if (q.entry == 2 && !accum)
     okk = sched == SWMM_T3_IP || sched == SWMM_T4_OVL || sched == SWMM_T4M_OVL || sched == SWMM_T5_OVR;
-  if (q.entry == 2 && accum_req) okk = sched == SWMM_T6_ACLR || sched == SWMM_T7_ACCR || sched == SWMM_T8_ACR;
+  if (q.entry == 2 && accum) okk = sched == SWMM_T6_ACLR || sched == SWMM_T7_ACCR || sched == SWMM_T8_ACR;
   if (!okk) return fail(h, SWMM_EINVAL, "schedule not valid for this entry point");
   const bool ne = q.m > 0 && q.n > 0;
-  if (!dry_only) {
+  if (check_ptrs) {
     if (ne && !q.C) return fail(h, SWMM_EINVAL, "C is NULL");
     if (ne && q.k > 0 && (!q.A || !q.B)) return fail(h, SWMM_EINVAL, "A or B is NULL");
     if (q.lda < std::max<int64_t>(q.k, 1) || q.ldb < std::max<int64_t>(q.n, 1) || q.ldc < std::max<int64_t>(q.n, 1))
@@ -225,63 +271,61 @@ int run(swmm_t h, const Req &q, const swmm_opts *o, bool dry_only, int64_t *pape
   }
   if (sched == SWMM_IPMM && q.m != q.n) return fail(h, SWMM_EINVAL, "IPMM needs m = n (Algorithm 2)");
 
-  Exec x;
+  P.q = q;
+  P.o = *o;
+  P.accum = accum;
+  P.ne = ne;
+  P.sched = sched;
+  P.depth = depth;
+  P.lv = lv;
+  Exec &x = P.x;
   x.fp32 = o->mode == SWMM_FP32;
   x.p = x.fp32 ? 0 : o->p;
   x.mode = x.fp32 ? MODE_FP32 : (o->p <= 256 ? MODE_MODP1 : MODE_MODP2);
   x.fused = !(o->flags & SWMM_FLAG_UNFUSED);
   x.simt = (o->flags & SWMM_FLAG_SIMT_LEAF) != 0;
-  x.stream = h->stream;
   x.num_sms = h->num_sms;
   x.err = h->d_err;
-  x.timing = (o->flags & SWMM_FLAG_TIMING) && !ext ? &h->timer : nullptr;
-  Scalar alpha, beta;
   if (x.fp32) {
-    alpha.f = q.alpha ? *(const float *)q.alpha : 1.f;
-    beta.f = q.beta ? *(const float *)q.beta : 0.f;
+    P.alpha.f = q.alpha ? *(const float *)q.alpha : 1.f;
+    P.beta.f = q.beta ? *(const float *)q.beta : 0.f;
   } else {
-    alpha.u = q.alpha ? *(const uint32_t *)q.alpha % x.p : 1u;
-    beta.u = q.beta ? *(const uint32_t *)q.beta % x.p : 0u;
+    P.alpha.u = q.alpha ? *(const uint32_t *)q.alpha % x.p : 1u;
+    P.beta.u = q.beta ? *(const uint32_t *)q.beta % x.p : 0u;
   }
-  View L, R, D;
-  L.ptr = (char *)q.A;
-  L.rows = q.m;
-  L.cols = q.k;
-  L.ld = q.lda;
-  R.ptr = (char *)q.B;
-  R.rows = q.k;
-  R.cols = q.n;
-  R.ld = q.ldb;
-  D.ptr = (char *)q.C;
-  D.rows = q.m;
-  D.cols = q.n;
-  D.ld = q.ldc;
-  const int64_t cutoff = o->ipmm_cutoff > 0 ? o->ipmm_cutoff : 1024;
-  const Kind ipmm_acc = o->ipmm_acc == SWMM_T9_ACC ? K_ACC : K_T2;
-
-  auto execute = [&](Exec &e) {
-    if (!ne) return;
-    if (sched == SWMM_IPMM)
-      e.ipmm(L, R, D, depth, cutoff, ipmm_acc);
-    else if (sched == SWMM_CLASSICAL)
-      e.leaf(alpha, accum_req, beta, L, R, D);
-    else
-      e.call(kind_of(sched), alpha, accum_req, beta, L, R, D, depth, Arena{});
-  };
+  P.L.ptr = (char *)q.A;
+  P.L.rows = q.m;
+  P.L.cols = q.k;
+  P.L.ld = q.lda;
+  P.R.ptr = (char *)q.B;
+  P.R.rows = q.k;
+  P.R.cols = q.n;
+  P.R.ld = q.ldb;
+  P.D.ptr = (char *)q.C;
+  P.D.rows = q.m;
+  P.D.cols = q.n;
+  P.D.ld = q.ldc;
+  P.cutoff = o->ipmm_cutoff > 0 ? o->ipmm_cutoff : 1024;
+  P.ipmm_acc = o->ipmm_acc == SWMM_T9_ACC ? K_ACC : K_T2;
   // planning pass: sizes and counts, no launches
   x.dry = true;
-  execute(x);
+  execute(P, x);
   if (!x.fail.empty()) return fail(h, SWMM_EINVAL, x.fail);
   // levels that materialise temporaries: all but a fused last one
   const int tmp_levels = (x.fused && lv > 0 && sched != SWMM_IPMM) ? lv - 1 : lv;
-  const int64_t paper = paper_elems(sched, q.m, q.k, q.n, tmp_levels);
-  if (paper_out) *paper_out = paper;
-  if (plan_out) *plan_out = x.tmp_peak_elems;
-  if (dry_only) return SWMM_OK;
+  P.paper = paper_elems(sched, q.m, q.k, q.n, tmp_levels);
+  return SWMM_OK;
+}
 
+// Issue a planned call on `stream`: workspace, kernels, final canonical
+// pass, release.  Adds its counters to `st`.
+int enqueue(swmm_t h, const Plan &P, cudaStream_t stream, TimingHook *timing, const Scratch *ext, swmm_stats &st) {
+  const Exec &x = P.x;
   Exec r = x;
   r.dry = false;
   r.lazy = false;
+  r.stream = stream;
+  r.timing = timing;
   r.ws_top = r.ws_peak = 0;
   r.tmp_elems = r.tmp_peak_elems = 0;
   r.add_elems = r.leaf_flops = r.leaf_launches = r.ew_launches = r.leaf_products = 0;
@@ -295,44 +339,149 @@ int run(swmm_t h, const Req &q, const swmm_opts *o, bool dry_only, int64_t *pape
                       std::to_string(ext->bytes) + "-byte static scratch");
     r.ws = x.ws_peak > 0 ? ext->base : nullptr;
     r.stage = x.stage_need > 0 ? ext->base + ws_bytes : nullptr;
-  } else if (x.ws_peak > 0) {
-    if (cudaMallocAsync((void **)&r.ws, x.ws_peak, h->stream) != cudaSuccess) {
+  } else {
+    if (x.ws_peak > 0 && cudaMallocAsync((void **)&r.ws, x.ws_peak, stream) != cudaSuccess) {
       cudaGetLastError();
       return fail(h, SWMM_ENOMEM, "workspace allocation failed");
     }
-  }
-  if (!ext && x.stage_need > 0) {
-    if (cudaMallocAsync((void **)&r.stage, x.stage_need, h->stream) != cudaSuccess) {
+    if (x.stage_need > 0 && cudaMallocAsync((void **)&r.stage, x.stage_need, stream) != cudaSuccess) {
       cudaGetLastError();
-      if (r.ws) cudaFreeAsync(r.ws, h->stream);
+      if (r.ws) cudaFreeAsync(r.ws, stream);
       return fail(h, SWMM_ENOMEM, "staging allocation failed");
     }
   }
-  execute(r);
+  execute(P, r);
   if (r.lazy && r.ok()) {
     // fused levels leave unreduced representatives: one canonicalising pass
     ++r.ew_launches;
-    cudaError_t e = launch_canon_modp(D, r.p, h->stream);
+    cudaError_t e = launch_canon_modp(P.D, r.p, stream);
     if (e != cudaSuccess) {
       r.cuda_err = e;
       r.fail = std::string("canonical pass: ") + cudaGetErrorString(e);
     }
   }
-  if (!ext && r.ws) cudaFreeAsync(r.ws, h->stream);
-  if (!ext && r.stage) cudaFreeAsync(r.stage, h->stream);
-  std::memset(&h->stats, 0, sizeof(h->stats));
-  h->stats.workspace_bytes = x.ws_peak;
-  h->stats.plan_extra_elems = x.tmp_peak_elems;
-  h->stats.paper_extra_elems = paper;
-  h->stats.add_elems = r.add_elems;
-  h->stats.leaf_flops = r.leaf_flops;
-  h->stats.leaf_launches = r.leaf_launches;
-  h->stats.ew_launches = r.ew_launches;
-  h->stats.leaf_products = r.leaf_products;
-  h->stats.staging_bytes = x.stage_need;
+  if (!ext && r.ws) cudaFreeAsync(r.ws, stream);
+  if (!ext && r.stage) cudaFreeAsync(r.stage, stream);
+  st.workspace_bytes = std::max<int64_t>(st.workspace_bytes, x.ws_peak);
+  st.plan_extra_elems = std::max<int64_t>(st.plan_extra_elems, x.tmp_peak_elems);
+  st.paper_extra_elems = std::max<int64_t>(st.paper_extra_elems, P.paper);
+  st.staging_bytes = std::max<int64_t>(st.staging_bytes, x.stage_need);
+  st.add_elems += r.add_elems;
+  st.leaf_flops += r.leaf_flops;
+  st.leaf_launches += r.leaf_launches;
+  st.ew_launches += r.ew_launches;
+  st.leaf_products += r.leaf_products;
   if (r.cuda_err != cudaSuccess) return fail(h, SWMM_ECUDA, r.fail);
   if (!r.fail.empty()) return fail(h, SWMM_EINVAL, r.fail);
   return SWMM_OK;
+}
+
+// Byte key of a call for the graph cache: everything that is baked into the
+// captured kernels' parameters.
+void key_append(std::string &k, const void *p, size_t n) { k.append((const char *)p, n); }
+void key_plan(std::string &k, const Plan &P) {
+  key_append(k, &P.q.entry, sizeof(P.q.entry));
+  int64_t dims[6] = {P.q.m, P.q.k, P.q.n, P.q.lda, P.q.ldb, P.q.ldc};
+  key_append(k, dims, sizeof(dims));
+  const void *ptrs[3] = {P.q.A, P.q.B, P.q.C};
+  key_append(k, ptrs, sizeof(ptrs));
+  key_append(k, &P.o, sizeof(P.o));
+  key_append(k, &P.alpha, sizeof(P.alpha));
+  key_append(k, &P.beta, sizeof(P.beta));
+  key_append(k, &P.accum, sizeof(P.accum));
+}
+
+// Run a list of plans, directly or through a cached CUDA graph.
+int run_plans(swmm_t h, const std::vector<Plan> &plans, uint32_t flags, const Scratch *ext) {
+  const bool timing = (flags & SWMM_FLAG_TIMING) != 0 && !ext;
+  swmm_stats st;
+  std::memset(&st, 0, sizeof(st));
+  if (!(flags & SWMM_FLAG_GRAPH) || ext) {
+    h->last_timer = &h->timer;
+    for (const Plan &P : plans) {
+      int rc = enqueue(h, P, h->stream, timing ? &h->timer : nullptr, ext, st);
+      if (rc != SWMM_OK) return rc;
+    }
+    h->stats = st;
+    return SWMM_OK;
+  }
+  std::string key;
+  key_append(key, &timing, sizeof(timing));
+  for (const Plan &P : plans) key_plan(key, P);
+  GraphEntry *g = nullptr;
+  for (auto &e : h->graphs)
+    if (e->key == key) g = e.get();
+  if (!g) {
+    if (!h->cap) {
+      if (cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) != cudaSuccess ||
+          cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(h, SWMM_ECUDA, "graph stream creation failed");
+      }
+    }
+    std::unique_ptr<GraphEntry> ne(new GraphEntry());
+    ne->key = key;
+    if (cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(h, SWMM_ECUDA, "stream capture failed to start");
+    }
+    int rc = SWMM_OK;
+    for (const Plan &P : plans) {
+      rc = enqueue(h, P, h->cap, timing ? &ne->timer : nullptr, nullptr, ne->stats);
+      if (rc != SWMM_OK) break;
+    }
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(h->cap, &graph);
+    if (rc != SWMM_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return rc;
+    }
+    if (e != cudaSuccess || cudaGraphInstantiate(&ne->exec, graph, 0) != cudaSuccess) {
+      cudaGetLastError();
+      if (graph) cudaGraphDestroy(graph);
+      return fail(h, SWMM_ECUDA, "graph capture or instantiation failed");
+    }
+    cudaGraphDestroy(graph);
+    if (h->graphs.size() >= 32) h->graphs.erase(h->graphs.begin());
+    g = ne.get();
+    h->graphs.push_back(std::move(ne));
+  }
+  if (cudaEventRecord(h->ev_in, h->stream) != cudaSuccess || cudaStreamWaitEvent(h->cap, h->ev_in, 0) != cudaSuccess ||
+      cudaGraphLaunch(g->exec, h->cap) != cudaSuccess || cudaEventRecord(h->ev_out, h->cap) != cudaSuccess ||
+      cudaStreamWaitEvent(h->stream, h->ev_out, 0) != cudaSuccess) {
+    cudaError_t e = cudaGetLastError();
+    return fail(h, SWMM_ECUDA, std::string("graph launch failed: ") + cudaGetErrorString(e));
+  }
+  h->stats = g->stats;
+  h->last_timer = &g->timer;
+  return SWMM_OK;
+}
+
+int run(swmm_t h, const Req &q, const swmm_opts *o, const Scratch *ext = nullptr) {
+  if (!h) return SWMM_EINVAL;
+  h->last_error.clear();
+  std::vector<Plan> plans(1);
+  int rc = make_plan(h, q, o, true, plans[0]);
+  if (rc != SWMM_OK) return rc;
+  return run_plans(h, plans, o->flags, ext);
+}
+
+// ---------------------------------------------------------------- autotuner
+// Cost model of a planned call on one GB300 (microseconds): tensor work at a
+// rate that falls with small leaf products, HBM-bound passes, and a fixed
+// cost per launch.
+double model_us(const Plan &P) {
+  const Exec &x = P.x;
+  const double limbs = x.mode == MODE_MODP1 ? 1.0 : (x.mode == MODE_MODP2 ? 4.0 : 3.0);
+  const double flops = (double)x.leaf_flops * limbs;
+  const double per_product = x.leaf_products ? (double)x.leaf_flops / (double)x.leaf_products : 0.0;
+  const double tiles = per_product / (2.0 * 128.0 * 128.0 * 1024.0);  // 128 x 128 x 1024 tile units
+  const double eff = 0.95 * tiles / (tiles + 6.0) + 0.05;
+  const double rate = 1.75e9 * eff;  // flop/us at the sustained tensor peak
+  const double bytes = (double)x.add_elems * 12.0 + (double)x.stage_need * 3.0;
+  const double launches = (double)(x.leaf_launches + x.ew_launches);
+  return flops / rate + bytes / 5.5e6 + launches * 2.5;
 }
 
 }  // namespace
@@ -346,7 +495,7 @@ int muladd_with_scratch(swmm_t h, int64_t m, int64_t k, int64_t n, const void *a
   if (!alpha || !beta) return fail(h, SWMM_EINVAL, "alpha and beta are required");
   Req q{1, m, k, n, A, B, C, lda, ldb, ldc, alpha, beta};
   Scratch s{(char *)scratch, scratch_bytes};
-  return run(h, q, opts, false, nullptr, nullptr, &s);
+  return run(h, q, opts, &s);
 }
 }  // namespace swmm
 
@@ -392,26 +541,27 @@ int swmm_set_stream(swmm_t h, void *stream) {
 int swmm_mul(swmm_t h, int64_t m, int64_t k, int64_t n, const void *A, int64_t lda, const void *B, int64_t ldb,
              void *C, int64_t ldc, const swmm_opts *opts) {
   Req q{0, m, k, n, A, B, C, lda, ldb, ldc, nullptr, nullptr};
-  return run(h, q, opts, false, nullptr, nullptr);
+  return run(h, q, opts);
 }
 
 int swmm_muladd(swmm_t h, int64_t m, int64_t k, int64_t n, const void *alpha, const void *A, int64_t lda,
                 const void *B, int64_t ldb, const void *beta, void *C, int64_t ldc, const swmm_opts *opts) {
   if (!alpha || !beta) return fail(h, SWMM_EINVAL, "alpha and beta are required");
   Req q{1, m, k, n, A, B, C, lda, ldb, ldc, alpha, beta};
-  return run(h, q, opts, false, nullptr, nullptr);
+  return run(h, q, opts);
 }
 
 int swmm_mul_inplace(swmm_t h, int64_t m, int64_t k, int64_t n, void *A, int64_t lda, void *B, int64_t ldb, void *C,
                      int64_t ldc, const void *alpha, const void *beta, const swmm_opts *opts) {
   Req q{2, m, k, n, A, B, C, lda, ldb, ldc, alpha, beta};
-  return run(h, q, opts, false, nullptr, nullptr);
+  return run(h, q, opts);
 }
 
-int swmm_workspace_elems(swmm_t h, int64_t m, int64_t k, int64_t n, const swmm_opts *opts, int64_t *paper_elems,
-                         int64_t *plan_elems) {
+int swmm_workspace_elems(swmm_t h, int64_t m, int64_t k, int64_t n, const swmm_opts *opts, int64_t *paper_out,
+                         int64_t *plan_out) {
   swmm_ctx planner;  // planning needs no device: a NULL handle is accepted
   if (!h) h = &planner;
+  h->last_error.clear();
   if (!opts) return fail(h, SWMM_EINVAL, "opts is NULL");
   const int s = opts->sched;
   const bool acc_inplace = s == SWMM_T6_ACLR || s == SWMM_T7_ACCR || s == SWMM_T8_ACR;
@@ -420,25 +570,104 @@ int swmm_workspace_elems(swmm_t h, int64_t m, int64_t k, int64_t n, const swmm_o
   if (s == SWMM_T3_IP || s == SWMM_T4_OVL || s == SWMM_T4M_OVL || s == SWMM_T5_OVR || acc_inplace) entry = 2;
   static const uint32_t one = 1;
   Req q{entry, m, k, n, nullptr, nullptr, nullptr, k, n, n, &one, acc_inplace || entry == 1 ? &one : nullptr};
-  return run(h, q, opts, true, paper_elems, plan_elems);
+  Plan P;
+  int rc = make_plan(h, q, opts, false, P);
+  if (rc != SWMM_OK) return rc;
+  if (paper_out) *paper_out = P.paper;
+  if (plan_out) *plan_out = P.x.tmp_peak_elems;
+  return SWMM_OK;
+}
+
+int swmm_autotune(swmm_t h, int64_t m, int64_t k, int64_t n, int32_t mode, uint32_t p, int32_t *sched,
+                  int32_t *depth, double *est_us, int64_t *extra_elems) {
+  swmm_ctx planner;
+  if (!h) h = &planner;
+  h->last_error.clear();
+  static const uint32_t one = 1;
+  static const float onef = 1.f;
+  const void *sc = mode == SWMM_FP32 ? (const void *)&onef : (const void *)&one;
+  double best = 1e300;
+  int bs = SWMM_CLASSICAL, bd = 0;
+  int64_t be = 0;
+  const int cands[3] = {SWMM_CLASSICAL, SWMM_T2_HLJJTT, SWMM_T9_ACC};
+  for (int c : cands) {
+    for (int d = (c == SWMM_CLASSICAL ? 0 : 1); d <= (c == SWMM_CLASSICAL ? 0 : 3); ++d) {
+      if (c == SWMM_T9_ACC && !(m == k && k == n)) continue;
+      swmm_opts o;
+      std::memset(&o, 0, sizeof(o));
+      o.mode = mode;
+      o.p = p;
+      o.sched = c;
+      o.depth = d;
+      Req q{1, m, k, n, nullptr, nullptr, nullptr, std::max<int64_t>(k, 1), std::max<int64_t>(n, 1),
+            std::max<int64_t>(n, 1), sc, sc};
+      Plan P;
+      if (make_plan(h, q, &o, false, P) != SWMM_OK) continue;
+      const double t = model_us(P);
+      if (t < best) {
+        best = t;
+        bs = c;
+        bd = d;
+        be = P.x.tmp_peak_elems;
+      }
+    }
+  }
+  if (best >= 1e300) return fail(h, SWMM_EINVAL, "no valid plan");
+  if (sched) *sched = bs;
+  if (depth) *depth = bd;
+  if (est_us) *est_us = best;
+  if (extra_elems) *extra_elems = be;
+  h->last_error.clear();
+  return SWMM_OK;
+}
+
+int swmm_muladd_batched(swmm_t h, int count, swmm_problem *probs, uint32_t flags) {
+  if (!h) return SWMM_EINVAL;
+  h->last_error.clear();
+  if (count < 0 || (count > 0 && !probs)) return fail(h, SWMM_EINVAL, "bad problem list");
+  std::vector<Plan> plans(count);
+  for (int i = 0; i < count; ++i) {
+    swmm_problem &pb = probs[i];
+    int32_t s = pb.sched, d = pb.depth;
+    if (s == SWMM_AUTO) {
+      int rc = swmm_autotune(h, pb.m, pb.k, pb.n, pb.mode, pb.p, &s, &d, nullptr, nullptr);
+      if (rc != SWMM_OK) return rc;
+    }
+    pb.chosen_sched = s;
+    pb.chosen_depth = d;
+    swmm_opts o;
+    std::memset(&o, 0, sizeof(o));
+    o.mode = pb.mode;
+    o.p = pb.p;
+    o.sched = s;
+    o.depth = d;
+    o.flags = flags & (SWMM_FLAG_UNFUSED | SWMM_FLAG_SIMT_LEAF);
+    const void *al = pb.mode == SWMM_FP32 ? (const void *)&pb.alpha_f : (const void *)&pb.alpha_u;
+    const void *be = pb.mode == SWMM_FP32 ? (const void *)&pb.beta_f : (const void *)&pb.beta_u;
+    Req q{1, pb.m, pb.k, pb.n, pb.A, pb.B, pb.C, pb.lda, pb.ldb, pb.ldc, al, be};
+    int rc = make_plan(h, q, &o, true, plans[i]);
+    if (rc != SWMM_OK) return fail(h, rc, "problem " + std::to_string(i) + ": " + h->last_error);
+  }
+  return run_plans(h, plans, flags, nullptr);
 }
 
 int swmm_leaf_timing(swmm_t h, int reset, double *gemm_ms, int64_t *launches, double *tensor_flops) {
   if (!h) return SWMM_EINVAL;
   cudaError_t e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) return fail(h, SWMM_ECUDA, cudaGetErrorString(e));
+  EventTimer &t = *h->last_timer;
   double ms = 0.0, fl = 0.0;
-  for (size_t i = 0; i < h->timer.used; ++i) {
-    float t = 0.f;
-    if (cudaEventElapsedTime(&t, h->timer.ev[2 * i], h->timer.ev[2 * i + 1]) != cudaSuccess)
+  for (size_t i = 0; i < t.used; ++i) {
+    float v = 0.f;
+    if (cudaEventElapsedTime(&v, t.ev[2 * i], t.ev[2 * i + 1]) != cudaSuccess)
       return fail(h, SWMM_ECUDA, "event timing failed");
-    ms += t;
-    fl += h->timer.flops[i];
+    ms += v;
+    fl += t.flops[i];
   }
   if (gemm_ms) *gemm_ms = ms;
-  if (launches) *launches = (int64_t)h->timer.used;
+  if (launches) *launches = (int64_t)t.used;
   if (tensor_flops) *tensor_flops = fl;
-  if (reset) h->timer.used = 0;
+  if (reset && h->last_timer == &h->timer) h->timer.used = 0;
   return SWMM_OK;
 }
 

@@ -358,9 +358,12 @@ void Exec::fused_level(Scalar alpha, bool acc, Scalar beta, View L, View R, View
 void Exec::call(Kind k, Scalar alpha, bool acc, Scalar beta, View L, View R, View D, int depth, const Arena &ar) {
   if (!ok()) return;
   const int64_t m = L.rows, kk = L.cols, n = R.cols;
-  const bool split = depth > 0 && m >= 2 && kk >= 2 && n >= 2 && m % 2 == 0 && kk % 2 == 0 && n % 2 == 0;
-  if (!split) {
+  if (depth <= 0 || m < 2 || kk < 2 || n < 2) {
     leaf(alpha, acc, beta, L, R, D);
+    return;
+  }
+  if (m % 2 || kk % 2 || n % 2) {
+    peel(k, alpha, acc, beta, L, R, D, depth, ar);
     return;
   }
   if (fused && depth == 1) {
@@ -368,6 +371,24 @@ void Exec::call(Kind k, Scalar alpha, bool acc, Scalar beta, View L, View R, Vie
     return;
   }
   table(k, alpha, acc, beta, L, R, D, depth, ar);
+}
+
+// Dynamic peeling of odd dimensions (the paper leaves "peeling or padding"
+// open, Sections 7.1 and 8): with m' = m - m%2, k' = k - k%2, n' = n - n%2,
+//   C[m', :]    <- alpha A[m', :] B            (+ beta C[m', :])   last row
+//   C[:m', n']  <- alpha A[:m', :] B[:, n']    (+ beta C[:m', n'])  last column
+//   C[:m', :n'] <- the schedule on the even core A[:m', :k'] B[:k', :n']
+//   C[:m', :n'] += alpha A[:m', k'] B[k', :n']                   rank-1 for odd k
+// The row and column products run first because an overwriting schedule
+// may destroy the core of A and B; the rank-1 term only reads the peeled
+// column of A and row of B, which no schedule on the core touches.
+void Exec::peel(Kind k, Scalar alpha, bool acc, Scalar beta, View L, View R, View D, int depth, const Arena &ar) {
+  const int64_t m = L.rows, kk = L.cols, n = R.cols;
+  const int64_t m2 = m - m % 2, k2 = kk - kk % 2, n2 = n - n % 2;
+  if (m2 < m) leaf(alpha, acc, beta, L.sub(m2, 0, 1, kk), R, D.sub(m2, 0, 1, n));
+  if (n2 < n) leaf(alpha, acc, beta, L.sub(0, 0, m2, kk), R.sub(0, n2, kk, 1), D.sub(0, n2, m2, 1));
+  call(k, alpha, acc, beta, L.sub(0, 0, m2, k2), R.sub(0, 0, k2, n2), D.sub(0, 0, m2, n2), depth, ar);
+  if (k2 < kk) leaf(alpha, true, one(), L.sub(0, k2, m2, 1), R.sub(k2, 0, 1, n2), D.sub(0, 0, m2, n2));
 }
 
 void Exec::table(Kind k, Scalar alpha, bool acc, Scalar beta, View L, View R, View D, int depth,

@@ -68,6 +68,7 @@ struct Exec {
 
  private:
   void fused_level(Scalar alpha, bool acc, Scalar beta, View L, View R, View D);
+  void peel(Kind k, Scalar alpha, bool acc, Scalar beta, View L, View R, View D, int depth, const Arena &ar);
   void table(Kind k, Scalar alpha, bool acc, Scalar beta, View L, View R, View D, int depth, const Arena &ar);
   void add(View d, View s1, View s2, Scalar c1, Scalar c2);
   void scale(View d, bool keep, Scalar beta);  // d <- beta d, or 0

@@ -21,11 +21,12 @@ MODP, FP32 = 0, 1
 # schedules (paper table numbers)
 CLASSICAL, T1_DHSS, T2_HLJJTT, T3_IP, T4_OVL, T5_OVR = 0, 1, 2, 3, 4, 5
 T6_ACLR, T7_ACCR, T8_ACR, T9_ACC, IPMM, T4M_OVL = 6, 7, 8, 9, 10, 11
+AUTO = -1
 SCHED_NAMES = {CLASSICAL: "classical", T1_DHSS: "T1", T2_HLJJTT: "T2", T3_IP: "IP", T4_OVL: "OvL",
                T5_OVR: "OvR", T6_ACLR: "AcLR", T7_ACCR: "AccR", T8_ACR: "AcR", T9_ACC: "Acc",
                IPMM: "IPMM", T4M_OVL: "OvLM"}
 # flags
-FLAG_UNFUSED, FLAG_SIMT_LEAF, FLAG_TIMING = 1, 2, 4
+FLAG_UNFUSED, FLAG_SIMT_LEAF, FLAG_TIMING, FLAG_GRAPH = 1, 2, 4, 8
 
 
 class SwmmError(RuntimeError):
@@ -48,11 +49,20 @@ class _Stats(ctypes.Structure):
                 ("staging_bytes", ctypes.c_int64), ("reserved", ctypes.c_int64 * 7)]
 
 
+class Problem(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int64), ("k", ctypes.c_int64), ("n", ctypes.c_int64),
+                ("A", ctypes.c_void_p), ("lda", ctypes.c_int64), ("B", ctypes.c_void_p), ("ldb", ctypes.c_int64),
+                ("C", ctypes.c_void_p), ("ldc", ctypes.c_int64), ("mode", ctypes.c_int32), ("p", ctypes.c_uint32),
+                ("alpha_u", ctypes.c_uint32), ("beta_u", ctypes.c_uint32), ("alpha_f", ctypes.c_float),
+                ("beta_f", ctypes.c_float), ("sched", ctypes.c_int32), ("depth", ctypes.c_int32),
+                ("chosen_sched", ctypes.c_int32), ("chosen_depth", ctypes.c_int32)]
+
+
 # every symbol include/swmm.h declares
 EXPORTS = ["swmm_create", "swmm_destroy", "swmm_set_stream", "swmm_mul", "swmm_muladd", "swmm_muladd_noalloc",
            "swmm_mul_inplace",
-           "swmm_workspace_elems", "swmm_leaf_timing", "swmm_get_stats", "swmm_sync", "swmm_strerror",
-           "swmm_last_error"]
+           "swmm_muladd_batched", "swmm_autotune", "swmm_workspace_elems", "swmm_leaf_timing", "swmm_get_stats",
+           "swmm_sync", "swmm_strerror", "swmm_last_error"]
 
 _lib = None
 
@@ -79,6 +89,10 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.swmm_workspace_elems.argtypes = [vp, i64, i64, i64, ctypes.POINTER(_Opts), ctypes.POINTER(i64),
                                          ctypes.POINTER(i64)]
     lib.swmm_get_stats.argtypes = [vp, ctypes.POINTER(_Stats)]
+    lib.swmm_muladd_batched.argtypes = [vp, ctypes.c_int, ctypes.POINTER(Problem), ctypes.c_uint32]
+    lib.swmm_autotune.argtypes = [vp, i64, i64, i64, ctypes.c_int32, ctypes.c_uint32, ctypes.POINTER(ctypes.c_int32),
+                                  ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double),
+                                  ctypes.POINTER(i64)]
     lib.swmm_leaf_timing.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64),
                                      ctypes.POINTER(ctypes.c_double)]
     lib.swmm_sync.argtypes = [vp]
@@ -106,6 +120,18 @@ class Opts:
 
     def c(self) -> _Opts:
         return _Opts(self.mode, self.p, self.sched, self.depth, self.flags, self.ipmm_cutoff, self.ipmm_acc, 0)
+
+
+def autotune(m, k, n, mode=MODP, p=65521):
+    """(sched, depth, modelled microseconds, peak temporary elements) the
+    library's autotuner picks; no GPU needed."""
+    lib = load()
+    s, d = ctypes.c_int32(), ctypes.c_int32()
+    t, e = ctypes.c_double(), ctypes.c_int64()
+    rc = lib.swmm_autotune(None, m, k, n, mode, p, ctypes.byref(s), ctypes.byref(d), ctypes.byref(t), ctypes.byref(e))
+    if rc != OK:
+        raise SwmmError(rc, "autotune failed")
+    return s.value, d.value, t.value, e.value
 
 
 def _scalar(mode, v):
@@ -205,6 +231,26 @@ class Handle:
         self._check(self.lib.swmm_mul_inplace(self.h, m, k, n, a, lda, b, ldb, c, ldc, _scalar(opts.mode, alpha),
                                               _scalar(opts.mode, beta), ctypes.byref(opts.c())))
         return C
+
+    def muladd_batched(self, problems, flags: int = 0):
+        """problems: list of dicts with A, B, C (torch tensors), mode, p,
+        alpha, beta, sched (AUTO default), depth.  Returns the (sched, depth)
+        each problem ran with."""
+        self._stream()
+        arr = (Problem * len(problems))()
+        for i, q in enumerate(problems):
+            a, lda = _mat(q["A"], "A")
+            b, ldb = _mat(q["B"], "B")
+            c, ldc = _mat(q["C"], "C")
+            mode = q.get("mode", MODP)
+            arr[i] = Problem(q["A"].shape[0], q["A"].shape[1], q["B"].shape[1], a, lda, b, ldb, c, ldc, mode,
+                             q.get("p", 65521), int(q.get("alpha", 1)) if mode == MODP else 0,
+                             int(q.get("beta", 1)) if mode == MODP else 0,
+                             float(q.get("alpha", 1.0)) if mode == FP32 else 0.0,
+                             float(q.get("beta", 1.0)) if mode == FP32 else 0.0,
+                             q.get("sched", AUTO), q.get("depth", 0), 0, 0)
+        self._check(self.lib.swmm_muladd_batched(self.h, len(problems), arr, flags))
+        return [(arr[i].chosen_sched, arr[i].chosen_depth) for i in range(len(problems))]
 
     def workspace_elems(self, m, k, n, opts: Opts):
         paper = ctypes.c_int64()

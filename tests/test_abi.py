@@ -88,3 +88,20 @@ def test_planner_rejects_bad_arguments(S):
     assert plan(S, 64, 64, 32, sched=10, depth=1)[0] == S.EINVAL  # IPMM needs m = n
     assert plan(S, 64, 64, 64, sched=3, depth=1, mode=7)[0] == S.EINVAL
     assert plan(S, 128, 64, 32, sched=3, depth=1)[0] == S.EINVAL  # IP needs k = n <= m
+
+
+def test_autotune_choices(S):
+    for shape in [(384, 384, 384), (1001, 2000, 777), (8192, 8192, 8192), (16384, 16384, 16384)]:
+        s, d, t, e = S.autotune(*shape)
+        assert s in (S.CLASSICAL, S.T2_HLJJTT, S.T9_ACC)
+        assert 0 <= d <= 3 and t > 0 and e >= 0
+        if s == S.CLASSICAL:
+            assert d == 0 and e == 0
+    # small problems stay classical: the additions cannot pay off
+    assert S.autotune(384, 384, 384)[0] == S.CLASSICAL
+
+
+def test_planner_peeling_odd_sizes(S):
+    # odd dimensions are peeled: the recursion continues on the even core
+    rc, paper, planned = plan(S, 1001, 1001, 1001, sched=9, depth=3, flags=S.FLAG_UNFUSED)
+    assert rc == 0 and planned == paper == 2 * (500 ** 2 + 250 ** 2 + 125 ** 2)
