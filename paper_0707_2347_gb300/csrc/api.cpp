@@ -48,7 +48,10 @@ bool make_tmap(CUtensorMap *map, const void *base, int64_t rows, int64_t kpad, i
 
 bool make_target_tmap(CUtensorMap *map, const void *base, int64_t rows, int64_t cols, int64_t ld, bool fp32) {
   EncodeTiledFn fn = encode_fn();
-  if (!fn || ((uintptr_t)base % 16) != 0 || (ld % 4) != 0 || rows <= 0 || cols <= 0) return false;
+  // TMA stores write whole 16-byte chunks at the inner boundary: a width that
+  // is not a multiple of 4 words would clobber the neighbouring columns, so
+  // such targets take the epilogue's direct path.
+  if (!fn || ((uintptr_t)base % 16) != 0 || (ld % 4) != 0 || rows <= 0 || cols <= 0 || (cols % 4) != 0) return false;
   cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
   cuuint64_t strides[1] = {(cuuint64_t)ld * 4};
   cuuint32_t box[2] = {32, (cuuint32_t)kBM};

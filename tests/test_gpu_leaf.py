@@ -78,3 +78,20 @@ def test_empty_inner_dimension(handle):
                   S.Opts(mode=S.MODP, p=p, sched=S.CLASSICAL, depth=0))
     handle.sync()
     assert np.array_equal(host(dC), (2 * C) % p)
+
+
+@pytest.mark.parametrize("cols", [194, 97, 1, 388])
+def test_store_leaves_neighbouring_columns_alone(handle, cols):
+    """A target narrower than its leading dimension must not be written
+    outside its columns (TMA stores work in 16-byte chunks)."""
+    p = 65521
+    m, k, ld = 249, 138, 400
+    A = synth.modp_matrix(1, m, k, p)
+    B = synth.modp_matrix(2, k, cols, p)
+    C = synth.modp_matrix(3, m, ld, p)
+    dC = dev(C)
+    handle.mul(dev(A), dev(B), dC[:, :cols], S.Opts(mode=S.MODP, p=p, sched=S.CLASSICAL, depth=0))
+    handle.sync()
+    out = host(dC)
+    assert np.array_equal(out[:, :cols], classical.mul_modp(A, B, p))
+    assert np.array_equal(out[:, cols:], C[:, cols:])
