@@ -78,10 +78,12 @@ struct EventTimer : TimingHook {
       ev.push_back(b);
       flops.push_back(0.0);
     }
-    cudaEventRecord(ev[2 * used], s);
+    // external record: inside a stream capture it becomes an event node of
+    // the graph, so each replay refreshes the timestamps
+    cudaEventRecordWithFlags(ev[2 * used], s, cudaEventRecordExternal);
   }
   void end(cudaStream_t s, double f) override {
-    cudaEventRecord(ev[2 * used + 1], s);
+    cudaEventRecordWithFlags(ev[2 * used + 1], s, cudaEventRecordExternal);
     flops[used] = f;
     ++used;
   }
