@@ -78,12 +78,20 @@ struct EventTimer : TimingHook {
       ev.push_back(b);
       flops.push_back(0.0);
     }
-    // external record: inside a stream capture it becomes an event node of
-    // the graph, so each replay refreshes the timestamps
-    cudaEventRecordWithFlags(ev[2 * used], s, cudaEventRecordExternal);
+    record(ev[2 * used], s);
+  }
+  // Inside a stream capture an external record becomes an event node of the
+  // graph, so each replay refreshes the timestamps; outside, a plain record.
+  static void record(cudaEvent_t e, cudaStream_t s) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(s, &cs);
+    if (cs == cudaStreamCaptureStatusActive)
+      cudaEventRecordWithFlags(e, s, cudaEventRecordExternal);
+    else
+      cudaEventRecord(e, s);
   }
   void end(cudaStream_t s, double f) override {
-    cudaEventRecordWithFlags(ev[2 * used + 1], s, cudaEventRecordExternal);
+    record(ev[2 * used + 1], s);
     flops[used] = f;
     ++used;
   }
