@@ -237,7 +237,7 @@ def main():
     def call(opts, Cdev, Adev=dA, Bdev=dB):
         if w["entry"] == "muladd":
             h.muladd(1, Adev, Bdev, 1, Cdev, opts)
-        elif w["entry"] == "mul":
+        elif w["entry"] == "mul" or opts.sched == CLASSICAL:
             h.mul(Adev, Bdev, Cdev, opts)
         else:
             h.mul_inplace(Adev, Bdev, Cdev, opts)
