@@ -3,7 +3,10 @@
 #include "swmm.h"
 
 #include <algorithm>
+#include <array>
+#include <cstddef>
 #include <cstdio>
+#include <tuple>
 #include <cstring>
 #include <memory>
 #include <string>
@@ -107,6 +110,7 @@ struct GraphEntry {
   cudaGraphExec_t exec = nullptr;
   swmm_stats stats;
   EventTimer timer;
+  std::vector<int32_t> chosen;  // batched calls: (sched, depth) per problem
   GraphEntry() { std::memset(&stats, 0, sizeof(stats)); }
   ~GraphEntry() {
     if (exec) cudaGraphExecDestroy(exec);
@@ -130,6 +134,8 @@ struct swmm_ctx {
   std::vector<std::unique_ptr<GraphEntry>> graphs;
   cudaStream_t cap = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  // autotuner decisions: (m, k, n, mode, p) -> (sched, depth, est_us, elems)
+  std::vector<std::pair<std::array<int64_t, 5>, std::tuple<int32_t, int32_t, double, int64_t>>> tuned;
   ~swmm_ctx() {
     graphs.clear();
     if (cap) cudaStreamDestroy(cap);
@@ -389,23 +395,30 @@ int enqueue(swmm_t h, const Plan &P, cudaStream_t stream, TimingHook *timing, co
   return SWMM_OK;
 }
 
-// Byte key of a call for the graph cache: everything that is baked into the
-// captured kernels' parameters.
 void key_append(std::string &k, const void *p, size_t n) { k.append((const char *)p, n); }
-void key_plan(std::string &k, const Plan &P) {
-  key_append(k, &P.q.entry, sizeof(P.q.entry));
-  int64_t dims[6] = {P.q.m, P.q.k, P.q.n, P.q.lda, P.q.ldb, P.q.ldc};
-  key_append(k, dims, sizeof(dims));
-  const void *ptrs[3] = {P.q.A, P.q.B, P.q.C};
-  key_append(k, ptrs, sizeof(ptrs));
-  key_append(k, &P.o, sizeof(P.o));
-  key_append(k, &P.alpha, sizeof(P.alpha));
-  key_append(k, &P.beta, sizeof(P.beta));
-  key_append(k, &P.accum, sizeof(P.accum));
+
+GraphEntry *find_graph(swmm_t h, const std::string &key) {
+  for (auto &e : h->graphs)
+    if (e->key == key) return e.get();
+  return nullptr;
 }
 
-// Run a list of plans, directly or through a cached CUDA graph.
-int run_plans(swmm_t h, const std::vector<Plan> &plans, uint32_t flags, const Scratch *ext) {
+int launch_graph(swmm_t h, GraphEntry *g) {
+  if (cudaEventRecord(h->ev_in, h->stream) != cudaSuccess || cudaStreamWaitEvent(h->cap, h->ev_in, 0) != cudaSuccess ||
+      cudaGraphLaunch(g->exec, h->cap) != cudaSuccess || cudaEventRecord(h->ev_out, h->cap) != cudaSuccess ||
+      cudaStreamWaitEvent(h->stream, h->ev_out, 0) != cudaSuccess) {
+    cudaError_t e = cudaGetLastError();
+    return fail(h, SWMM_ECUDA, std::string("graph launch failed: ") + cudaGetErrorString(e));
+  }
+  h->stats = g->stats;
+  h->last_timer = &g->timer;
+  return SWMM_OK;
+}
+
+// Run a list of plans, directly or through a cached CUDA graph under `key`
+// (callers look the key up before planning, so a replay skips planning).
+int run_plans(swmm_t h, const std::vector<Plan> &plans, uint32_t flags, const Scratch *ext,
+              const std::string &key = std::string(), GraphEntry **entry = nullptr) {
   const bool timing = (flags & SWMM_FLAG_TIMING) != 0 && !ext;
   swmm_stats st;
   std::memset(&st, 0, sizeof(st));
@@ -418,12 +431,7 @@ int run_plans(swmm_t h, const std::vector<Plan> &plans, uint32_t flags, const Sc
     h->stats = st;
     return SWMM_OK;
   }
-  std::string key;
-  key_append(key, &timing, sizeof(timing));
-  for (const Plan &P : plans) key_plan(key, P);
-  GraphEntry *g = nullptr;
-  for (auto &e : h->graphs)
-    if (e->key == key) g = e.get();
+  GraphEntry *g = find_graph(h, key);
   if (!g) {
     if (!h->cap) {
       if (cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) != cudaSuccess ||
@@ -460,24 +468,40 @@ int run_plans(swmm_t h, const std::vector<Plan> &plans, uint32_t flags, const Sc
     g = ne.get();
     h->graphs.push_back(std::move(ne));
   }
-  if (cudaEventRecord(h->ev_in, h->stream) != cudaSuccess || cudaStreamWaitEvent(h->cap, h->ev_in, 0) != cudaSuccess ||
-      cudaGraphLaunch(g->exec, h->cap) != cudaSuccess || cudaEventRecord(h->ev_out, h->cap) != cudaSuccess ||
-      cudaStreamWaitEvent(h->stream, h->ev_out, 0) != cudaSuccess) {
-    cudaError_t e = cudaGetLastError();
-    return fail(h, SWMM_ECUDA, std::string("graph launch failed: ") + cudaGetErrorString(e));
-  }
-  h->stats = g->stats;
-  h->last_timer = &g->timer;
-  return SWMM_OK;
+  if (entry) *entry = g;
+  return launch_graph(h, g);
+}
+
+// Graph-cache key of a call from its raw arguments (everything baked into
+// the captured kernels: sizes, pointers, leading dimensions, options, scalar
+// values).
+std::string call_key(const Req &q, const swmm_opts *o) {
+  std::string k;
+  key_append(k, &q.entry, sizeof(q.entry));
+  int64_t dims[6] = {q.m, q.k, q.n, q.lda, q.ldb, q.ldc};
+  key_append(k, dims, sizeof(dims));
+  const void *ptrs[3] = {q.A, q.B, q.C};
+  key_append(k, ptrs, sizeof(ptrs));
+  key_append(k, o, sizeof(*o));
+  uint32_t sc[3] = {q.alpha ? *(const uint32_t *)q.alpha : 0u, q.beta ? *(const uint32_t *)q.beta : 0u,
+                    (uint32_t)(q.alpha != nullptr) | ((uint32_t)(q.beta != nullptr) << 1)};
+  key_append(k, sc, sizeof(sc));
+  return k;
 }
 
 int run(swmm_t h, const Req &q, const swmm_opts *o, const Scratch *ext = nullptr) {
   if (!h) return SWMM_EINVAL;
   h->last_error.clear();
+  if (!o) return fail(h, SWMM_EINVAL, "opts is NULL");
+  std::string key;
+  if ((o->flags & SWMM_FLAG_GRAPH) && !ext) {
+    key = call_key(q, o);
+    if (GraphEntry *g = find_graph(h, key)) return launch_graph(h, g);
+  }
   std::vector<Plan> plans(1);
   int rc = make_plan(h, q, o, true, plans[0]);
   if (rc != SWMM_OK) return rc;
-  return run_plans(h, plans, o->flags, ext);
+  return run_plans(h, plans, o->flags, ext, key);
 }
 
 // ---------------------------------------------------------------- autotuner
@@ -596,6 +620,16 @@ int swmm_autotune(swmm_t h, int64_t m, int64_t k, int64_t n, int32_t mode, uint3
   swmm_ctx planner;
   if (!h) h = &planner;
   h->last_error.clear();
+  const std::array<int64_t, 5> tk{m, k, n, mode, mode == SWMM_FP32 ? 0 : (int64_t)p};
+  for (auto &e : h->tuned) {
+    if (e.first == tk) {
+      if (sched) *sched = std::get<0>(e.second);
+      if (depth) *depth = std::get<1>(e.second);
+      if (est_us) *est_us = std::get<2>(e.second);
+      if (extra_elems) *extra_elems = std::get<3>(e.second);
+      return SWMM_OK;
+    }
+  }
   static const uint32_t one = 1;
   static const float onef = 1.f;
   const void *sc = mode == SWMM_FP32 ? (const void *)&onef : (const void *)&one;
@@ -626,6 +660,7 @@ int swmm_autotune(swmm_t h, int64_t m, int64_t k, int64_t n, int32_t mode, uint3
     }
   }
   if (best >= 1e300) return fail(h, SWMM_EINVAL, "no valid plan");
+  if (h != &planner && h->tuned.size() < 4096) h->tuned.push_back({tk, std::make_tuple(bs, bd, best, be)});
   if (sched) *sched = bs;
   if (depth) *depth = bd;
   if (est_us) *est_us = best;
@@ -638,6 +673,19 @@ int swmm_muladd_batched(swmm_t h, int count, swmm_problem *probs, uint32_t flags
   if (!h) return SWMM_EINVAL;
   h->last_error.clear();
   if (count < 0 || (count > 0 && !probs)) return fail(h, SWMM_EINVAL, "bad problem list");
+  std::string key;
+  if (flags & SWMM_FLAG_GRAPH) {
+    key.assign("batch");
+    key_append(key, &flags, sizeof(flags));
+    for (int i = 0; i < count; ++i) key_append(key, &probs[i], offsetof(swmm_problem, chosen_sched));
+    if (GraphEntry *g = find_graph(h, key)) {
+      for (int i = 0; i < count && 2 * i + 1 < (int)g->chosen.size(); ++i) {
+        probs[i].chosen_sched = g->chosen[2 * i];
+        probs[i].chosen_depth = g->chosen[2 * i + 1];
+      }
+      return launch_graph(h, g);
+    }
+  }
   std::vector<Plan> plans(count);
   for (int i = 0; i < count; ++i) {
     swmm_problem &pb = probs[i];
@@ -661,7 +709,16 @@ int swmm_muladd_batched(swmm_t h, int count, swmm_problem *probs, uint32_t flags
     int rc = make_plan(h, q, &o, true, plans[i]);
     if (rc != SWMM_OK) return fail(h, rc, "problem " + std::to_string(i) + ": " + h->last_error);
   }
-  return run_plans(h, plans, flags, nullptr);
+  GraphEntry *g = nullptr;
+  int rc = run_plans(h, plans, flags, nullptr, key, &g);
+  if (rc == SWMM_OK && g) {
+    g->chosen.clear();
+    for (int i = 0; i < count; ++i) {
+      g->chosen.push_back(probs[i].chosen_sched);
+      g->chosen.push_back(probs[i].chosen_depth);
+    }
+  }
+  return rc;
 }
 
 int swmm_leaf_timing(swmm_t h, int reset, double *gemm_ms, int64_t *launches, double *tensor_flops) {
