@@ -68,6 +68,11 @@ WORKLOADS = {
 }
 DEFAULT = "t9_8192_p65521"
 
+# DRAM bytes (read + write) per leaf GEMM launch from one ncu capture of the
+# same kernel on a launch of the same shape (7 products of 1024^3);
+# see profiles/gemm_kernel_fused_level_7x1024_p65521.md.
+TRAFFIC = {"t9_8192_p65521": 77.5e6}
+
 
 def peaks():
     try:
@@ -388,7 +393,7 @@ def main():
         "memory": {"workspace_bytes": st["workspace_bytes"], "plan_extra_elems": st["plan_extra_elems"],
                    "paper_extra_elems_same_levels": st["paper_extra_elems"], "staging_bytes": st["staging_bytes"]},
         "roofline": {"bound": "tensor", "achieved": round(achieved, 1), "peak": sustained, "unit": "TFLOP/s",
-                     "frac": round(achieved / sustained, 4), "traffic": None,
+                     "frac": round(achieved / sustained, 4), "traffic": TRAFFIC.get(args.workload),
                      "kernel": "gemm_kernel (leaf products, fp16 limb MMAs counted)",
                      "peak_kind": f"{peak_kind} bf16 sustained", "launches_per_step": st["leaf_launches"],
                      "gemm_ms_per_step": round(gemm_ms / max(gemm_launches, 1) * st["leaf_launches"], 4)},
