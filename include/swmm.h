@@ -227,6 +227,38 @@ int swmm_workspace_elems(swmm_t h, int64_t m, int64_t k, int64_t n,
 int swmm_leaf_timing(swmm_t h, int reset, double *gemm_ms, int64_t *launches,
                      double *tensor_flops);
 
+/* Randomised residual probe of a product (Freivalds' check).  The paper
+ * has no counterpart: it verifies the result of any entry point above
+ * without an O(n^3) reference product.
+ *
+ * swmm_matvec: y = M x for a row-major rows x cols matrix M with leading
+ * dimension ldm.  SWMM_MODP: M holds int32 values (reduced mod p as read),
+ * x and y are uint32 in [0, p), and the sum is exact.  SWMM_FP32: M holds
+ * float, x and y are double, and the sum is formed in FP64.  M, x and y are
+ * DEVICE pointers (y: rows entries); only opts->mode and opts->p are read.
+ * Asynchronous on the handle's stream.
+ *
+ * swmm_residual: r = C x - alpha A (B x) - beta y0, where C is the result of
+ * an earlier C <- alpha A B + beta C_in (or C <- alpha A B with beta = 0) and
+ * y0 = C_in x was formed with swmm_matvec before that call (y0 may be NULL
+ * when beta is 0).  x has n entries, y0 and r have m entries; all are
+ * DEVICE pointers of swmm_matvec's element type.  alpha and beta point to
+ * HOST scalars as for swmm_muladd.  Over Z/pZ a wrong C gives r == 0 with
+ * probability at most 1/p for a uniformly random x.  In SWMM_FP32 mode r is
+ * the FP64 residual of the float result; FP64 is used in this probe only,
+ * never in the products.  Temporaries (k + 2m entries) are taken from and
+ * returned to the stream-ordered pool within the call.
+ * Errors: SWMM_EINVAL for bad sizes, NULL or misaligned pointers (x, y, r,
+ * y0 must be 4-byte aligned mod p, 8-byte aligned in FP32 mode), or a
+ * missing y0 with beta != 0; SWMM_ENOMEM; SWMM_ECUDA. */
+int swmm_matvec(swmm_t h, int64_t rows, int64_t cols, const void *M,
+                int64_t ldm, const void *x, void *y, const swmm_opts *opts);
+int swmm_residual(swmm_t h, int64_t m, int64_t k, int64_t n,
+                  const void *alpha, const void *A, int64_t lda,
+                  const void *B, int64_t ldb, const void *beta,
+                  const void *y0, const void *C, int64_t ldc, const void *x,
+                  void *r, const swmm_opts *opts);
+
 /* Statistics of the last completed call on this handle. */
 int swmm_get_stats(swmm_t h, swmm_stats *out);
 

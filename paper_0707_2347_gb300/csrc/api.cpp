@@ -741,6 +741,76 @@ int swmm_leaf_timing(swmm_t h, int reset, double *gemm_ms, int64_t *launches, do
   return SWMM_OK;
 }
 
+int swmm_matvec(swmm_t h, int64_t rows, int64_t cols, const void *M, int64_t ldm, const void *x, void *y,
+                const swmm_opts *opts) {
+  if (!h) return SWMM_EINVAL;
+  if (!opts) return fail(h, SWMM_EINVAL, "opts is NULL");
+  const bool modp = opts->mode == SWMM_MODP;
+  if (!modp && opts->mode != SWMM_FP32) return fail(h, SWMM_EINVAL, "unknown mode");
+  if (modp && (opts->p <= 2 || opts->p >= 65536)) return fail(h, SWMM_EINVAL, "p must satisfy 2 < p < 65536");
+  if (rows < 0 || cols < 0) return fail(h, SWMM_EINVAL, "negative dimension");
+  if (rows > (1 << 30) || cols > (1 << 30)) return fail(h, SWMM_EINVAL, "dimension too large");
+  if (rows == 0) return SWMM_OK;
+  if (!y || (cols > 0 && (!M || !x))) return fail(h, SWMM_EINVAL, "NULL pointer");
+  if (ldm < cols || ldm < 1) return fail(h, SWMM_EINVAL, "leading dimension smaller than the number of columns");
+  const uintptr_t xa = modp ? 3 : 7;
+  if (((uintptr_t)M & 3) || ((uintptr_t)x & xa) || ((uintptr_t)y & xa))
+    return fail(h, SWMM_EINVAL, "misaligned pointer");
+  cudaError_t e = launch_matvec(M, rows, cols, ldm, x, y, opts->p, modp, h->num_sms, h->stream);
+  if (e != cudaSuccess) return fail(h, SWMM_ECUDA, cudaGetErrorString(e));
+  return SWMM_OK;
+}
+
+int swmm_residual(swmm_t h, int64_t m, int64_t k, int64_t n, const void *alpha, const void *A, int64_t lda,
+                  const void *B, int64_t ldb, const void *beta, const void *y0, const void *C, int64_t ldc,
+                  const void *x, void *r, const swmm_opts *opts) {
+  if (!h) return SWMM_EINVAL;
+  if (!opts) return fail(h, SWMM_EINVAL, "opts is NULL");
+  if (!alpha || !beta) return fail(h, SWMM_EINVAL, "alpha and beta are required");
+  const bool modp = opts->mode == SWMM_MODP;
+  if (!modp && opts->mode != SWMM_FP32) return fail(h, SWMM_EINVAL, "unknown mode");
+  if (modp && (opts->p <= 2 || opts->p >= 65536)) return fail(h, SWMM_EINVAL, "p must satisfy 2 < p < 65536");
+  if (m < 0 || k < 0 || n < 0) return fail(h, SWMM_EINVAL, "negative dimension");
+  if (m == 0) return SWMM_OK;
+  if (!r || !C || (n > 0 && !x) || (k > 0 && (!A || !B))) return fail(h, SWMM_EINVAL, "NULL pointer");
+  uint32_t au = 0, bu = 0;
+  double af = 0.0, bf = 0.0;
+  bool with_beta;
+  if (modp) {
+    au = *static_cast<const uint32_t *>(alpha) % opts->p;
+    bu = *static_cast<const uint32_t *>(beta) % opts->p;
+    with_beta = bu != 0;
+  } else {
+    af = *static_cast<const float *>(alpha);
+    bf = *static_cast<const float *>(beta);
+    with_beta = bf != 0.0;
+  }
+  if (with_beta && !y0) return fail(h, SWMM_EINVAL, "y0 = C_in x is required when beta != 0");
+  const uintptr_t va = modp ? 3 : 7;
+  if (((uintptr_t)r & va) || ((uintptr_t)y0 & va) || ((uintptr_t)x & va))
+    return fail(h, SWMM_EINVAL, "misaligned pointer");
+  const size_t es = modp ? 4 : 8;
+  char *tmp = nullptr;
+  const size_t bytes = (size_t)(k + 2 * m) * es;
+  cudaError_t e = cudaMallocAsync((void **)&tmp, bytes, h->stream);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(h, SWMM_ENOMEM, "probe temporaries");
+  }
+  void *t = tmp, *u = tmp + k * es, *v = tmp + (k + m) * es;
+  int rc = SWMM_OK;
+  // t = B x, u = A t, v = C x, r = v - alpha u - beta y0
+  if (k > 0) rc = swmm_matvec(h, k, n, B, ldb, x, t, opts);
+  if (rc == SWMM_OK) rc = swmm_matvec(h, m, k, A, k > 0 ? lda : 1, t, u, opts);
+  if (rc == SWMM_OK) rc = swmm_matvec(h, m, n, C, n > 0 ? ldc : 1, x, v, opts);
+  if (rc == SWMM_OK) {
+    e = launch_residual(m, v, u, with_beta ? y0 : nullptr, r, au, bu, af, bf, opts->p, modp, h->num_sms, h->stream);
+    if (e != cudaSuccess) rc = fail(h, SWMM_ECUDA, cudaGetErrorString(e));
+  }
+  cudaFreeAsync(tmp, h->stream);
+  return rc;
+}
+
 int swmm_get_stats(swmm_t h, swmm_stats *out) {
   if (!h || !out) return SWMM_EINVAL;
   *out = h->stats;

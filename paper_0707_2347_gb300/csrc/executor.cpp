@@ -292,6 +292,8 @@ void Exec::fused_level(Scalar alpha, bool acc, Scalar beta, View L, View R, View
       }
       pa.nsrc = pb.nsrc = 4;
       pa.nout = pb.nout = 7;
+      pa.set = PACK_WINOGRAD_A;  // the chains of acoef / bcoef, formed once per element
+      pb.set = PACK_WINOGRAD_B;
       for (int i = 0; i < 7; ++i) {
         pa.out[i] = reinterpret_cast<uint16_t *>(stage + i * abytes);
         pb.out[i] = reinterpret_cast<uint16_t *>(stage + 7 * abytes + i * bbytes);

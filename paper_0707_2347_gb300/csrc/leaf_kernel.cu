@@ -96,7 +96,17 @@ __device__ __forceinline__ void convert8(const uint32_t (&x)[8], uint32_t p, uin
   o1 = make_uint4(w1[0], w1[1], w1[2], w1[3]);
 }
 
-// signed combination of up to four source values for output o
+// Bring a raw source value to the representative the combinations use:
+// mod p any 32-bit representative -> [0, p) (Barrett, m = floor(2^32 / p));
+// FP32 unchanged.
+template <int MODE>
+__device__ __forceinline__ uint32_t source_value(uint32_t x, uint32_t p, uint32_t m) {
+  if (MODE == MODE_FP32) return x;
+  uint32_t r = x - __umulhi(x, m) * p;
+  return min(r, r - p);
+}
+
+// signed combination sum_q coef[o][q] * v[q] of reduced source values
 template <int MODE>
 __device__ __forceinline__ uint32_t combine(const PackArgs &a, int o, const uint32_t *v, uint32_t p) {
   if (MODE == MODE_FP32) {
@@ -109,27 +119,108 @@ __device__ __forceinline__ uint32_t combine(const PackArgs &a, int o, const uint
     }
     return __float_as_uint(s);
   } else {
-    // sources hold any representative below 2^31: Barrett-reduce each first
-    const uint32_t m = a.barrett;
     uint32_t s = 0;
 #pragma unroll
     for (int q = 0; q < kMaxSrc; ++q) {
       const int c = a.coef[o][q];
-      if (c != 0) {
-        uint32_t r = v[q] - __umulhi(v[q], m) * p;
-        r = min(r, r - p);
-        s += c > 0 ? r : p - r;
-      }
+      if (c > 0) s += v[q];
+      if (c < 0) s += p - v[q];
     }
     return red4p(s, p);
   }
 }
 
-// ------------------------------------------------------------------ pack
-// plain layout: thread = 8 consecutive columns of one row
+// write output o of one 8-element unit: plane 0 and plane 1
 template <int MODE>
-__global__ void pack_rows_kernel(const __grid_constant__ PackArgs a) {
-  constexpr int PL = MODE == MODE_MODP1 ? 1 : 2;
+__device__ __forceinline__ void emit_unit(const PackArgs &a, int o, const uint32_t (&v)[kMaxSrc][8], uint16_t *dst,
+                                          int64_t plane) {
+  uint32_t x[8];
+#pragma unroll
+  for (int e = 0; e < 8; ++e) {
+    uint32_t w[kMaxSrc];
+#pragma unroll
+    for (int q = 0; q < kMaxSrc; ++q) w[q] = v[q][e];
+    x[e] = combine<MODE>(a, o, w, a.p);
+  }
+  uint4 o0, o1;
+  convert8<MODE>(x, a.p, o0, o1);
+  *reinterpret_cast<uint4 *>(dst) = o0;
+  if (MODE != MODE_MODP1) *reinterpret_cast<uint4 *>(dst + plane) = o1;
+}
+
+// one 8-element unit of already combined values -> plane 0 and plane 1
+template <int MODE>
+__device__ __forceinline__ void emit8(const uint32_t (&x)[8], uint32_t p, uint16_t *dst, int64_t plane) {
+  uint4 o0, o1;
+  convert8<MODE>(x, p, o0, o1);
+  *reinterpret_cast<uint4 *>(dst) = o0;
+  if (MODE != MODE_MODP1) *reinterpret_cast<uint4 *>(dst + plane) = o1;
+}
+
+// x - y of two reduced values (mod p: both in [0, p), result in [0, p))
+template <int MODE>
+__device__ __forceinline__ uint32_t lin_sub(uint32_t x, uint32_t y, uint32_t p) {
+  if (MODE == MODE_FP32) return __float_as_uint(__uint_as_float(x) - __uint_as_float(y));
+  const uint32_t r = x + p - y;
+  return min(r, r - p);
+}
+template <int MODE>
+__device__ __forceinline__ uint32_t lin_add(uint32_t x, uint32_t y, uint32_t p) {
+  if (MODE == MODE_FP32) return __float_as_uint(__uint_as_float(x) + __uint_as_float(y));
+  const uint32_t r = x + y;
+  return min(r, r - p);
+}
+
+// every output of one unit (sources already reduced); v[q] = quadrant q of
+// (X11, X12, X21, X22) for the Winograd sets
+template <int MODE, int SET>
+__device__ __forceinline__ void emit_all(const PackArgs &a, const uint32_t (&v)[kMaxSrc][8], int64_t off,
+                                         int64_t plane) {
+  const uint32_t p = a.p;
+  if (SET == PACK_WINOGRAD_A) {
+    uint32_t s1[8], s2[8], t[8];
+    emit8<MODE>(v[0], p, a.out[0] + off, plane);  // A11
+    emit8<MODE>(v[1], p, a.out[1] + off, plane);  // A12
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      s1[e] = lin_add<MODE>(v[2][e], v[3][e], p);  // S1 = A21 + A22
+      s2[e] = lin_sub<MODE>(s1[e], v[0][e], p);    // S2 = S1 - A11
+      t[e] = lin_sub<MODE>(v[1][e], s2[e], p);     // S4 = A12 - S2
+    }
+    emit8<MODE>(t, p, a.out[2] + off, plane);
+    emit8<MODE>(v[3], p, a.out[3] + off, plane);  // A22
+    emit8<MODE>(s1, p, a.out[4] + off, plane);
+    emit8<MODE>(s2, p, a.out[5] + off, plane);
+#pragma unroll
+    for (int e = 0; e < 8; ++e) t[e] = lin_sub<MODE>(v[0][e], v[2][e], p);  // S3 = A11 - A21
+    emit8<MODE>(t, p, a.out[6] + off, plane);
+  } else if (SET == PACK_WINOGRAD_B) {
+    uint32_t t1[8], t2[8], t[8];
+    emit8<MODE>(v[0], p, a.out[0] + off, plane);  // B11
+    emit8<MODE>(v[2], p, a.out[1] + off, plane);  // B21
+    emit8<MODE>(v[3], p, a.out[2] + off, plane);  // B22
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      t1[e] = lin_sub<MODE>(v[1][e], v[0][e], p);  // T1 = B12 - B11
+      t2[e] = lin_sub<MODE>(v[3][e], t1[e], p);    // T2 = B22 - T1
+      t[e] = lin_sub<MODE>(t2[e], v[2][e], p);     // T4 = T2 - B21
+    }
+    emit8<MODE>(t, p, a.out[3] + off, plane);
+    emit8<MODE>(t1, p, a.out[4] + off, plane);
+    emit8<MODE>(t2, p, a.out[5] + off, plane);
+#pragma unroll
+    for (int e = 0; e < 8; ++e) t[e] = lin_sub<MODE>(v[3][e], v[1][e], p);  // T3 = B22 - B12
+    emit8<MODE>(t, p, a.out[6] + off, plane);
+  } else {
+    for (int o = 0; o < a.nout; ++o) emit_unit<MODE>(a, o, v, a.out[o] + off, plane);
+  }
+}
+
+// ------------------------------------------------------------------ pack
+// plain layout: thread = 8 consecutive columns of one row; every source
+// value is loaded and reduced once, then combined for each output.
+template <int MODE, int SET>
+__global__ void __launch_bounds__(256) pack_rows_kernel(const __grid_constant__ PackArgs a) {
   const int64_t units = (int64_t)a.prow_pad * (a.pcol_pad / 8);
   const int64_t plane = (int64_t)a.prow_pad * a.pcol_pad;
   for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < units; u += (int64_t)gridDim.x * blockDim.x) {
@@ -150,40 +241,27 @@ __global__ void pack_rows_kernel(const __grid_constant__ PackArgs a) {
           for (int e = 0; e < 8; ++e)
             v[q][e] = (r < a.rows && c0 + e < a.cols) ? reinterpret_cast<const uint32_t *>(base)[e] : 0u;
         }
+#pragma unroll
+        for (int e = 0; e < 8; ++e) v[q][e] = source_value<MODE>(v[q][e], a.p, a.barrett);
       } else {
 #pragma unroll
         for (int e = 0; e < 8; ++e) v[q][e] = 0;
       }
     }
-    for (int o = 0; o < a.nout; ++o) {
-      uint32_t x[8];
-#pragma unroll
-      for (int e = 0; e < 8; ++e) {
-        uint32_t w[kMaxSrc];
-#pragma unroll
-        for (int q = 0; q < kMaxSrc; ++q) w[q] = v[q][e];
-        x[e] = combine<MODE>(a, o, w, a.p);
-      }
-      uint4 o0, o1;
-      convert8<MODE>(x, a.p, o0, o1);
-      uint16_t *dst = a.out[o] + (int64_t)r * a.pcol_pad + c0;
-      *reinterpret_cast<uint4 *>(dst) = o0;
-      if (PL == 2) *reinterpret_cast<uint4 *>(dst + plane) = o1;
-    }
+    emit_all<MODE, SET>(a, v, (int64_t)r * a.pcol_pad + c0, plane);
   }
 }
 
 // transposed layout: a CTA stages a 32 (source rows) x 64 (source cols) tile
-// of every source in shared memory, then writes packed rows = source cols.
-template <int MODE>
+// of every source in shared memory (reduced once), then each thread reads
+// its 8 source rows of one source column and writes packed row = column.
+template <int MODE, int SET>
 __global__ void __launch_bounds__(256) pack_cols_kernel(const __grid_constant__ PackArgs a) {
-  constexpr int PL = MODE == MODE_MODP1 ? 1 : 2;
   __shared__ uint32_t tile[kMaxSrc][32][65];
   const int r0 = blockIdx.y * 32;  // source rows = packed columns (K)
   const int c0 = blockIdx.x * 64;  // source cols = packed rows (N)
   const int t = threadIdx.x;
   const int64_t plane = (int64_t)a.prow_pad * a.pcol_pad;
-  // load: 32 rows x 64 cols = 512 vectors of 4; 2 per thread
   for (int q = 0; q < a.nsrc; ++q) {
 #pragma unroll
     for (int i = 0; i < 2; ++i) {
@@ -201,29 +279,18 @@ __global__ void __launch_bounds__(256) pack_cols_kernel(const __grid_constant__ 
           w[e] = (gr < a.rows && gc + e < a.cols) ? reinterpret_cast<const uint32_t *>(base)[e] : 0u;
       }
 #pragma unroll
-      for (int e = 0; e < 4; ++e) tile[q][rr][cc + e] = w[e];
+      for (int e = 0; e < 4; ++e) tile[q][rr][cc + e] = source_value<MODE>(w[e], a.p, a.barrett);
     }
   }
-  for (int q = a.nsrc; q < kMaxSrc; ++q)
-    for (int i = t; i < 32 * 64; i += 256) tile[q][i >> 6][i & 63] = 0;
   __syncthreads();
-  // write: packed row c0 + (t >> 2), packed columns r0 + 8 * (t & 3) .. + 8
   const int pc = t >> 2, pr8 = (t & 3) * 8;
-  for (int o = 0; o < a.nout; ++o) {
-    uint32_t x[8];
+  uint32_t v[kMaxSrc][8];
 #pragma unroll
-    for (int e = 0; e < 8; ++e) {
-      uint32_t w[kMaxSrc];
+  for (int q = 0; q < kMaxSrc; ++q) {
 #pragma unroll
-      for (int q = 0; q < kMaxSrc; ++q) w[q] = tile[q][pr8 + e][pc];
-      x[e] = combine<MODE>(a, o, w, a.p);
-    }
-    uint4 o0, o1;
-    convert8<MODE>(x, a.p, o0, o1);
-    uint16_t *dst = a.out[o] + (int64_t)(c0 + pc) * a.pcol_pad + r0 + pr8;
-    *reinterpret_cast<uint4 *>(dst) = o0;
-    if (PL == 2) *reinterpret_cast<uint4 *>(dst + plane) = o1;
+    for (int e = 0; e < 8; ++e) v[q][e] = q < a.nsrc ? tile[q][pr8 + e][pc] : 0u;
   }
+  emit_all<MODE, SET>(a, v, (int64_t)(c0 + pc) * a.pcol_pad + r0 + pr8, plane);
 }
 
 // ------------------------------------------------------------ GEMM glue
@@ -340,20 +407,26 @@ __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.comm
 __device__ __forceinline__ void bulk_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
 __device__ __forceinline__ void bulk_wait0() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float *v) {
-  uint32_t r[8];
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
-               : "r"(taddr));
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
 #pragma unroll
-  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
-__device__ __forceinline__ void tmem_st8(uint32_t taddr, const float *v) {
-  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr),
-               "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
-               "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
-               "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7]))
-               : "memory");
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const float *v) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
+          taddr),
+      "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])), "r"(__float_as_uint(v[3])),
+      "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])), "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])),
+      "r"(__float_as_uint(v[8])), "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])),
+      "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])),
+      "r"(__float_as_uint(v[15]))
+      : "memory");
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
@@ -431,39 +504,39 @@ struct Epi {
   }
 };
 
-// Values of 8 consecutive columns of one row before any beta term: mod p
+// Values of 16 consecutive columns of one row before any beta term: mod p
 // results (alpha applied; REDUCE: the signed contribution p - v for a
 // negative target) or floats (FP32: alpha applied, sign folded for REDUCE).
 template <int MODE>
 __device__ __forceinline__ void tile_values(const GemmParams &P, const Epi &E, uint32_t d, int col, int sign,
                                             uint32_t *v) {
   if (MODE == MODE_MODP2) {
-    float hh[8], hl[8], lh[8], ll[8];
-    tmem_ld8(d + col, hh);
-    tmem_ld8(d + 128 + col, hl);
-    tmem_ld8(d + 256 + col, lh);
-    tmem_ld8(d + 384 + col, ll);
+    float hh[16], hl[16], lh[16], ll[16];
+    tmem_ld16(d + col, hh);
+    tmem_ld16(d + 128 + col, hl);
+    tmem_ld16(d + 256 + col, lh);
+    tmem_ld16(d + 384 + col, ll);
     tmem_wait_ld();
 #pragma unroll
-    for (int e = 0; e < 8; ++e) {
+    for (int e = 0; e < 16; ++e) {
       // 2^16 hh + 2^8 (hl + lh) + ll, every intermediate an exact fp32 integer
       const float s = E.fr(E.fr(hl[e]) + E.fr(lh[e]));
       const float t1 = E.fr(__fmaf_rn(256.f, E.fr(hh[e]), s));
       v[e] = E.canon(E.fr(__fmaf_rn(256.f, t1, E.fr(ll[e]))));
     }
   } else if (MODE == MODE_MODP1) {
-    float a[8];
-    tmem_ld8(d + col, a);
+    float a[16];
+    tmem_ld16(d + col, a);
     tmem_wait_ld();
 #pragma unroll
-    for (int e = 0; e < 8; ++e) v[e] = E.canon(E.fr(a[e]));
+    for (int e = 0; e < 16; ++e) v[e] = E.canon(E.fr(a[e]));
   } else {
-    float a[8], b[8];
-    tmem_ld8(d + col, a);
-    tmem_ld8(d + 128 + col, b);
+    float a[16], b[16];
+    tmem_ld16(d + col, a);
+    tmem_ld16(d + 128 + col, b);
     tmem_wait_ld();
 #pragma unroll
-    for (int e = 0; e < 8; ++e) {
+    for (int e = 0; e < 16; ++e) {
       float f = P.alpha_f * (a[e] + b[e]);
       if (P.epilogue == EPI_REDUCE && sign < 0) f = -f;
       v[e] = __float_as_uint(f);
@@ -471,7 +544,7 @@ __device__ __forceinline__ void tile_values(const GemmParams &P, const Epi &E, u
     return;
   }
 #pragma unroll
-  for (int e = 0; e < 8; ++e) {
+  for (int e = 0; e < 16; ++e) {
     uint32_t x = v[e];
     if (P.alpha_u != 1) x = E.mulmod(P.alpha_u, x);
     if (P.epilogue == EPI_REDUCE && sign < 0) x = x == 0 ? 0u : E.p - x;
@@ -680,13 +753,15 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_kernel(const __grid_constant
           }
           tc_fence_after();
           constexpr int cols = MODE == MODE_MODP2 ? 512 : 256;
-          for (int c = hsel * (cols / 2); c < (hsel + 1) * (cols / 2); c += 8) {
-            float v[8];
-            tmem_ld8(d + c, v);
+          for (int c = hsel * (cols / 2); c < (hsel + 1) * (cols / 2); c += 32) {
+            float v[32];
+            tmem_ld16(d + c, v);
+            tmem_ld16(d + c + 16, v + 16);
             tmem_wait_ld();
 #pragma unroll
-            for (int e = 0; e < 8; ++e) v[e] = E.fr(v[e]);
-            tmem_st8(d + c, v);
+            for (int e = 0; e < 32; ++e) v[e] = E.fr(v[e]);
+            tmem_st16(d + c, v);
+            tmem_st16(d + c + 16, v + 16);
           }
           tmem_wait_st();
           tc_fence_before();
@@ -699,14 +774,31 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_kernel(const __grid_constant
       if (ctl->abort) break;
       tc_fence_after();
       constexpr int NCH = BN / 64;
+      // Chunks are read out of tensor memory and stored one after the other
+      // (HOLD = 1): the store of one chunk overlaps the next chunk's math.
+      // HOLD = NCH would read every chunk before the first store.
+      constexpr int HOLD = 1;
+      uint32_t vals[HOLD][32];
+      if (HOLD > 1) {
+#pragma unroll
+        for (int ch = 0; ch < HOLD; ++ch) {
+          tile_values<MODE>(P, E, d, ch * 64 + hsel * 32, sign, vals[ch]);
+          tile_values<MODE>(P, E, d, ch * 64 + hsel * 32 + 16, sign, vals[ch] + 16);
+        }
+        tc_fence_before();
+        mbar_arrive(&acc_empty[buf]);  // accumulators free for the next tile
+      }
+#pragma unroll
       for (int ch = 0; ch < NCH; ++ch) {
         const int tc0 = ch * 64 + hsel * 32;  // tile column of this thread's first value
-        uint32_t v[32];
-#pragma unroll
-        for (int s = 0; s < 4; ++s) tile_values<MODE>(P, E, d, tc0 + 8 * s, sign, v + 8 * s);
-        if (ch == NCH - 1) {
-          tc_fence_before();
-          mbar_arrive(&acc_empty[buf]);  // accumulators free for the next tile
+        uint32_t *v = vals[HOLD > 1 ? ch : 0];
+        if (HOLD == 1) {
+          tile_values<MODE>(P, E, d, tc0, sign, v);
+          tile_values<MODE>(P, E, d, tc0 + 16, sign, v + 16);
+          if (ch == NCH - 1) {
+            tc_fence_before();
+            mbar_arrive(&acc_empty[buf]);  // accumulators free for the next tile
+          }
         }
         const int gc0 = ti.n0 + tc0;
         if (tma) {
@@ -858,19 +950,27 @@ __global__ void leaf_simt_kernel(const __grid_constant__ SimtArgs A, const __gri
 }  // namespace dev
 
 // ================================================================= host side
-template <int MODE>
-static cudaError_t pack_mode(const PackArgs &a, cudaStream_t s) {
-  if (a.prow_pad == 0 || a.pcol_pad == 0) return cudaSuccess;
+template <int MODE, int SET>
+static cudaError_t pack_set(const PackArgs &a, cudaStream_t s) {
   if (a.transpose) {
     dim3 grid(a.prow_pad / 64, a.pcol_pad / 32);
-    dev::pack_cols_kernel<MODE><<<grid, 256, 0, s>>>(a);
+    dev::pack_cols_kernel<MODE, SET><<<grid, 256, 0, s>>>(a);
   } else {
     int64_t units = (int64_t)a.prow_pad * (a.pcol_pad / 8);
     int64_t b = (units + 255) / 256;
     int blocks = (int)(b > 152 * 16 ? 152 * 16 : b);
-    dev::pack_rows_kernel<MODE><<<blocks, 256, 0, s>>>(a);
+    dev::pack_rows_kernel<MODE, SET><<<blocks, 256, 0, s>>>(a);
   }
   return cudaGetLastError();
+}
+template <int MODE>
+static cudaError_t pack_mode(const PackArgs &a, cudaStream_t s) {
+  if (a.prow_pad == 0 || a.pcol_pad == 0) return cudaSuccess;
+  const bool quads = a.nsrc == 4 && a.nout == 7;
+  if (a.set == PACK_WINOGRAD_A && quads) return pack_set<MODE, PACK_WINOGRAD_A>(a, s);
+  if (a.set == PACK_WINOGRAD_B && quads) return pack_set<MODE, PACK_WINOGRAD_B>(a, s);
+  if (a.set != PACK_GENERIC) return cudaErrorInvalidValue;
+  return pack_set<MODE, PACK_GENERIC>(a, s);
 }
 
 cudaError_t launch_pack(const PackArgs &a, int mode, cudaStream_t s) {

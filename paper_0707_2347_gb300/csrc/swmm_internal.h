@@ -56,7 +56,13 @@ struct PackArgs {
   int32_t transpose;
   uint32_t p;
   uint32_t barrett;  // floor(2^32 / p)
+  int32_t set;       // PACK_GENERIC: coef; PACK_WINOGRAD_A / _B: the Section 2 sums
 };
+// Output sets of a pack launch.  The Winograd sets take the four quadrants
+// (X11, X12, X21, X22) and write, in order, A11, A12, S4, A22, S1, S2, S3
+// (A side) or B11, B21, B22, T4, T1, T2, T3 (B side), forming the chains
+// S2 = S1 - A11, S4 = A12 - S2 and T2 = B22 - T1, T4 = T2 - B21 once.
+enum PackSet : int { PACK_GENERIC = 0, PACK_WINOGRAD_A = 1, PACK_WINOGRAD_B = 2 };
 cudaError_t launch_pack(const PackArgs &a, int mode, cudaStream_t s);
 
 // ---------------------------------------------------------------- leaf GEMM
@@ -144,5 +150,14 @@ cudaError_t launch_canon_modp(View dst, uint32_t p, cudaStream_t s);
 cudaError_t launch_zero(View dst, cudaStream_t s);
 // dst <- src
 cudaError_t launch_copy(View dst, View src, cudaStream_t s);
+
+// ------------------------------------------------------- residual probe
+// y = M x for a row-major rows x cols matrix (mod p: int32 elements, uint32
+// x and y in [0, p); FP32 mode: float elements, double x and y).
+cudaError_t launch_matvec(const void *M, int64_t rows, int64_t cols, int64_t ld, const void *x, void *y, uint32_t p,
+                          bool modp, int num_sms, cudaStream_t s);
+// r = v - alpha u - beta y0 elementwise over m entries (y0 may be null)
+cudaError_t launch_residual(int64_t m, const void *v, const void *u, const void *y0, void *r, uint32_t au,
+                            uint32_t bu, double af, double bf, uint32_t p, bool modp, int num_sms, cudaStream_t s);
 
 }  // namespace swmm

@@ -62,7 +62,7 @@ class Problem(ctypes.Structure):
 EXPORTS = ["swmm_create", "swmm_destroy", "swmm_set_stream", "swmm_mul", "swmm_muladd", "swmm_muladd_noalloc",
            "swmm_mul_inplace",
            "swmm_muladd_batched", "swmm_autotune", "swmm_workspace_elems", "swmm_leaf_timing", "swmm_get_stats",
-           "swmm_sync", "swmm_strerror", "swmm_last_error"]
+           "swmm_sync", "swmm_strerror", "swmm_last_error", "swmm_matvec", "swmm_residual"]
 
 _lib = None
 
@@ -96,6 +96,9 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.swmm_leaf_timing.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64),
                                      ctypes.POINTER(ctypes.c_double)]
     lib.swmm_sync.argtypes = [vp]
+    lib.swmm_matvec.argtypes = [vp, i64, i64, cvp, i64, cvp, vp, ctypes.POINTER(_Opts)]
+    lib.swmm_residual.argtypes = [vp, i64, i64, i64, cvp, cvp, i64, cvp, i64, cvp, cvp, cvp, i64, cvp, vp,
+                                  ctypes.POINTER(_Opts)]
     lib.swmm_strerror.argtypes = [ctypes.c_int]
     lib.swmm_strerror.restype = ctypes.c_char_p
     lib.swmm_last_error.argtypes = [vp]
@@ -149,6 +152,15 @@ def _mat(t, what):
     if t.dim() != 2 or (t.shape[1] > 1 and t.stride(1) != 1):
         raise ValueError(f"{what} must be a 2-D row-major tensor")
     return ctypes.c_void_p(t.data_ptr()), max(int(t.stride(0)), int(t.shape[1]), 1)
+
+
+def _vec(t):
+    """device pointer of a contiguous 1-D tensor (None -> NULL)."""
+    if t is None:
+        return None
+    if t.dim() != 1 or (t.numel() > 1 and t.stride(0) != 1):
+        raise ValueError("vectors must be contiguous 1-D tensors")
+    return ctypes.c_void_p(t.data_ptr())
 
 
 class Handle:
@@ -219,6 +231,29 @@ class Handle:
         self._check(self.lib.swmm_muladd_noalloc(self.h, m, k, n, _scalar(opts.mode, alpha), a, lda, b, ldb,
                                                  _scalar(opts.mode, beta), c, ldc, ctypes.byref(opts.c())))
         return C
+
+    def matvec(self, M, x, y, opts: Opts):
+        """swmm_matvec: y = M x (mod p: uint32 x, y as int32 tensors holding
+        [0, p); FP32 mode: float64 x, y)."""
+        self._stream()
+        mp, ldm = _mat(M, "M")
+        rows, cols = M.shape
+        self._check(self.lib.swmm_matvec(self.h, rows, cols, mp, ldm, _vec(x), _vec(y), ctypes.byref(opts.c())))
+        return y
+
+    def residual(self, alpha, A, B, beta, y0, C, x, r, opts: Opts):
+        """swmm_residual: r = C x - alpha A (B x) - beta y0 with y0 = C_in x
+        (None when beta is 0)."""
+        self._stream()
+        a, lda = _mat(A, "A")
+        b, ldb = _mat(B, "B")
+        c, ldc = _mat(C, "C")
+        m, k = A.shape
+        n = B.shape[1]
+        self._check(self.lib.swmm_residual(self.h, m, k, n, _scalar(opts.mode, alpha), a, lda, b, ldb,
+                                           _scalar(opts.mode, beta), _vec(y0), c, ldc, _vec(x), _vec(r),
+                                           ctypes.byref(opts.c())))
+        return r
 
     def mul_inplace(self, A, B, C, opts: Opts, alpha=1, beta=None):
         """Schedules that may overwrite A and/or B (Tables 3-8)."""

@@ -16,7 +16,7 @@ from __future__ import annotations
 
 import numpy as np
 
-SEED_A, SEED_B, SEED_C, SEED_SHAPES = 1, 2, 3, 4
+SEED_A, SEED_B, SEED_C, SEED_SHAPES, SEED_X = 1, 2, 3, 4, 5  # SEED_X: probe vectors
 
 
 def _rng(seed: int, tag: int = 0) -> np.random.Generator:
