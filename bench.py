@@ -295,6 +295,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-classical", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="launch kernels directly instead of a CUDA graph")
+    ap.add_argument("--serial", action="store_true",
+                    help="capture the graph in row order on one stream (no dataflow overlap)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     w = WORKLOADS[args.workload]
@@ -367,11 +369,18 @@ def main():
             ms = float(t.item())
         return ms
 
-    gflag = 0 if args.no_graph else S.FLAG_GRAPH
-    opts = S.Opts(mode=mode, p=p or 65521, sched=w["sched"], depth=w["depth"], flags=S.FLAG_TIMING | gflag,
+    gflag = 0 if args.no_graph else (S.FLAG_GRAPH | (S.FLAG_SERIAL if args.serial else 0))
+    opts = S.Opts(mode=mode, p=p or 65521, sched=w["sched"], depth=w["depth"], flags=gflag,
                   ipmm_cutoff=w.get("cutoff", 0))
     with Clocks(local) as clk:
         ms = timed(opts, args.steps, args.warmup)
+    # Per-launch GEMM durations: the same K steps again with an event pair
+    # around every leaf GEMM launch (recorded on the launching stream, inside
+    # the graph).  The event nodes cost ~5 us each, so the value above is
+    # timed without them.
+    topts = S.Opts(mode=mode, p=p or 65521, sched=w["sched"], depth=w["depth"], flags=S.FLAG_TIMING | gflag,
+                   ipmm_cutoff=w.get("cutoff", 0))
+    tms = timed(topts, args.steps, args.warmup)
     gemm_ms, gemm_launches, tensor_flops = h.leaf_timing(reset=True)
     st = h.stats()
     flops = 2.0 * m * n * k
@@ -396,14 +405,17 @@ def main():
                      "frac": round(achieved / sustained, 4), "traffic": TRAFFIC.get(args.workload),
                      "kernel": "gemm_kernel (leaf products, fp16 limb MMAs counted)",
                      "peak_kind": f"{peak_kind} bf16 sustained", "launches_per_step": st["leaf_launches"],
-                     "gemm_ms_per_step": round(gemm_ms / max(gemm_launches, 1) * st["leaf_launches"], 4)},
+                     "gemm_ms_per_step": round(gemm_ms / max(gemm_launches, 1) * st["leaf_launches"], 4),
+                     "timing_pass_ms_per_step": round(tms, 4)},
     }
     line["clocks"] = clk.summary()
 
     if not args.no_classical and w["sched"] != CLASSICAL:
         dC.copy_(dC0)
+        cms = timed(S.Opts(mode=mode, p=p or 65521, sched=CLASSICAL, depth=0, flags=gflag), args.steps, args.warmup)
+        dC.copy_(dC0)
         copts = S.Opts(mode=mode, p=p or 65521, sched=CLASSICAL, depth=0, flags=S.FLAG_TIMING | gflag)
-        cms = timed(copts, args.steps, args.warmup)
+        timed(copts, args.steps, args.warmup)
         cg_ms, cg_n, cg_fl = h.leaf_timing(reset=True)
         cval = world * flops / (cms * 1e-3) / 1e9
         line["classical"] = {"value": round(cval, 2), "ms_per_step": round(cms, 4),

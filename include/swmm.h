@@ -88,7 +88,14 @@ extern "C" {
                                   calls (same sizes, pointers, options and
                                   scalars); the graph runs on an internal
                                   stream ordered after and before the handle's
-                                  stream by events */
+                                  stream by events.  The captured launches
+                                  are ordered by the memory they touch: a
+                                  launch waits only for earlier launches
+                                  whose blocks it reads or writes, so
+                                  independent rows of a schedule may overlap
+                                  (operand staging is then double-buffered) */
+#define SWMM_FLAG_SERIAL 16u   /* with SWMM_FLAG_GRAPH: capture every launch
+                                  in row order on one stream */
 
 typedef struct swmm_ctx *swmm_t;
 

@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libswmm.so")
 SOURCES = ["api.cpp", "executor.cpp", "schedules.cpp", "ew_kernels.cu", "leaf_kernel.cu", "noalloc.cu",
-           "probe_kernels.cu"]
+           "probe_kernels.cu", "flow.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -134,10 +134,16 @@ struct swmm_ctx {
   std::vector<std::unique_ptr<GraphEntry>> graphs;
   cudaStream_t cap = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  // dataflow capture: side streams and an event per launch of a captured call
+  cudaStream_t flow_streams[kFlowStreams - 1] = {};
+  std::vector<cudaEvent_t> flow_events;
   // autotuner decisions: (m, k, n, mode, p) -> (sched, depth, est_us, elems)
   std::vector<std::pair<std::array<int64_t, 5>, std::tuple<int32_t, int32_t, double, int64_t>>> tuned;
   ~swmm_ctx() {
     graphs.clear();
+    for (cudaStream_t s : flow_streams)
+      if (s) cudaStreamDestroy(s);
+    for (cudaEvent_t e : flow_events) cudaEventDestroy(e);
     if (cap) cudaStreamDestroy(cap);
     if (ev_in) cudaEventDestroy(ev_in);
     if (ev_out) cudaEventDestroy(ev_out);
@@ -338,9 +344,12 @@ int make_plan(swmm_t h, const Req &q, const swmm_opts *o, bool check_ptrs, Plan 
 
 // Issue a planned call on `stream`: workspace, kernels, final canonical
 // pass, release.  Adds its counters to `st`.
-int enqueue(swmm_t h, const Plan &P, cudaStream_t stream, TimingHook *timing, const Scratch *ext, swmm_stats &st) {
+int enqueue(swmm_t h, const Plan &P, cudaStream_t stream, TimingHook *timing, const Scratch *ext, swmm_stats &st,
+            bool use_flow = false) {
   const Exec &x = P.x;
   Exec r = x;
+  r.stage_slots = use_flow ? 2 : 1;
+  const int64_t stage_bytes = r.stage_slots * ((x.stage_need + 1023) / 1024 * 1024);
   r.dry = false;
   r.lazy = false;
   r.stream = stream;
@@ -352,9 +361,9 @@ int enqueue(swmm_t h, const Plan &P, cudaStream_t stream, TimingHook *timing, co
   if (ext) {
     // caller-provided scratch: carve, never allocate
     const int64_t ws_bytes = (x.ws_peak + 1023) / 1024 * 1024;
-    if (ws_bytes + x.stage_need > ext->bytes)
+    if (ws_bytes + stage_bytes > ext->bytes)
       return fail(h, SWMM_EINVAL,
-                  "plan needs " + std::to_string(ws_bytes + x.stage_need) + " bytes of scratch, more than the " +
+                  "plan needs " + std::to_string(ws_bytes + stage_bytes) + " bytes of scratch, more than the " +
                       std::to_string(ext->bytes) + "-byte static scratch");
     r.ws = x.ws_peak > 0 ? ext->base : nullptr;
     r.stage = x.stage_need > 0 ? ext->base + ws_bytes : nullptr;
@@ -363,13 +372,25 @@ int enqueue(swmm_t h, const Plan &P, cudaStream_t stream, TimingHook *timing, co
       cudaGetLastError();
       return fail(h, SWMM_ENOMEM, "workspace allocation failed");
     }
-    if (x.stage_need > 0 && cudaMallocAsync((void **)&r.stage, x.stage_need, stream) != cudaSuccess) {
+    if (x.stage_need > 0 && cudaMallocAsync((void **)&r.stage, stage_bytes, stream) != cudaSuccess) {
       cudaGetLastError();
       if (r.ws) cudaFreeAsync(r.ws, stream);
       return fail(h, SWMM_ENOMEM, "staging allocation failed");
     }
   }
-  execute(P, r);
+  if (use_flow) {
+    Flow flow(stream, h->flow_streams, h->flow_events);
+    r.flow = &flow;
+    execute(P, r);
+    flow.join();
+    r.flow = nullptr;
+    if (flow.error() != cudaSuccess && r.cuda_err == cudaSuccess) {
+      r.cuda_err = flow.error();
+      r.fail = std::string("dataflow ordering: ") + cudaGetErrorString(flow.error());
+    }
+  } else {
+    execute(P, r);
+  }
   if (r.lazy && r.ok()) {
     // fused levels leave unreduced representatives: one canonicalising pass
     ++r.ew_launches;
@@ -384,7 +405,7 @@ int enqueue(swmm_t h, const Plan &P, cudaStream_t stream, TimingHook *timing, co
   st.workspace_bytes = std::max<int64_t>(st.workspace_bytes, x.ws_peak);
   st.plan_extra_elems = std::max<int64_t>(st.plan_extra_elems, x.tmp_peak_elems);
   st.paper_extra_elems = std::max<int64_t>(st.paper_extra_elems, P.paper);
-  st.staging_bytes = std::max<int64_t>(st.staging_bytes, x.stage_need);
+  st.staging_bytes = std::max<int64_t>(st.staging_bytes, x.stage_need > 0 ? stage_bytes : 0);
   st.add_elems += r.add_elems;
   st.leaf_flops += r.leaf_flops;
   st.leaf_launches += r.leaf_launches;
@@ -441,6 +462,27 @@ int run_plans(swmm_t h, const std::vector<Plan> &plans, uint32_t flags, const Sc
         return fail(h, SWMM_ECUDA, "graph stream creation failed");
       }
     }
+    const bool use_flow = !(flags & SWMM_FLAG_SERIAL);
+    if (use_flow) {
+      // side streams and enough events for the largest plan, made before
+      // the capture starts
+      size_t need = 2;
+      for (const Plan &P : plans)
+        need = std::max<size_t>(need, (size_t)(8 * P.x.leaf_launches + P.x.ew_launches + 2));
+      for (cudaStream_t &s : h->flow_streams)
+        if (!s && cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+          cudaGetLastError();
+          return fail(h, SWMM_ECUDA, "flow stream creation failed");
+        }
+      while (h->flow_events.size() < need) {
+        cudaEvent_t e;
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+          cudaGetLastError();
+          return fail(h, SWMM_ECUDA, "flow event creation failed");
+        }
+        h->flow_events.push_back(e);
+      }
+    }
     std::unique_ptr<GraphEntry> ne(new GraphEntry());
     ne->key = key;
     if (cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
@@ -449,7 +491,7 @@ int run_plans(swmm_t h, const std::vector<Plan> &plans, uint32_t flags, const Sc
     }
     int rc = SWMM_OK;
     for (const Plan &P : plans) {
-      rc = enqueue(h, P, h->cap, timing ? &ne->timer : nullptr, nullptr, ne->stats);
+      rc = enqueue(h, P, h->cap, timing ? &ne->timer : nullptr, nullptr, ne->stats, use_flow);
       if (rc != SWMM_OK) break;
     }
     cudaGraph_t graph = nullptr;

@@ -61,23 +61,41 @@ View Exec::alloc_tmp(int64_t rows, int64_t cols) {
   return v;
 }
 
+cudaStream_t Exec::op_begin(const std::vector<Rect> &rd, const std::vector<Rect> &wr) {
+  if (!flow) return stream;
+  return flow->begin(rd.data(), (int)rd.size(), wr.data(), (int)wr.size());
+}
+
+void Exec::op_end() {
+  if (flow) flow->end();
+}
+
+char *Exec::next_stage() {
+  const int64_t slot = rup(stage_need, 1024);
+  return stage + (stage_turn++ % stage_slots) * slot;
+}
+
 void Exec::add(View d, View s1, View s2, Scalar c1, Scalar c2) {
   add_elems += d.rows * d.cols;
   ++ew_launches;
   if (dry) return;
+  cudaStream_t st = op_begin({rect_of(s1), rect_of(s2)}, {rect_of(d)});
   if (fp32)
-    check(launch_add_f(d, s1, s2, c1.f, c2.f, stream), "add");
+    check(launch_add_f(d, s1, s2, c1.f, c2.f, st), "add");
   else
-    check(launch_add(d, s1, s2, c1.u, c2.u, p, 0, stream), "add");
+    check(launch_add(d, s1, s2, c1.u, c2.u, p, 0, st), "add");
+  op_end();
 }
 
 void Exec::scale(View d, bool keep, Scalar beta) {
   ++ew_launches;
   if (dry) return;
+  cudaStream_t st = op_begin({}, {rect_of(d)});
   if (fp32)
-    check(launch_scale_f(d, keep ? beta.f : 0.f, stream), "scale");
+    check(launch_scale_f(d, keep ? beta.f : 0.f, st), "scale");
   else
-    check(launch_scale_modp(d, keep ? beta.u : 0u, p, stream), "scale");
+    check(launch_scale_modp(d, keep ? beta.u : 0u, p, st), "scale");
+  op_end();
 }
 
 // ----------------------------------------------------------------- leaves
@@ -126,7 +144,9 @@ void Exec::leaf(Scalar alpha, bool acc, Scalar beta, View L, View R, View D) {
     S.M = (int)m;
     S.N = (int)n;
     S.K = (int)k;
-    check(launch_leaf_simt(S, P, mode, stream), "simt leaf");
+    cudaStream_t st = op_begin({rect_of(L), rect_of(R)}, {rect_of(D)});
+    check(launch_leaf_simt(S, P, mode, st), "simt leaf");
+    op_end();
     return;
   }
   const int pl = planes_of(mode), bn = bn_of(mode);
@@ -135,8 +155,10 @@ void Exec::leaf(Scalar alpha, bool acc, Scalar beta, View L, View R, View D) {
   stage_need = std::max(stage_need, abytes + bbytes);
   ew_launches += 2;
   if (dry) return;
-  uint16_t *Ap = reinterpret_cast<uint16_t *>(stage);
-  uint16_t *Bp = reinterpret_cast<uint16_t *>(stage + abytes);
+  char *stg = next_stage();
+  uint16_t *Ap = reinterpret_cast<uint16_t *>(stg);
+  uint16_t *Bp = reinterpret_cast<uint16_t *>(stg + abytes);
+  const Rect ra = rect_bytes(Ap, abytes), rb = rect_bytes(Bp, bbytes);
   PackArgs pa;
   std::memset(&pa, 0, sizeof(pa));
   pa.src[0] = L.ptr;
@@ -152,7 +174,9 @@ void Exec::leaf(Scalar alpha, bool acc, Scalar beta, View L, View R, View D) {
   pa.transpose = 0;
   pa.p = p;
   pa.barrett = p ? (uint32_t)(0x100000000ull / p) : 0;
-  check(launch_pack(pa, mode, stream), "pack A");
+  cudaStream_t st = op_begin({rect_of(L)}, {ra});
+  check(launch_pack(pa, mode, st), "pack A");
+  op_end();
   pa.src[0] = R.ptr;
   pa.ld[0] = R.ld;
   pa.out[0] = Bp;
@@ -161,7 +185,9 @@ void Exec::leaf(Scalar alpha, bool acc, Scalar beta, View L, View R, View D) {
   pa.prow_pad = (int)Np;
   pa.pcol_pad = (int)Kp;
   pa.transpose = 1;
-  check(launch_pack(pa, mode, stream), "pack B");
+  st = op_begin({rect_of(R)}, {rb});
+  check(launch_pack(pa, mode, st), "pack B");
+  op_end();
   Product &pr = P.prod[0];
   if (!make_tmap(&pr.ta, Ap, pl * Mp, Kp, kBM) || !make_tmap(&pr.tb, Bp, pl * Np, Kp, bn)) {
     if (fail.empty()) fail = "tensor map encoding failed";
@@ -183,9 +209,11 @@ void Exec::leaf(Scalar alpha, bool acc, Scalar beta, View L, View R, View D) {
   pr.tile_begin = 0;
   P.nprod = 1;
   P.total_tiles = pr.tiles_m * pr.tiles_n;
-  if (timing) timing->begin(stream);
-  check(launch_gemm_tc(P, mode, num_sms, stream), "leaf gemm");
-  if (timing) timing->end(stream, 2.0 * m * n * k * limb_products());
+  st = op_begin({ra, rb}, {rect_of(D)});
+  if (timing) timing->begin(st);
+  check(launch_gemm_tc(P, mode, num_sms, st), "leaf gemm");
+  if (timing) timing->end(st, 2.0 * m * n * k * limb_products());
+  op_end();
 }
 
 // One whole Winograd level (Section 2) with fused pre- and post-additions.
@@ -236,12 +264,14 @@ void Exec::fused_level(Scalar alpha, bool acc, Scalar beta, View L, View R, View
   if (!keep) {
     ++ew_launches;
     if (!dry) {
+      cudaStream_t st = op_begin({}, {rect_of(D)});
       if (!acc)
-        check(launch_zero(D, stream), "fused prologue");
+        check(launch_zero(D, st), "fused prologue");
       else if (fp32)
-        check(launch_scale_f(D, beta.f, stream), "fused prologue");
+        check(launch_scale_f(D, beta.f, st), "fused prologue");
       else
-        check(launch_scale_modp(D, beta.u, p, stream), "fused prologue");
+        check(launch_scale_modp(D, beta.u, p, st), "fused prologue");
+      op_end();
     }
   }
   GemmParams P;
@@ -271,7 +301,9 @@ void Exec::fused_level(Scalar alpha, bool acc, Scalar beta, View L, View R, View
         S.M = (int)hm;
         S.N = (int)hn;
         S.K = (int)hk;
-        check(launch_leaf_simt(S, P, mode, stream), "simt fused leaf");
+        cudaStream_t st = op_begin({rect_of(L), rect_of(R)}, {rect_of(D)});
+        check(launch_leaf_simt(S, P, mode, st), "simt fused leaf");
+        op_end();
       }
     }
   } else {
@@ -281,6 +313,8 @@ void Exec::fused_level(Scalar alpha, bool acc, Scalar beta, View L, View R, View
     stage_need = std::max(stage_need, 7 * (abytes + bbytes));
     ew_launches += 2;
     if (!dry) {
+      char *stg = next_stage();
+      const Rect ra = rect_bytes(stg, 7 * abytes), rb = rect_bytes(stg + 7 * abytes, 7 * bbytes);
       PackArgs pa, pb;
       std::memset(&pa, 0, sizeof(pa));
       std::memset(&pb, 0, sizeof(pb));
@@ -295,8 +329,8 @@ void Exec::fused_level(Scalar alpha, bool acc, Scalar beta, View L, View R, View
       pa.set = PACK_WINOGRAD_A;  // the chains of acoef / bcoef, formed once per element
       pb.set = PACK_WINOGRAD_B;
       for (int i = 0; i < 7; ++i) {
-        pa.out[i] = reinterpret_cast<uint16_t *>(stage + i * abytes);
-        pb.out[i] = reinterpret_cast<uint16_t *>(stage + 7 * abytes + i * bbytes);
+        pa.out[i] = reinterpret_cast<uint16_t *>(stg + i * abytes);
+        pb.out[i] = reinterpret_cast<uint16_t *>(stg + 7 * abytes + i * bbytes);
         for (int q = 0; q < 4; ++q) {
           pa.coef[i][q] = acoef[i][q];
           pb.coef[i][q] = bcoef[i][q];
@@ -316,8 +350,12 @@ void Exec::fused_level(Scalar alpha, bool acc, Scalar beta, View L, View R, View
       pb.pcol_pad = (int)Kp;
       pb.transpose = 1;
       pb.p = p;
-      check(launch_pack(pa, mode, stream), "fused pack A");
-      check(launch_pack(pb, mode, stream), "fused pack B");
+      cudaStream_t st = op_begin({rect_of(L)}, {ra});
+      check(launch_pack(pa, mode, st), "fused pack A");
+      op_end();
+      st = op_begin({rect_of(R)}, {rb});
+      check(launch_pack(pb, mode, st), "fused pack B");
+      op_end();
       int tiles = 0;
       for (int i = 0; i < 7; ++i) {
         Product &pr = P.prod[i];
@@ -349,9 +387,11 @@ void Exec::fused_level(Scalar alpha, bool acc, Scalar beta, View L, View R, View
       }
       P.nprod = 7;
       P.total_tiles = tiles;
-      if (timing) timing->begin(stream);
-      check(launch_gemm_tc(P, mode, num_sms, stream), "fused gemm");
-      if (timing) timing->end(stream, 7 * 2.0 * hm * hn * hk * limb_products());
+      st = op_begin({ra, rb}, {rect_of(D)});
+      if (timing) timing->begin(st);
+      check(launch_gemm_tc(P, mode, num_sms, st), "fused gemm");
+      if (timing) timing->end(st, 7 * 2.0 * hm * hn * hk * limb_products());
+      op_end();
     }
   }
 }
@@ -474,7 +514,12 @@ void Exec::table(Kind k, Scalar alpha, bool acc, Scalar beta, View L, View R, Vi
       View d = at(row.dst, row.shape);
       ++ew_launches;
       add_elems += d.rows * d.cols;
-      if (!dry) check(launch_copy(d, at(row.s1, row.shape), stream), "copy");
+      if (!dry) {
+        const View src = at(row.s1, row.shape);
+        cudaStream_t st = op_begin({rect_of(src)}, {rect_of(d)});
+        check(launch_copy(d, src, st), "copy");
+        op_end();
+      }
     } else {
       const KindInfo &S = kind_info(row.kind);
       call(row.kind, coef(row.c1), S.accumulate, row.acc ? coef(row.cacc) : Scalar{}, at(row.s1, SH_A),

@@ -1,10 +1,14 @@
 // Recursive executor: walks the paper's schedule tables and lowers each row
-// to kernel launches on one stream, in row order.
+// to kernel launches in row order, on one stream or, under a Flow, on
+// capture streams ordered by the memory each launch touches.
 #pragma once
 
 #include <cstdint>
 #include <string>
 
+#include <vector>
+
+#include "flow.h"
 #include "schedules.h"
 #include "swmm_internal.h"
 
@@ -44,9 +48,15 @@ struct Exec {
   // workspace for temporaries (bump allocator, bytes)
   char *ws = nullptr;
   int64_t ws_top = 0, ws_peak = 0;
-  // tensor-core operand staging (reused by every leaf launch, bytes)
+  // tensor-core operand staging (bytes): stage_slots areas of stage_need
+  // bytes used in turn by successive leaf launches (two under a Flow, so
+  // the next leaf's operands are packed while the current one multiplies)
   char *stage = nullptr;
   int64_t stage_need = 0;
+  int stage_slots = 1;
+  int stage_turn = 0;
+  // dataflow ordering over capture streams (null: every launch on `stream`)
+  Flow *flow = nullptr;
 
   // statistics
   int64_t tmp_elems = 0, tmp_peak_elems = 0;
@@ -71,6 +81,10 @@ struct Exec {
   void peel(Kind k, Scalar alpha, bool acc, Scalar beta, View L, View R, View D, int depth, const Arena &ar);
   void table(Kind k, Scalar alpha, bool acc, Scalar beta, View L, View R, View D, int depth, const Arena &ar);
   void add(View d, View s1, View s2, Scalar c1, Scalar c2);
+  // stream for a launch reading rd and writing wr; op_end() after issuing it
+  cudaStream_t op_begin(const std::vector<Rect> &rd, const std::vector<Rect> &wr);
+  void op_end();
+  char *next_stage();
   void scale(View d, bool keep, Scalar beta);  // d <- beta d, or 0
   void check(cudaError_t e, const char *what);
   View alloc_tmp(int64_t rows, int64_t cols);

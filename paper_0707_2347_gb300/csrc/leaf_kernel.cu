@@ -774,10 +774,11 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_kernel(const __grid_constant
       if (ctl->abort) break;
       tc_fence_after();
       constexpr int NCH = BN / 64;
-      // Chunks are read out of tensor memory and stored one after the other
-      // (HOLD = 1): the store of one chunk overlaps the next chunk's math.
-      // HOLD = NCH would read every chunk before the first store.
-      constexpr int HOLD = 1;
+      // With a single accumulator buffer the next tile's MMAs wait for this
+      // drain, so every chunk is read out of tensor memory before the first
+      // store (HOLD = NCH); with two buffers the chunks are read and stored
+      // one after the other.
+      constexpr int HOLD = C::ACC_BUFS == 1 ? NCH : 1;
       uint32_t vals[HOLD][32];
       if (HOLD > 1) {
 #pragma unroll

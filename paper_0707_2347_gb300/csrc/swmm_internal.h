@@ -13,9 +13,11 @@ constexpr int kErrTimeout = 5;  // matches SWMM_ETIMEOUT
 struct View {
   char *ptr = nullptr;
   int64_t rows = 0, cols = 0, ld = 0;  // ld in elements
+  char *base = nullptr;                // root of the matrix the view was cut from (null: ptr)
   char *at(int64_t r, int64_t c) const { return ptr + 4 * (r * ld + c); }
   View sub(int64_t r0, int64_t c0, int64_t nr, int64_t nc) const {
     View v;
+    v.base = base ? base : ptr;
     v.ptr = at(r0, c0);
     v.rows = nr;
     v.cols = nc;

@@ -26,7 +26,7 @@ SCHED_NAMES = {CLASSICAL: "classical", T1_DHSS: "T1", T2_HLJJTT: "T2", T3_IP: "I
                T5_OVR: "OvR", T6_ACLR: "AcLR", T7_ACCR: "AccR", T8_ACR: "AcR", T9_ACC: "Acc",
                IPMM: "IPMM", T4M_OVL: "OvLM"}
 # flags
-FLAG_UNFUSED, FLAG_SIMT_LEAF, FLAG_TIMING, FLAG_GRAPH = 1, 2, 4, 8
+FLAG_UNFUSED, FLAG_SIMT_LEAF, FLAG_TIMING, FLAG_GRAPH, FLAG_SERIAL = 1, 2, 4, 8, 16
 
 
 class SwmmError(RuntimeError):
