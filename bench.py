@@ -35,7 +35,7 @@ import numpy as np  # noqa: E402
 import synth  # noqa: E402
 
 MODP, FP32 = 0, 1
-CLASSICAL, T1, T2, IP, T9, IPMM = 0, 1, 2, 3, 9, 10
+CLASSICAL, T1, T2, IP, T9, IPMM, IP0VMM, TBLOCK = 0, 1, 2, 3, 9, 10, 12, 13
 
 WORKLOADS = {
     # configs[1]: the accumulate schedule at 8192 (default)
@@ -65,6 +65,18 @@ WORKLOADS = {
                           p=251, sched=T1, depth=2, entry="mul"),
     "fp32_t9_8192": dict(desc="C<-AB+C FP32 mode (3xbf16), 8192^2, Table 9 depth 2", m=8192, k=8192, n=8192,
                          mode=FP32, p=0, sched=T9, depth=2, entry="muladd"),
+    "t9_32768_p65521": dict(desc="C<-AB+C over Z/65521, 32768^2, Table 9 (Acc) depth 2, fused last level",
+                            m=32768, k=32768, n=32768, mode=MODP, p=65521, sched=T9, depth=2, entry="muladd"),
+    "tblock2_16384_p65521": dict(desc="C<-AB+C over Z/65521, 16384^2, Section 7.2 t=2 blocks by Table 9, depth 1",
+                                 m=16384, k=16384, n=16384, mode=MODP, p=65521, sched=TBLOCK, depth=1,
+                                 entry="muladd", tblock=2, acc=T9),
+    "ip0vmm_16384x8192x4096_p251": dict(desc="C<-AB over Z/251, m=16384 k=8192 n=4096, Algorithm 1 (IP0vMM) depth 2",
+                                        m=16384, k=8192, n=4096, mode=MODP, p=251, sched=IP0VMM, depth=2,
+                                        entry="inplace"),
+    # configs[3]: FP32 mode error and speed per depth
+    "fp32_sweep": dict(desc="C<-AB+C FP32 mode (3xbf16), n in {4096, 8192, 16384}, Table 9 depth 1-4 vs classical",
+                       m=16384, k=16384, n=16384, mode=FP32, p=0, sched=T9, depth=0, entry="sweep",
+                       ns=(4096, 8192, 16384), depths=(1, 2, 3, 4)),
 }
 DEFAULT = "t9_8192_p65521"
 
@@ -203,6 +215,61 @@ def run_reference(args, w, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def run_sweep(args, w, S, h, torch, dev, rank):
+    """FP32 mode per size and depth: effective GOP/s (graph replay, device-
+    resident inputs) and max |C - C64| / (|A|max |B|max) on 16 spot rows
+    against FP64 on the host, next to the classical split-bf16 product."""
+    rows = []
+    for n in w["ns"]:
+        A, B, C = (synth.normal_matrix(synth.SEED_A, n, n), synth.normal_matrix(synth.SEED_B, n, n),
+                   synth.normal_matrix(synth.SEED_C, n, n))
+        idx = np.linspace(0, n - 1, 16).astype(np.int64)
+        ref = A[idx].astype(np.float64) @ B.astype(np.float64) + C[idx].astype(np.float64)
+        scale = float(np.abs(A).max()) * float(np.abs(B).max())
+        dA, dB = torch.from_numpy(A).to(dev), torch.from_numpy(B).to(dev)
+        dC0 = torch.from_numpy(C).to(dev)
+        dC = dC0.clone()
+        for depth in (0,) + tuple(w["depths"]):
+            sched = S.CLASSICAL if depth == 0 else S.T9_ACC
+            o = S.Opts(mode=S.FP32, sched=sched, depth=depth, flags=S.FLAG_GRAPH)
+            dC.copy_(dC0)
+            h.muladd(1.0, dA, dB, 1.0, dC, o)
+            h.sync()
+            err = float(np.abs(dC[torch.from_numpy(idx).to(dev)].double().cpu().numpy() - ref).max()) / scale
+            for _ in range(args.warmup):
+                h.muladd(1.0, dA, dB, 1.0, dC, o)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(args.steps):
+                h.muladd(1.0, dA, dB, 1.0, dC, o)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / args.steps
+            st = h.stats()
+            bound = 1e-5 * n ** 0.6
+            rows.append({"n": n, "depth": depth, "schedule": "classical" if depth == 0 else "Acc",
+                         "gops": round(2.0 * n ** 3 / (ms * 1e-3) / 1e9, 1), "ms": round(ms, 3),
+                         "max_rel_err": float(f"{err:.3e}"), "bound": float(f"{bound:.3e}"),
+                         "within_bound": err <= bound, "workspace_bytes": st["workspace_bytes"]})
+        del dA, dB, dC, dC0
+        torch.cuda.empty_cache()
+    for r in rows:
+        base = next(x for x in rows if x["n"] == r["n"] and x["depth"] == 0)
+        r["vs_classical"] = round(r["gops"] / base["gops"], 4)
+    head = next(r for r in rows if r["n"] == max(w["ns"]) and r["depth"] == 2)
+    line = {
+        "metric": "effective GOP/s (2mnk/t)", "value": head["gops"], "unit": "GOP/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 (3xbf16)", "data": "synthetic",
+        "config": {"workload": w["desc"], "value_is": f"n={head['n']} depth 2",
+                   "l2": "inputs > 129 MB L2, no flush", "parallelism": "replicas x1"},
+        "sweep": rows,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def run_batch(args, w, S, h, torch, dev, dist, world, rank):
     """The batched workload: every rank runs its share of the problems (LPT
     partition on the modelled cost), inputs drawn on the device from a seeded
@@ -323,6 +390,9 @@ def main():
     if w["entry"] == "batch":
         run_batch(args, w, S, h, torch, dev, dist, world, rank)
         return
+    if w["entry"] == "sweep":
+        run_sweep(args, w, S, h, torch, dev, rank)
+        return
     m, k, n = w["m"], w["k"], w["n"]
     A, B, C = make_inputs(w)
     dA, dB = torch.from_numpy(A).to(dev), torch.from_numpy(B).to(dev)
@@ -370,8 +440,8 @@ def main():
         return ms
 
     gflag = 0 if args.no_graph else (S.FLAG_GRAPH | (S.FLAG_SERIAL if args.serial else 0))
-    opts = S.Opts(mode=mode, p=p or 65521, sched=w["sched"], depth=w["depth"], flags=gflag,
-                  ipmm_cutoff=w.get("cutoff", 0))
+    extra = dict(ipmm_cutoff=w.get("cutoff", 0), tblock=w.get("tblock", 0), ipmm_acc=w.get("acc", 0))
+    opts = S.Opts(mode=mode, p=p or 65521, sched=w["sched"], depth=w["depth"], flags=gflag, **extra)
     with Clocks(local) as clk:
         ms = timed(opts, args.steps, args.warmup)
     # Per-launch GEMM durations: the same K steps again with an event pair
@@ -379,7 +449,7 @@ def main():
     # the graph).  The event nodes cost ~5 us each, so the value above is
     # timed without them.
     topts = S.Opts(mode=mode, p=p or 65521, sched=w["sched"], depth=w["depth"], flags=S.FLAG_TIMING | gflag,
-                   ipmm_cutoff=w.get("cutoff", 0))
+                   **extra)
     tms = timed(topts, args.steps, args.warmup)
     gemm_ms, gemm_launches, tensor_flops = h.leaf_timing(reset=True)
     st = h.stats()
@@ -425,7 +495,7 @@ def main():
     if not args.no_e2e:
         pin = [torch.from_numpy(x).pin_memory() for x in (A, B, C)]
         out = torch.empty_like(pin[2]).pin_memory()
-        opts_e = S.Opts(mode=mode, p=p or 65521, sched=w["sched"], depth=w["depth"], flags=gflag)
+        opts_e = S.Opts(mode=mode, p=p or 65521, sched=w["sched"], depth=w["depth"], flags=gflag, **extra)
 
         def e2e_step():
             dA.copy_(pin[0], non_blocking=True)

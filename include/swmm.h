@@ -72,6 +72,12 @@ extern "C" {
 #define SWMM_T9_ACC 9    /* Table 9, C <- aAB + bC, read-only inputs */
 #define SWMM_IPMM 10     /* Algorithm 2, C <- AB, read-only, no extra memory */
 #define SWMM_T4M_OVL 11  /* Section 5.1 variant of Table 4: overwrites A11, A21 */
+#define SWMM_IP0VMM 12   /* Algorithm 1, C <- aAB for n < m, n <= k, n dividing
+                            m and k; overwrites A, no extra memory */
+#define SWMM_TBLOCK 13   /* Section 7.2, C <- aAB + bC, read-only inputs: C in
+                            t x t blocks, each the sum of t products with
+                            accumulation by Table 2 (or Table 9); the
+                            temporaries of one block call at a time */
 #define SWMM_AUTO (-1)   /* batched calls: the autotuner picks schedule and depth */
 
 /* flags */
@@ -102,14 +108,16 @@ typedef struct swmm_ctx *swmm_t;
 typedef struct {
   int32_t mode;        /* SWMM_MODP or SWMM_FP32 */
   uint32_t p;          /* modulus for SWMM_MODP: 2 < p < 65536 */
-  int32_t sched;       /* SWMM_CLASSICAL ... SWMM_T4M_OVL */
+  int32_t sched;       /* SWMM_CLASSICAL ... SWMM_IP0VMM */
   int32_t depth;       /* Winograd recursion levels (0 = classical) */
   uint32_t flags;      /* SWMM_FLAG_* */
   int32_t ipmm_cutoff; /* IPMM: classical base case once the C block is
                           <= this size (0 = 1024) */
-  int32_t ipmm_acc;    /* IPMM accumulation schedule: SWMM_T2_HLJJTT
-                          (default, 0) or SWMM_T9_ACC (Section 7.1 end) */
-  int32_t reserved;
+  int32_t ipmm_acc;    /* accumulation schedule of IPMM and SWMM_TBLOCK:
+                          SWMM_T2_HLJJTT (default, 0) or SWMM_T9_ACC
+                          (Sections 7.1 and 7.2) */
+  int32_t tblock;      /* SWMM_TBLOCK: t >= 2 blocks per dimension (0 = 2);
+                          m, k and n must be multiples of t */
 } swmm_opts;
 
 typedef struct {
@@ -163,7 +171,9 @@ typedef struct {
 } swmm_problem;
 
 /* C <- alpha A B + beta C with read-only A and B: SWMM_CLASSICAL,
- * SWMM_T2_HLJJTT (Table 2), SWMM_T9_ACC (Table 9, square). */
+ * SWMM_T2_HLJJTT (Table 2), SWMM_T9_ACC (Table 9, square), SWMM_TBLOCK
+ * (Section 7.2; m, k, n multiples of opts->tblock, square blocks when the
+ * base schedule is Table 9). */
 int swmm_muladd(swmm_t h, int64_t m, int64_t k, int64_t n, const void *alpha,
                 const void *A, int64_t lda, const void *B, int64_t ldb,
                 const void *beta, void *C, int64_t ldc, const swmm_opts *opts);
@@ -190,11 +200,15 @@ int swmm_muladd_noalloc(swmm_t h, int64_t m, int64_t k, int64_t n, const void *a
 
 /* Schedules that may overwrite their inputs (Sections 5.1-5.3).
  * beta == NULL: C <- alpha A B with SWMM_T3_IP (k = n <= m), SWMM_T4_OVL,
- * SWMM_T4M_OVL, SWMM_T5_OVR (square).  beta != NULL: C <- alpha A B + beta C
+ * SWMM_T4M_OVL, SWMM_T5_OVR (square), or SWMM_IP0VMM (Algorithm 1: A is
+ * m x k, B is k x n with n < m, n <= k, n dividing m and k; C is split
+ * into n x n row blocks C_1..C_m/n; C_1 <- A_11 B_1 by Table 1 with C_2 as
+ * scratch, then A_11 is the scratch of C_i <- A_i1 B_1 by Table 4 and of
+ * C_i <- A_ij B_j + C_i by Table 2).  beta != NULL: C <- alpha A B + beta C
  * with SWMM_T6_ACLR, SWMM_T7_ACCR (square), SWMM_T8_ACR (any even shape).
  * On return the overwritten operand blocks hold unspecified values:
- *   IP, AcLR: all of A and B;  OvL: A;  OvLM: A11, A21;  OvR, AccR: B;
- *   AcR: B12, B21.  Every other block is left bit-identical. */
+ *   IP, AcLR: all of A and B;  OvL, IP0vMM: A;  OvLM: A11, A21;
+ *   OvR, AccR: B;  AcR: B12, B21.  Every other block is left bit-identical. */
 int swmm_mul_inplace(swmm_t h, int64_t m, int64_t k, int64_t n,
                      void *A, int64_t lda, void *B, int64_t ldb,
                      void *C, int64_t ldc, const void *alpha, const void *beta,

@@ -242,7 +242,8 @@ struct Plan {
   bool accum = false, ne = false;
   int sched = 0, depth = 0, lv = 0;
   int64_t cutoff = 1024;
-  Kind ipmm_acc = K_T2;
+  Kind ipmm_acc = K_T2;  // accumulation kind of IPMM and of the Section 7.2 blocks
+  int tblock = 2;
   int64_t paper = 0;
 };
 
@@ -250,6 +251,10 @@ void execute(const Plan &P, Exec &e) {
   if (!P.ne) return;
   if (P.sched == SWMM_IPMM)
     e.ipmm(P.L, P.R, P.D, P.depth, P.cutoff, P.ipmm_acc);
+  else if (P.sched == SWMM_IP0VMM)
+    e.ip0vmm(P.alpha, P.L, P.R, P.D, P.depth);
+  else if (P.sched == SWMM_TBLOCK)
+    e.tblock(P.alpha, P.beta, P.L, P.R, P.D, P.tblock, P.depth, P.ipmm_acc);
   else if (P.sched == SWMM_CLASSICAL)
     e.leaf(P.alpha, P.accum, P.beta, P.L, P.R, P.D);
   else
@@ -268,9 +273,11 @@ int make_plan(swmm_t h, const Req &q, const swmm_opts *o, bool check_ptrs, Plan 
   // schedule / entry point consistency (overwrite contracts, Sections 3, 5)
   bool okk = false;
   if (q.entry == 0) okk = sched == SWMM_CLASSICAL || sched == SWMM_T1_DHSS || sched == SWMM_IPMM;
-  if (q.entry == 1) okk = sched == SWMM_CLASSICAL || sched == SWMM_T2_HLJJTT || sched == SWMM_T9_ACC;
+  if (q.entry == 1)
+    okk = sched == SWMM_CLASSICAL || sched == SWMM_T2_HLJJTT || sched == SWMM_T9_ACC || sched == SWMM_TBLOCK;
   if (q.entry == 2 && !accum)
-    okk = sched == SWMM_T3_IP || sched == SWMM_T4_OVL || sched == SWMM_T4M_OVL || sched == SWMM_T5_OVR;
+    okk = sched == SWMM_T3_IP || sched == SWMM_T4_OVL || sched == SWMM_T4M_OVL || sched == SWMM_T5_OVR ||
+          sched == SWMM_IP0VMM;
   if (q.entry == 2 && accum) okk = sched == SWMM_T6_ACLR || sched == SWMM_T7_ACCR || sched == SWMM_T8_ACR;
   if (!okk) return fail(h, SWMM_EINVAL, "schedule not valid for this entry point");
   const bool ne = q.m > 0 && q.n > 0;
@@ -286,8 +293,17 @@ int make_plan(swmm_t h, const Req &q, const swmm_opts *o, bool check_ptrs, Plan 
       return fail(h, SWMM_EINVAL, "A and B overlap (the schedule overwrites them)");
   }
   const int depth = sched == SWMM_CLASSICAL ? 0 : o->depth;
-  const int lv = levels_possible(q.m, q.k, q.n, depth);
-  if (sched != SWMM_CLASSICAL && sched != SWMM_IPMM && lv > 0) {
+  const int tb = o->tblock > 0 ? o->tblock : 2;
+  if (sched == SWMM_TBLOCK) {
+    if (tb < 2 || tb > 64) return fail(h, SWMM_EINVAL, "tblock must be in [2, 64] (Section 7.2)");
+    if (q.m % tb || q.k % tb || q.n % tb)
+      return fail(h, SWMM_EINVAL, "Section 7.2 blocking needs m, k and n multiples of t");
+    if (o->ipmm_acc == SWMM_T9_ACC && !(q.m == q.k && q.k == q.n))
+      return fail(h, SWMM_EINVAL, "Section 7.2 with Table 9 blocks needs square operands");
+  }
+  const int lv = sched == SWMM_TBLOCK ? levels_possible(q.m / tb, q.k / tb, q.n / tb, depth)
+                                      : levels_possible(q.m, q.k, q.n, depth);
+  if (sched != SWMM_CLASSICAL && sched != SWMM_IPMM && sched != SWMM_IP0VMM && sched != SWMM_TBLOCK && lv > 0) {
     const KindInfo &K = kind_info(kind_of(sched));
     if (K.square && !(q.m == q.k && q.k == q.n))
       return fail(h, SWMM_EINVAL, std::string(K.name) + " needs square operands (Section 5.3)");
@@ -295,6 +311,9 @@ int make_plan(swmm_t h, const Req &q, const swmm_opts *o, bool check_ptrs, Plan 
       return fail(h, SWMM_EINVAL, "IP needs k = n <= m (Section 5.3)");
   }
   if (sched == SWMM_IPMM && q.m != q.n) return fail(h, SWMM_EINVAL, "IPMM needs m = n (Algorithm 2)");
+  if (sched == SWMM_IP0VMM && ne &&
+      !(q.n < q.m && q.n <= q.k && q.n > 0 && q.m % q.n == 0 && q.k % q.n == 0))
+    return fail(h, SWMM_EINVAL, "IP0vMM needs n < m, n <= k, n dividing m and k (Algorithm 1)");
 
   P.q = q;
   P.o = *o;
@@ -332,13 +351,18 @@ int make_plan(swmm_t h, const Req &q, const swmm_opts *o, bool check_ptrs, Plan 
   P.D.ld = q.ldc;
   P.cutoff = o->ipmm_cutoff > 0 ? o->ipmm_cutoff : 1024;
   P.ipmm_acc = o->ipmm_acc == SWMM_T9_ACC ? K_ACC : K_T2;
+  P.tblock = tb;
   // planning pass: sizes and counts, no launches
   x.dry = true;
   execute(P, x);
   if (!x.fail.empty()) return fail(h, SWMM_EINVAL, x.fail);
   // levels that materialise temporaries: all but a fused last one
   const int tmp_levels = (x.fused && lv > 0 && sched != SWMM_IPMM) ? lv - 1 : lv;
-  P.paper = paper_elems(sched, q.m, q.k, q.n, tmp_levels);
+  if (sched == SWMM_TBLOCK)  // one block call's temporaries (Section 7.2)
+    P.paper = paper_elems(o->ipmm_acc == SWMM_T9_ACC ? SWMM_T9_ACC : SWMM_T2_HLJJTT, q.m / tb, q.k / tb, q.n / tb,
+                          tmp_levels);
+  else
+    P.paper = paper_elems(sched, q.m, q.k, q.n, tmp_levels);
   return SWMM_OK;
 }
 
@@ -645,8 +669,10 @@ int swmm_workspace_elems(swmm_t h, int64_t m, int64_t k, int64_t n, const swmm_o
   const int s = opts->sched;
   const bool acc_inplace = s == SWMM_T6_ACLR || s == SWMM_T7_ACCR || s == SWMM_T8_ACR;
   int entry = 0;
-  if (s == SWMM_T2_HLJJTT || s == SWMM_T9_ACC) entry = 1;
-  if (s == SWMM_T3_IP || s == SWMM_T4_OVL || s == SWMM_T4M_OVL || s == SWMM_T5_OVR || acc_inplace) entry = 2;
+  if (s == SWMM_T2_HLJJTT || s == SWMM_T9_ACC || s == SWMM_TBLOCK) entry = 1;
+  if (s == SWMM_T3_IP || s == SWMM_T4_OVL || s == SWMM_T4M_OVL || s == SWMM_T5_OVR || s == SWMM_IP0VMM ||
+      acc_inplace)
+    entry = 2;
   static const uint32_t one = 1;
   Req q{entry, m, k, n, nullptr, nullptr, nullptr, k, n, n, &one, acc_inplace || entry == 1 ? &one : nullptr};
   Plan P;

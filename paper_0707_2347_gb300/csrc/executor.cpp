@@ -563,4 +563,48 @@ void Exec::ipmm(View L, View R, View D, int depth, int64_t cutoff, Kind acc_kind
   ipmm(L.sub(h, 0, h, k), R.sub(0, h, k, h), D.quad(1, 1), depth, cutoff, acc_kind);
 }
 
+// Algorithm 1 (IP0vMM, Section 5.3): C (m x n) is split into n x n row
+// blocks C_1..C_m0, A into n x n blocks A_ij, B into n x n row blocks B_j.
+//   C_1 <- alpha A_11 B_1                    Table 1, temporaries in C_2
+//   C_i <- alpha A_i1 B_1        i >= 2      Table 4 (overwrites A_i1),
+//   C_i <- alpha A_ij B_j + C_i  j >= 2      Table 2,
+// the last two with every temporary carved from A_11, which is dead once
+// C_1 is formed.  A is overwritten; B is read-only; no extra memory.
+void Exec::ip0vmm(Scalar alpha, View L, View R, View D, int depth) {
+  if (!ok()) return;
+  const int64_t m = L.rows, k = L.cols, n = R.cols;
+  const int64_t m0 = m / n, k0 = k / n;
+  int d = 0;
+  for (int64_t s = n; d < depth && s % 2 == 0 && s >= 2; s /= 2) ++d;
+  Arena first;
+  first.carve = true;
+  first.region = D.sub(n, 0, n, n);
+  call(K_T1, alpha, false, Scalar{}, L.sub(0, 0, n, n), R.sub(0, 0, n, n), D.sub(0, 0, n, n), d, first);
+  Arena rest;
+  rest.carve = true;
+  rest.region = L.sub(0, 0, n, n);
+  for (int64_t i = 1; i < m0; ++i)
+    call(K_OVL, alpha, false, Scalar{}, L.sub(i * n, 0, n, n), R.sub(0, 0, n, n), D.sub(i * n, 0, n, n), d, rest);
+  for (int64_t j = 1; j < k0; ++j)
+    for (int64_t i = 0; i < m0; ++i)
+      call(K_T2, alpha, true, one(), L.sub(i * n, j * n, n, n), R.sub(j * n, 0, n, n), D.sub(i * n, 0, n, n), d,
+           rest);
+}
+
+// Section 7.2: D (m x n) in t x t blocks D_ij of (m/t) x (n/t); each is
+//   D_ij <- alpha A_i1 B_1j + beta D_ij,  then  D_ij <- alpha A_il B_lj + D_ij
+// for l = 2..t, every call by the accumulating schedule acc_kind (Table 2,
+// or Table 9) at `depth` levels.  The calls run one after the other, so the
+// temporaries of one block call are all the extra memory: (n/t)^2 with
+// Table 2, 2 (n/t)^2 / 3 with Table 9.
+void Exec::tblock(Scalar alpha, Scalar beta, View L, View R, View D, int t, int depth, Kind acc_kind) {
+  if (!ok()) return;
+  const int64_t mt = L.rows / t, kt = L.cols / t, nt = R.cols / t;
+  for (int i = 0; i < t; ++i)
+    for (int j = 0; j < t; ++j)
+      for (int l = 0; l < t; ++l)
+        call(acc_kind, alpha, true, l == 0 ? beta : one(), L.sub(i * mt, l * kt, mt, kt), R.sub(l * kt, j * nt, kt, nt),
+             D.sub(i * mt, j * nt, mt, nt), depth, Arena{});
+}
+
 }  // namespace swmm

@@ -75,6 +75,10 @@ struct Exec {
   void leaf(Scalar alpha, bool acc, Scalar beta, View L, View R, View D);
   // Algorithm 2 (IPMM)
   void ipmm(View L, View R, View D, int depth, int64_t cutoff, Kind acc_kind);
+  // Algorithm 1 (IP0vMM): D <- alpha L R for n < m, n <= k, n | m, n | k
+  void ip0vmm(Scalar alpha, View L, View R, View D, int depth);
+  // Section 7.2: D <- alpha L R + beta D by t x t blocks of D
+  void tblock(Scalar alpha, Scalar beta, View L, View R, View D, int t, int depth, Kind acc_kind);
 
  private:
   void fused_level(Scalar alpha, bool acc, Scalar beta, View L, View R, View D);

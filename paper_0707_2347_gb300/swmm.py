@@ -20,11 +20,11 @@ OK, EINVAL, ENOMEM, EUNSUPPORTED, ECUDA, ETIMEOUT = range(6)
 MODP, FP32 = 0, 1
 # schedules (paper table numbers)
 CLASSICAL, T1_DHSS, T2_HLJJTT, T3_IP, T4_OVL, T5_OVR = 0, 1, 2, 3, 4, 5
-T6_ACLR, T7_ACCR, T8_ACR, T9_ACC, IPMM, T4M_OVL = 6, 7, 8, 9, 10, 11
+T6_ACLR, T7_ACCR, T8_ACR, T9_ACC, IPMM, T4M_OVL, IP0VMM, TBLOCK = 6, 7, 8, 9, 10, 11, 12, 13
 AUTO = -1
 SCHED_NAMES = {CLASSICAL: "classical", T1_DHSS: "T1", T2_HLJJTT: "T2", T3_IP: "IP", T4_OVL: "OvL",
                T5_OVR: "OvR", T6_ACLR: "AcLR", T7_ACCR: "AccR", T8_ACR: "AcR", T9_ACC: "Acc",
-               IPMM: "IPMM", T4M_OVL: "OvLM"}
+               IPMM: "IPMM", T4M_OVL: "OvLM", IP0VMM: "IP0vMM", TBLOCK: "Sec7.2"}
 # flags
 FLAG_UNFUSED, FLAG_SIMT_LEAF, FLAG_TIMING, FLAG_GRAPH, FLAG_SERIAL = 1, 2, 4, 8, 16
 
@@ -38,7 +38,7 @@ class SwmmError(RuntimeError):
 class _Opts(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("p", ctypes.c_uint32), ("sched", ctypes.c_int32),
                 ("depth", ctypes.c_int32), ("flags", ctypes.c_uint32), ("ipmm_cutoff", ctypes.c_int32),
-                ("ipmm_acc", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("ipmm_acc", ctypes.c_int32), ("tblock", ctypes.c_int32)]
 
 
 class _Stats(ctypes.Structure):
@@ -120,9 +120,11 @@ class Opts:
     flags: int = 0
     ipmm_cutoff: int = 0
     ipmm_acc: int = 0
+    tblock: int = 0
 
     def c(self) -> _Opts:
-        return _Opts(self.mode, self.p, self.sched, self.depth, self.flags, self.ipmm_cutoff, self.ipmm_acc, 0)
+        return _Opts(self.mode, self.p, self.sched, self.depth, self.flags, self.ipmm_cutoff, self.ipmm_acc,
+                     self.tblock)
 
 
 def autotune(m, k, n, mode=MODP, p=65521):

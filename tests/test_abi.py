@@ -88,6 +88,18 @@ def test_planner_rejects_bad_arguments(S):
     assert plan(S, 64, 64, 32, sched=10, depth=1)[0] == S.EINVAL  # IPMM needs m = n
     assert plan(S, 64, 64, 64, sched=3, depth=1, mode=7)[0] == S.EINVAL
     assert plan(S, 128, 64, 32, sched=3, depth=1)[0] == S.EINVAL  # IP needs k = n <= m
+    # Algorithm 1 needs n < m, n <= k, n dividing m and k
+    assert plan(S, 256, 256, 256, sched=S.IP0VMM, depth=1)[0] == S.EINVAL
+    assert plan(S, 512, 128, 256, sched=S.IP0VMM, depth=1)[0] == S.EINVAL
+    assert plan(S, 768, 512, 256, sched=S.IP0VMM, depth=1)[0] == 0
+    assert plan(S, 640, 512, 256, sched=S.IP0VMM, depth=1)[0] == S.EINVAL
+
+
+def test_planner_ip0vmm_needs_no_memory(S):
+    for depth, unfused in [(1, True), (2, True), (3, False)]:
+        rc, paper, planned = plan(S, 2048, 1536, 512, sched=S.IP0VMM, depth=depth,
+                                  flags=S.FLAG_UNFUSED if unfused else 0)
+        assert rc == 0 and paper == planned == 0
 
 
 def test_autotune_choices(S):
@@ -105,3 +117,34 @@ def test_planner_peeling_odd_sizes(S):
     # odd dimensions are peeled: the recursion continues on the even core
     rc, paper, planned = plan(S, 1001, 1001, 1001, sched=9, depth=3, flags=S.FLAG_UNFUSED)
     assert rc == 0 and planned == paper == 2 * (500 ** 2 + 250 ** 2 + 125 ** 2)
+
+
+@pytest.mark.parametrize("t,n", [(2, 1024), (3, 768), (4, 1024)])
+@pytest.mark.parametrize("base", ["T2", "Acc"])
+def test_planner_tblock_memory(S, t, n, base):
+    """Section 7.2: the temporaries of one block call, (n/t)^2 with Table 2
+    and 2 (n/t)^2 / 3 with Table 9 (Table 10), summed over the levels run."""
+    acc = S.T9_ACC if base == "Acc" else 0
+    b = n // t
+    rc, paper, planned = plan(S, n, n, n, sched=S.TBLOCK, tblock=t, ipmm_acc=acc, depth=3, flags=S.FLAG_UNFUSED)
+    assert rc == 0 and planned == paper == counts.mem_depth(base, b, 3)
+    # the fused last level needs no temporaries of its own
+    rc, paper, planned = plan(S, n, n, n, sched=S.TBLOCK, tblock=t, ipmm_acc=acc, depth=3)
+    assert rc == 0 and planned == paper == counts.mem_depth(base, b, 2)
+
+
+def test_planner_tblock_table10_leading_terms(S):
+    # full recursion on 2^j blocks: n^2/4 (t = 2) and n^2/9 (t = 3) less the 1/b^2 tail of Lemma 1
+    for t, n in [(2, 256), (3, 192)]:
+        b = n // t
+        levels = b.bit_length() - 1
+        rc, paper, planned = plan(S, n, n, n, sched=S.TBLOCK, tblock=t, depth=levels, flags=S.FLAG_UNFUSED)
+        assert rc == 0 and planned == paper == b * b - 1
+
+
+def test_planner_tblock_rejects(S):
+    assert plan(S, 1000, 1000, 1000, sched=S.TBLOCK, tblock=3, depth=1)[0] == S.EINVAL  # 3 does not divide 1000
+    assert plan(S, 512, 256, 512, sched=S.TBLOCK, tblock=2, ipmm_acc=S.T9_ACC, depth=1)[0] == S.EINVAL
+    assert plan(S, 512, 256, 512, sched=S.TBLOCK, tblock=2, depth=1)[0] == 0
+    assert plan(S, 512, 512, 512, sched=S.TBLOCK, tblock=1, depth=1)[0] == S.EINVAL
+

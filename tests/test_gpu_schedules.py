@@ -159,3 +159,60 @@ def test_invalid_arguments(handle):
         handle.mul(dA, dB, dC, S.Opts(mode=S.MODP, p=1, sched=S.T1_DHSS, depth=1))
     with pytest.raises(S.SwmmError):
         handle.muladd(1, dA, dB, 1, dC, S.Opts(mode=S.MODP, p=p, sched=S.T3_IP, depth=1))
+
+
+@pytest.mark.parametrize("m,k,n,depth", [(1024, 1024, 512, 2), (2048, 1536, 512, 3), (1536, 512, 256, 1),
+                                         (768, 768, 256, 2)])
+@pytest.mark.parametrize("p", [251, 65521])
+@pytest.mark.parametrize("unfused", [False, True])
+def test_ip0vmm(handle, m, k, n, depth, p, unfused):
+    """Algorithm 1: C <- alpha A B overwriting A only, no extra memory."""
+    A, B, C = modp_inputs(m, k, n, p, tag=5)
+    o = S.Opts(mode=S.MODP, p=p, sched=S.IP0VMM, depth=depth, flags=S.FLAG_UNFUSED if unfused else 0)
+    dA, dB, dC = dev(A), dev(B), dev(C)
+    handle.mul_inplace(dA, dB, dC, o, alpha=7)
+    handle.sync()
+    assert np.array_equal(host(dC), classical.muladd_modp(7, A, B, 0, C, p))
+    assert np.array_equal(host(dB), B)
+    st = handle.stats()
+    assert st["plan_extra_elems"] == 0 and st["workspace_bytes"] == 0
+
+
+def test_ip0vmm_fp32(handle):
+    m, k, n = 2048, 1024, 512
+    A, B, C = fp_inputs(m, k, n, tag=4)
+    dA, dB, dC = dev(A), dev(B), dev(C)
+    handle.mul_inplace(dA, dB, dC, S.Opts(mode=S.FP32, sched=S.IP0VMM, depth=2))
+    handle.sync()
+    err = probes.fp_error(host(dC), classical.mul_f64(A, B), A, B)["max_rel"]
+    assert err <= probes.fp_bound(k), err
+
+
+@pytest.mark.parametrize("t,n,depth", [(2, 1024, 3), (3, 768, 2), (4, 1024, 1)])
+@pytest.mark.parametrize("base", [0, S.T9_ACC], ids=["T2", "Acc"])
+@pytest.mark.parametrize("unfused", [False, True])
+def test_tblock(handle, t, n, depth, base, unfused):
+    """Section 7.2: C <- alpha A B + beta C by t x t blocks of accumulating
+    Winograd calls; inputs read-only; one block call's temporaries."""
+    p = 65521
+    A, B, C = modp_inputs(n, n, n, p, tag=t)
+    o = S.Opts(mode=S.MODP, p=p, sched=S.TBLOCK, depth=depth, tblock=t, ipmm_acc=base,
+               flags=S.FLAG_UNFUSED if unfused else 0)
+    dA, dB, dC = dev(A), dev(B), dev(C)
+    handle.muladd(3, dA, dB, 5, dC, o)
+    handle.sync()
+    assert np.array_equal(host(dC), classical.muladd_modp(3, A, B, 5, C, p))
+    assert np.array_equal(host(dA), A) and np.array_equal(host(dB), B)
+    st = handle.stats()
+    lv = depth if unfused else depth - 1
+    assert st["plan_extra_elems"] == st["paper_extra_elems"] == counts.mem_depth("Acc" if base else "T2", n // t, lv)
+
+
+def test_tblock_rectangular_fp32(handle):
+    m, k, n = 1536, 1024, 768
+    A, B, C = fp_inputs(m, k, n, tag=6)
+    dC = dev(C)
+    handle.muladd(1.0, dev(A), dev(B), 1.0, dC, S.Opts(mode=S.FP32, sched=S.TBLOCK, depth=2, tblock=2))
+    handle.sync()
+    err = probes.fp_error(host(dC), classical.muladd_f64(1.0, A, B, 1.0, C), A, B)["max_rel"]
+    assert err <= probes.fp_bound(k), err
