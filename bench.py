@@ -63,8 +63,8 @@ WORKLOADS = {
                      hi=6144),
     "t1_16384_p251": dict(desc="C<-AB over Z/251, 16384^2, Table 1 depth 2", m=16384, k=16384, n=16384, mode=MODP,
                           p=251, sched=T1, depth=2, entry="mul"),
-    "fp32_t9_8192": dict(desc="C<-AB+C FP32 mode (3xbf16), 8192^2, Table 9 depth 2", m=8192, k=8192, n=8192,
-                         mode=FP32, p=0, sched=T9, depth=2, entry="muladd"),
+    "fp32_t9_8192": dict(desc="C<-AB+C FP32 mode (3 fp16 split products), 8192^2, Table 9 depth 2",
+                         m=8192, k=8192, n=8192, mode=FP32, p=0, sched=T9, depth=2, entry="muladd"),
     "t9_32768_p65521": dict(desc="C<-AB+C over Z/65521, 32768^2, Table 9 (Acc) depth 2, fused last level",
                             m=32768, k=32768, n=32768, mode=MODP, p=65521, sched=T9, depth=2, entry="muladd"),
     "tblock2_16384_p65521": dict(desc="C<-AB+C over Z/65521, 16384^2, Section 7.2 t=2 blocks by Table 9, depth 1",
@@ -74,7 +74,8 @@ WORKLOADS = {
                                         m=16384, k=8192, n=4096, mode=MODP, p=251, sched=IP0VMM, depth=2,
                                         entry="inplace"),
     # configs[3]: FP32 mode error and speed per depth
-    "fp32_sweep": dict(desc="C<-AB+C FP32 mode (3xbf16), n in {4096, 8192, 16384}, Table 9 depth 1-4 vs classical",
+    "fp32_sweep": dict(desc="C<-AB+C FP32 mode (3 fp16 split products), n in {4096, 8192, 16384}, "
+                            "Table 9 depth 1-4 vs classical",
                        m=16384, k=16384, n=16384, mode=FP32, p=0, sched=T9, depth=0, entry="sweep",
                        ns=(4096, 8192, 16384), depths=(1, 2, 3, 4)),
 }
@@ -261,7 +262,7 @@ def run_sweep(args, w, S, h, torch, dev, rank):
     line = {
         "metric": "effective GOP/s (2mnk/t)", "value": head["gops"], "unit": "GOP/s", "n_gpus": 1,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms"], "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32 (3xbf16)", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 (3 fp16 split products)", "data": "synthetic",
         "config": {"workload": w["desc"], "value_is": f"n={head['n']} depth 2",
                    "l2": "inputs > 129 MB L2, no flush", "parallelism": "replicas x1"},
         "sweep": rows,
@@ -332,7 +333,7 @@ def run_batch(args, w, S, h, torch, dev, dist, world, rank):
     line = {
         "metric": "effective GOP/s (2mnk/t)", "value": round(value, 2), "unit": "GOP/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True,
-        "scaling": "strong", "vs_baseline": None, "dtype": "i32 mod p (fp16 limbs) / f32 (3xbf16)",
+        "scaling": "strong", "vs_baseline": None, "dtype": "i32 mod p (fp16 limbs) / f32 (3 fp16 split products)",
         "data": "synthetic (device generator)",
         "config": {"workload": w["desc"], "problems": len(shapes), "sum_2mnk": total, "this_rank": len(mine),
                    "autotuner_picks_rank0": picks, "l2": "operands far larger than L2, no flush",
@@ -462,7 +463,7 @@ def main():
         "metric": "effective GOP/s (2mnk/t)", "value": round(value, 2), "unit": "GOP/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": "i32 mod p (fp16 limbs, fp32 accum)" if mode == MODP else "f32 (3xbf16)",
+        "dtype": "i32 mod p (fp16 limbs, fp32 accum)" if mode == MODP else "f32 (3 fp16 split products)",
         "data": "synthetic",
         "config": {"workload": w["desc"], "m": m, "k": k, "n": n, "p": p, "schedule": S.SCHED_NAMES[w["sched"]],
                    "depth": w["depth"], "l2": f"inputs {3 * m * n * 4 / 1e6:.0f} MB > 129 MB L2, no flush",

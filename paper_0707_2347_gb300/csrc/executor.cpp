@@ -75,6 +75,38 @@ char *Exec::next_stage() {
   return stage + (stage_turn++ % stage_slots) * slot;
 }
 
+// FP32 mode: zero the two amax words at the head of a staging slot, then
+// max |x| over the A-side and the B-side sources of the coming packs.
+void Exec::fp32_amax(uint32_t *amax, const View *a, int na, const View *b, int nb) {
+  const Rect rh = rect_bytes(amax, 2 * sizeof(uint32_t));
+  cudaStream_t st = op_begin({}, {rh});
+  check(cudaMemsetAsync(amax, 0, 2 * sizeof(uint32_t), st), "amax reset");
+  op_end();
+  AmaxArgs g;
+  std::memset(&g, 0, sizeof(g));
+  std::vector<Rect> rd;
+  for (int q = 0; q < na; ++q) {
+    g.src[0][q] = a[q].ptr;
+    g.ld[0][q] = a[q].ld;
+    rd.push_back(rect_of(a[q]));
+  }
+  for (int q = 0; q < nb; ++q) {
+    g.src[1][q] = b[q].ptr;
+    g.ld[1][q] = b[q].ld;
+    rd.push_back(rect_of(b[q]));
+  }
+  g.nsrc[0] = na;
+  g.nsrc[1] = nb;
+  g.rows[0] = na ? a[0].rows : 0;
+  g.cols[0] = na ? a[0].cols : 0;
+  g.rows[1] = nb ? b[0].rows : 0;
+  g.cols[1] = nb ? b[0].cols : 0;
+  g.amax = amax;
+  st = op_begin(rd, {rh});
+  check(launch_amax(g, st), "amax");
+  op_end();
+}
+
 void Exec::add(View d, View s1, View s2, Scalar c1, Scalar c2) {
   add_elems += d.rows * d.cols;
   ++ew_launches;
@@ -152,13 +184,16 @@ void Exec::leaf(Scalar alpha, bool acc, Scalar beta, View L, View R, View D) {
   const int pl = planes_of(mode), bn = bn_of(mode);
   const int64_t Mp = rup(m, kBM), Np = rup(n, bn), Kp = rup(k, kBK);
   const int64_t abytes = rup(pl * Mp * Kp * 2, 1024), bbytes = rup(pl * Np * Kp * 2, 1024);
-  stage_need = std::max(stage_need, abytes + bbytes);
-  ew_launches += 2;
+  const int64_t hdr = fp32 ? 1024 : 0;  // FP32 mode: the operands' amax words
+  stage_need = std::max(stage_need, hdr + abytes + bbytes);
+  ew_launches += fp32 ? 3 : 2;
   if (dry) return;
   char *stg = next_stage();
-  uint16_t *Ap = reinterpret_cast<uint16_t *>(stg);
-  uint16_t *Bp = reinterpret_cast<uint16_t *>(stg + abytes);
-  const Rect ra = rect_bytes(Ap, abytes), rb = rect_bytes(Bp, bbytes);
+  uint32_t *amax = fp32 ? reinterpret_cast<uint32_t *>(stg) : nullptr;
+  uint16_t *Ap = reinterpret_cast<uint16_t *>(stg + hdr);
+  uint16_t *Bp = reinterpret_cast<uint16_t *>(stg + hdr + abytes);
+  const Rect ra = rect_bytes(Ap, abytes), rb = rect_bytes(Bp, bbytes), rh = rect_bytes(stg, 8);
+  if (fp32) fp32_amax(amax, &L, 1, &R, 1);
   PackArgs pa;
   std::memset(&pa, 0, sizeof(pa));
   pa.src[0] = L.ptr;
@@ -174,7 +209,9 @@ void Exec::leaf(Scalar alpha, bool acc, Scalar beta, View L, View R, View D) {
   pa.transpose = 0;
   pa.p = p;
   pa.barrett = p ? (uint32_t)(0x100000000ull / p) : 0;
-  cudaStream_t st = op_begin({rect_of(L)}, {ra});
+  pa.amax = amax;
+  pa.terms = 1;
+  cudaStream_t st = op_begin({rect_of(L), rh}, {ra});
   check(launch_pack(pa, mode, st), "pack A");
   op_end();
   pa.src[0] = R.ptr;
@@ -185,7 +222,8 @@ void Exec::leaf(Scalar alpha, bool acc, Scalar beta, View L, View R, View D) {
   pa.prow_pad = (int)Np;
   pa.pcol_pad = (int)Kp;
   pa.transpose = 1;
-  st = op_begin({rect_of(R)}, {rb});
+  pa.amax = amax ? amax + 1 : nullptr;
+  st = op_begin({rect_of(R), rh}, {rb});
   check(launch_pack(pa, mode, st), "pack B");
   op_end();
   Product &pr = P.prod[0];
@@ -209,7 +247,9 @@ void Exec::leaf(Scalar alpha, bool acc, Scalar beta, View L, View R, View D) {
   pr.tile_begin = 0;
   P.nprod = 1;
   P.total_tiles = pr.tiles_m * pr.tiles_n;
-  st = op_begin({ra, rb}, {rect_of(D)});
+  P.amax = amax;
+  P.terms_a = P.terms_b = 1;
+  st = op_begin({ra, rb, rh}, {rect_of(D)});
   if (timing) timing->begin(st);
   check(launch_gemm_tc(P, mode, num_sms, st), "leaf gemm");
   if (timing) timing->end(st, 2.0 * m * n * k * limb_products());
@@ -310,11 +350,16 @@ void Exec::fused_level(Scalar alpha, bool acc, Scalar beta, View L, View R, View
     const int pl = planes_of(mode), bn = bn_of(mode);
     const int64_t Mp = rup(hm, kBM), Np = rup(hn, bn), Kp = rup(hk, kBK);
     const int64_t abytes = rup(pl * Mp * Kp * 2, 1024), bbytes = rup(pl * Np * Kp * 2, 1024);
-    stage_need = std::max(stage_need, 7 * (abytes + bbytes));
-    ew_launches += 2;
+    const int64_t hdr = fp32 ? 1024 : 0;  // FP32 mode: the operands' amax words
+    stage_need = std::max(stage_need, hdr + 7 * (abytes + bbytes));
+    ew_launches += fp32 ? 3 : 2;
     if (!dry) {
-      char *stg = next_stage();
+      char *base = next_stage();
+      uint32_t *amax = fp32 ? reinterpret_cast<uint32_t *>(base) : nullptr;
+      char *stg = base + hdr;
       const Rect ra = rect_bytes(stg, 7 * abytes), rb = rect_bytes(stg + 7 * abytes, 7 * bbytes);
+      const Rect rh = rect_bytes(base, 8);
+      if (fp32) fp32_amax(amax, Lq, 4, Rq, 4);
       PackArgs pa, pb;
       std::memset(&pa, 0, sizeof(pa));
       std::memset(&pb, 0, sizeof(pb));
@@ -350,10 +395,14 @@ void Exec::fused_level(Scalar alpha, bool acc, Scalar beta, View L, View R, View
       pb.pcol_pad = (int)Kp;
       pb.transpose = 1;
       pb.p = p;
-      cudaStream_t st = op_begin({rect_of(L)}, {ra});
+      // |S4|, |T4| <= 4 max|quadrant entry|: the largest sums of the sets
+      pa.amax = amax;
+      pb.amax = amax ? amax + 1 : nullptr;
+      pa.terms = pb.terms = 4;
+      cudaStream_t st = op_begin({rect_of(L), rh}, {ra});
       check(launch_pack(pa, mode, st), "fused pack A");
       op_end();
-      st = op_begin({rect_of(R)}, {rb});
+      st = op_begin({rect_of(R), rh}, {rb});
       check(launch_pack(pb, mode, st), "fused pack B");
       op_end();
       int tiles = 0;
@@ -387,7 +436,9 @@ void Exec::fused_level(Scalar alpha, bool acc, Scalar beta, View L, View R, View
       }
       P.nprod = 7;
       P.total_tiles = tiles;
-      st = op_begin({ra, rb}, {rect_of(D)});
+      P.amax = amax;
+      P.terms_a = P.terms_b = 4;
+      st = op_begin({ra, rb, rh}, {rect_of(D)});
       if (timing) timing->begin(st);
       check(launch_gemm_tc(P, mode, num_sms, st), "fused gemm");
       if (timing) timing->end(st, 7 * 2.0 * hm * hn * hk * limb_products());

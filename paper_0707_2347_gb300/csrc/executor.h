@@ -89,6 +89,7 @@ struct Exec {
   cudaStream_t op_begin(const std::vector<Rect> &rd, const std::vector<Rect> &wr);
   void op_end();
   char *next_stage();
+  void fp32_amax(uint32_t *amax, const View *a, int na, const View *b, int nb);
   void scale(View d, bool keep, Scalar beta);  // d <- beta d, or 0
   void check(cudaError_t e, const char *what);
   View alloc_tmp(int64_t rows, int64_t cols);

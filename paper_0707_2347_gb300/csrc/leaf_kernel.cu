@@ -1,34 +1,33 @@
 // Leaf products of the Strassen-Winograd recursion on the sm_103a tensor
 // cores (tcgen05 MMA, accumulators in tensor memory, operands staged by TMA).
 //
-// Two kernels:
-//
 // pack_* : operand staging.  One launch reads the four quadrants of a
 //   Winograd level's operand once and writes the seven signed combinations
-//   the level multiplies (A11, A12, A22, S1..S4 or B11, B21, B22, T1..T4,
-//   Section 2), already converted to the tensor-core number format, so the
-//   pre-additions never exist as int32/float blocks in HBM.  Exact
+//   the level multiplies (A11, A12, S4, A22, S1, S2, S3 or B11, B21, B22,
+//   T4, T1, T2, T3, Section 2), already in the tensor-core number format, so
+//   the pre-additions never exist as int32/float blocks in HBM.  Exact
 //   arithmetic over Z/pZ on the floating-point tensor pipe (sm_103a has no
 //   integer tcgen05 MMA): each entry is brought to a centred representative
 //   and split into fp16 limbs of magnitude <= 128 (one limb when p <= 256,
 //   x = 256 h + l when p < 2^16); fp16 holds these integers exactly.  FP32
-//   mode splits each float into bf16 hi + lo.
+//   mode scales each operand by a power of two (from its max |x|, amax_*)
+//   and splits x s into fp16 hi + lo.
 //
 // gemm_* : persistent warp-specialised GEMM over up to seven products (one
 //   fused Winograd level, or one classical leaf).  Warp 0 issues TMA loads
 //   of 128-byte-swizzled K-major tiles into a shared-memory ring, warp 1
 //   allocates tensor memory and issues tcgen05.mma from one thread, warps
-//   2-5 drain the accumulators.  Limb products are <= 2^14 in magnitude, so
+//   2-9 drain the accumulators.  Limb products are <= 2^14 in magnitude, so
 //   an fp32 accumulator summing at most 1024 of them stays below 2^24 and is
 //   exact; longer K is reduced mod p in place in tensor memory every 960 K.
 //   The epilogue recombines 2^16 hh + 2^8 (hl + lh) + ll mod p with exact
-//   fp32 operations, applies alpha / beta, and either stores (one target)
-//   or adds its signed contribution into up to four float targets with
-//   vector reductions (the post-additions U1..U7 of a fused level).
+//   fp32 operations (FP32 mode: hi hi + hi lo + lo hi, unscaled), applies
+//   alpha / beta, and either stores (one target) or adds its signed
+//   contribution into up to four targets with TMA reductions (the
+//   post-additions U1..U7 of a fused level).
 // Every mbarrier wait is bounded (globaltimer); on expiry the kernel sets the
 // error word and unwinds, freeing its tensor memory.
 #include <cstdint>
-#include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
 #include "swmm_internal.h"
@@ -70,7 +69,7 @@ __device__ __forceinline__ uint32_t red4p(uint32_t x, uint32_t p) {
 
 // 8 combined values -> plane 0 and plane 1 (16 bytes each)
 template <int MODE>
-__device__ __forceinline__ void convert8(const uint32_t (&x)[8], uint32_t p, uint4 &o0, uint4 &o1) {
+__device__ __forceinline__ void convert8(const uint32_t (&x)[8], uint32_t p, float fs, uint4 &o0, uint4 &o1) {
   uint32_t w0[4], w1[4];
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
@@ -83,13 +82,14 @@ __device__ __forceinline__ void convert8(const uint32_t (&x)[8], uint32_t p, uin
       w0[j] = offset_to_h2(prmt(u0, u1, 0x4400u) & 0x00FF00FFu);
       w1[j] = 0;
     } else {
-      float a = __uint_as_float(x[2 * j]), b = __uint_as_float(x[2 * j + 1]);
-      __nv_bfloat162 hi = __floats2bfloat162_rn(a, b);
-      uint32_t hb = *reinterpret_cast<uint32_t *>(&hi);
-      float ha = __uint_as_float(hb << 16), hbf = __uint_as_float(hb & 0xFFFF0000u);
-      __nv_bfloat162 lo = __floats2bfloat162_rn(a - ha, b - hbf);
-      w0[j] = hb;
-      w1[j] = *reinterpret_cast<uint32_t *>(&lo);
+      // scaled value v = x fs (|v| < 2^14): hi = fp16(v), lo = fp16(v - hi);
+      // hi + lo carries 22 significant bits of v
+      const float a = __uint_as_float(x[2 * j]) * fs, b = __uint_as_float(x[2 * j + 1]) * fs;
+      const __half2 hi = __floats2half2_rn(a, b);
+      const float2 hf = __half22float2(hi);
+      const __half2 lo = __floats2half2_rn(a - hf.x, b - hf.y);
+      w0[j] = *reinterpret_cast<const uint32_t *>(&hi);
+      w1[j] = *reinterpret_cast<const uint32_t *>(&lo);
     }
   }
   o0 = make_uint4(w0[0], w0[1], w0[2], w0[3]);
@@ -133,7 +133,7 @@ __device__ __forceinline__ uint32_t combine(const PackArgs &a, int o, const uint
 // write output o of one 8-element unit: plane 0 and plane 1
 template <int MODE>
 __device__ __forceinline__ void emit_unit(const PackArgs &a, int o, const uint32_t (&v)[kMaxSrc][8], uint16_t *dst,
-                                          int64_t plane) {
+                                          int64_t plane, float fs) {
   uint32_t x[8];
 #pragma unroll
   for (int e = 0; e < 8; ++e) {
@@ -143,16 +143,16 @@ __device__ __forceinline__ void emit_unit(const PackArgs &a, int o, const uint32
     x[e] = combine<MODE>(a, o, w, a.p);
   }
   uint4 o0, o1;
-  convert8<MODE>(x, a.p, o0, o1);
+  convert8<MODE>(x, a.p, fs, o0, o1);
   *reinterpret_cast<uint4 *>(dst) = o0;
   if (MODE != MODE_MODP1) *reinterpret_cast<uint4 *>(dst + plane) = o1;
 }
 
 // one 8-element unit of already combined values -> plane 0 and plane 1
 template <int MODE>
-__device__ __forceinline__ void emit8(const uint32_t (&x)[8], uint32_t p, uint16_t *dst, int64_t plane) {
+__device__ __forceinline__ void emit8(const uint32_t (&x)[8], uint32_t p, float fs, uint16_t *dst, int64_t plane) {
   uint4 o0, o1;
-  convert8<MODE>(x, p, o0, o1);
+  convert8<MODE>(x, p, fs, o0, o1);
   *reinterpret_cast<uint4 *>(dst) = o0;
   if (MODE != MODE_MODP1) *reinterpret_cast<uint4 *>(dst + plane) = o1;
 }
@@ -175,44 +175,44 @@ __device__ __forceinline__ uint32_t lin_add(uint32_t x, uint32_t y, uint32_t p) 
 // (X11, X12, X21, X22) for the Winograd sets
 template <int MODE, int SET>
 __device__ __forceinline__ void emit_all(const PackArgs &a, const uint32_t (&v)[kMaxSrc][8], int64_t off,
-                                         int64_t plane) {
+                                         int64_t plane, float fs) {
   const uint32_t p = a.p;
   if (SET == PACK_WINOGRAD_A) {
     uint32_t s1[8], s2[8], t[8];
-    emit8<MODE>(v[0], p, a.out[0] + off, plane);  // A11
-    emit8<MODE>(v[1], p, a.out[1] + off, plane);  // A12
+    emit8<MODE>(v[0], p, fs, a.out[0] + off, plane);  // A11
+    emit8<MODE>(v[1], p, fs, a.out[1] + off, plane);  // A12
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
       s1[e] = lin_add<MODE>(v[2][e], v[3][e], p);  // S1 = A21 + A22
       s2[e] = lin_sub<MODE>(s1[e], v[0][e], p);    // S2 = S1 - A11
       t[e] = lin_sub<MODE>(v[1][e], s2[e], p);     // S4 = A12 - S2
     }
-    emit8<MODE>(t, p, a.out[2] + off, plane);
-    emit8<MODE>(v[3], p, a.out[3] + off, plane);  // A22
-    emit8<MODE>(s1, p, a.out[4] + off, plane);
-    emit8<MODE>(s2, p, a.out[5] + off, plane);
+    emit8<MODE>(t, p, fs, a.out[2] + off, plane);
+    emit8<MODE>(v[3], p, fs, a.out[3] + off, plane);  // A22
+    emit8<MODE>(s1, p, fs, a.out[4] + off, plane);
+    emit8<MODE>(s2, p, fs, a.out[5] + off, plane);
 #pragma unroll
     for (int e = 0; e < 8; ++e) t[e] = lin_sub<MODE>(v[0][e], v[2][e], p);  // S3 = A11 - A21
-    emit8<MODE>(t, p, a.out[6] + off, plane);
+    emit8<MODE>(t, p, fs, a.out[6] + off, plane);
   } else if (SET == PACK_WINOGRAD_B) {
     uint32_t t1[8], t2[8], t[8];
-    emit8<MODE>(v[0], p, a.out[0] + off, plane);  // B11
-    emit8<MODE>(v[2], p, a.out[1] + off, plane);  // B21
-    emit8<MODE>(v[3], p, a.out[2] + off, plane);  // B22
+    emit8<MODE>(v[0], p, fs, a.out[0] + off, plane);  // B11
+    emit8<MODE>(v[2], p, fs, a.out[1] + off, plane);  // B21
+    emit8<MODE>(v[3], p, fs, a.out[2] + off, plane);  // B22
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
       t1[e] = lin_sub<MODE>(v[1][e], v[0][e], p);  // T1 = B12 - B11
       t2[e] = lin_sub<MODE>(v[3][e], t1[e], p);    // T2 = B22 - T1
       t[e] = lin_sub<MODE>(t2[e], v[2][e], p);     // T4 = T2 - B21
     }
-    emit8<MODE>(t, p, a.out[3] + off, plane);
-    emit8<MODE>(t1, p, a.out[4] + off, plane);
-    emit8<MODE>(t2, p, a.out[5] + off, plane);
+    emit8<MODE>(t, p, fs, a.out[3] + off, plane);
+    emit8<MODE>(t1, p, fs, a.out[4] + off, plane);
+    emit8<MODE>(t2, p, fs, a.out[5] + off, plane);
 #pragma unroll
     for (int e = 0; e < 8; ++e) t[e] = lin_sub<MODE>(v[3][e], v[1][e], p);  // T3 = B22 - B12
-    emit8<MODE>(t, p, a.out[6] + off, plane);
+    emit8<MODE>(t, p, fs, a.out[6] + off, plane);
   } else {
-    for (int o = 0; o < a.nout; ++o) emit_unit<MODE>(a, o, v, a.out[o] + off, plane);
+    for (int o = 0; o < a.nout; ++o) emit_unit<MODE>(a, o, v, a.out[o] + off, plane, fs);
   }
 }
 
@@ -223,6 +223,7 @@ template <int MODE, int SET>
 __global__ void __launch_bounds__(256) pack_rows_kernel(const __grid_constant__ PackArgs a) {
   const int64_t units = (int64_t)a.prow_pad * (a.pcol_pad / 8);
   const int64_t plane = (int64_t)a.prow_pad * a.pcol_pad;
+  const float fs = MODE == MODE_FP32 ? fp16_scale(*a.amax, a.terms) : 1.f;
   for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < units; u += (int64_t)gridDim.x * blockDim.x) {
     const int r = (int)(u / (a.pcol_pad / 8));
     const int c0 = (int)(u - (int64_t)r * (a.pcol_pad / 8)) * 8;
@@ -248,7 +249,7 @@ __global__ void __launch_bounds__(256) pack_rows_kernel(const __grid_constant__ 
         for (int e = 0; e < 8; ++e) v[q][e] = 0;
       }
     }
-    emit_all<MODE, SET>(a, v, (int64_t)r * a.pcol_pad + c0, plane);
+    emit_all<MODE, SET>(a, v, (int64_t)r * a.pcol_pad + c0, plane, fs);
   }
 }
 
@@ -262,6 +263,7 @@ __global__ void __launch_bounds__(256) pack_cols_kernel(const __grid_constant__ 
   const int c0 = blockIdx.x * 64;  // source cols = packed rows (N)
   const int t = threadIdx.x;
   const int64_t plane = (int64_t)a.prow_pad * a.pcol_pad;
+  const float fs = MODE == MODE_FP32 ? fp16_scale(*a.amax, a.terms) : 1.f;
   for (int q = 0; q < a.nsrc; ++q) {
 #pragma unroll
     for (int i = 0; i < 2; ++i) {
@@ -290,7 +292,44 @@ __global__ void __launch_bounds__(256) pack_cols_kernel(const __grid_constant__ 
 #pragma unroll
     for (int e = 0; e < 8; ++e) v[q][e] = q < a.nsrc ? tile[q][pr8 + e][pc] : 0u;
   }
-  emit_all<MODE, SET>(a, v, (int64_t)(c0 + pc) * a.pcol_pad + r0 + pr8, plane);
+  emit_all<MODE, SET>(a, v, (int64_t)(c0 + pc) * a.pcol_pad + r0 + pr8, plane, fs);
+}
+
+// FP32 mode: max |x| over the sources of each side (blockIdx.y), one row per
+// block iteration, 16-byte loads when the view allows them; the block
+// maximum is atomically maxed into amax[side] as float bits (non-negative
+// floats order like their bit patterns).  NaN is ignored, inf propagates.
+__global__ void __launch_bounds__(256) amax_kernel(const __grid_constant__ AmaxArgs a) {
+  const int side = blockIdx.y;
+  const int64_t rows = a.rows[side], cols = a.cols[side];
+  float m = 0.f;
+  for (int q = 0; q < a.nsrc[side]; ++q) {
+    const char *base = a.src[side][q];
+    const int64_t ld = a.ld[side][q];
+    const bool vec = ((uintptr_t)base % 16 == 0) && (ld % 4 == 0) && (cols % 4 == 0);
+    for (int64_t r = blockIdx.x; r < rows; r += gridDim.x) {
+      const float *row = reinterpret_cast<const float *>(base) + r * ld;
+      if (vec) {
+        for (int64_t c = 4 * (int64_t)threadIdx.x; c < cols; c += 4 * (int64_t)blockDim.x) {
+          const float4 v = *reinterpret_cast<const float4 *>(row + c);
+          m = fmaxf(m, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
+        }
+      } else {
+        for (int64_t c = threadIdx.x; c < cols; c += blockDim.x) m = fmaxf(m, fabsf(row[c]));
+      }
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  __shared__ float wm[8];
+  if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    m = threadIdx.x < 8 ? wm[threadIdx.x] : 0.f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (threadIdx.x == 0 && m > 0.f) atomicMax(a.amax + side, __float_as_uint(m));
+  }
 }
 
 // ------------------------------------------------------------ GEMM glue
@@ -449,7 +488,7 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
   d |= (uint64_t)2 << 61;            // 128-byte swizzle
   return d;
 }
-// Instruction descriptor, kind::f16: D fp32, A/B fp16 (fmt 0) or bf16 (1),
+// Instruction descriptor, kind::f16: D fp32, A/B fp16 (fmt 0; 1 would be bf16),
 // K-major, N >> 3 at bit 17, M >> 4 at bit 24.
 __host__ __device__ constexpr uint32_t idesc_f16(int ab_fmt, int M, int N) {
   return (1u << 4) | ((uint32_t)ab_fmt << 7) | ((uint32_t)ab_fmt << 10) | ((uint32_t)(N >> 3) << 17) |
@@ -482,6 +521,7 @@ __device__ __forceinline__ TileInfo decode(const GemmParams &P, int g) {
 struct Epi {
   uint32_t p, m;
   float pf, inv_p;
+  float fsc;  // FP32 mode: alpha / (s_A s_B), undoing the operand scales
   __device__ __forceinline__ float fr(float f) const {  // centred residue, exact |f| <= 2^24
     const float MAGIC = 12582912.0f;                     // 1.5 * 2^23: rint via addition
     float q = __fmaf_rn(f, inv_p, MAGIC) - MAGIC;
@@ -537,7 +577,7 @@ __device__ __forceinline__ void tile_values(const GemmParams &P, const Epi &E, u
     tmem_wait_ld();
 #pragma unroll
     for (int e = 0; e < 16; ++e) {
-      float f = P.alpha_f * (a[e] + b[e]);
+      float f = E.fsc * (a[e] + b[e]);
       if (P.epilogue == EPI_REDUCE && sign < 0) f = -f;
       v[e] = __float_as_uint(f);
     }
@@ -649,7 +689,7 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_kernel(const __grid_constant
   } else if (warp == 1) {
     // ================================ MMA issuer ================================
     if (lane == 0) {
-      const uint32_t fmt = MODE == MODE_FP32 ? 1 : 0;
+      const uint32_t fmt = 0;  // fp16 operands in every mode
       const uint32_t id256 = idesc_f16(fmt, kBM, 256);
       const uint32_t id128 = idesc_f16(fmt, kBM, 128);
       int stage = 0;
@@ -729,6 +769,9 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_kernel(const __grid_constant
     E.m = P.barrett;
     E.pf = (float)P.p;
     E.inv_p = P.inv_p;
+    E.fsc = MODE == MODE_FP32
+                ? P.alpha_f / (fp16_scale(P.amax[0], P.terms_a) * fp16_scale(P.amax[1], P.terms_b))
+                : 0.f;
     uint32_t tcount = 0, dcount = 0, cphase = 0;
     for (int g = blockIdx.x; g < P.total_tiles; g += gridDim.x, ++tcount) {
       const TileInfo ti = decode<BN>(P, g);
@@ -972,6 +1015,14 @@ static cudaError_t pack_mode(const PackArgs &a, cudaStream_t s) {
   if (a.set == PACK_WINOGRAD_B && quads) return pack_set<MODE, PACK_WINOGRAD_B>(a, s);
   if (a.set != PACK_GENERIC) return cudaErrorInvalidValue;
   return pack_set<MODE, PACK_GENERIC>(a, s);
+}
+
+cudaError_t launch_amax(const AmaxArgs &a, cudaStream_t s) {
+  const int64_t rows = a.rows[0] > a.rows[1] ? a.rows[0] : a.rows[1];
+  if (rows <= 0) return cudaSuccess;
+  dim3 grid((unsigned)(rows < 152 * 4 ? rows : 152 * 4), 2);
+  dev::amax_kernel<<<grid, 256, 0, s>>>(a);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_pack(const PackArgs &a, int mode, cudaStream_t s) {

@@ -1,7 +1,9 @@
 // Internal interfaces shared by the host executor and the CUDA kernels.
 #pragma once
 
+#include <cmath>
 #include <cstdint>
+#include <cstring>
 #include <cuda.h>
 #include <cuda_runtime.h>
 
@@ -59,6 +61,11 @@ struct PackArgs {
   uint32_t p;
   uint32_t barrett;  // floor(2^32 / p)
   int32_t set;       // PACK_GENERIC: coef; PACK_WINOGRAD_A / _B: the Section 2 sums
+  // FP32 mode: max |source| (float bits, written on the device by
+  // launch_amax) and the largest sum of |coef| over the outputs; the pack
+  // scales every value by fp16_scale(*amax, terms) before splitting it.
+  const uint32_t *amax;
+  int32_t terms;
 };
 // Output sets of a pack launch.  The Winograd sets take the four quadrants
 // (X11, X12, X21, X22) and write, in order, A11, A12, S4, A22, S1, S2, S3
@@ -111,7 +118,36 @@ struct GemmParams {
   float inv_p;       // 1/p rounded to float
   int32_t use_beta;  // STORE: read T0 and add beta * T0
   int *err;          // device error word (bounded waits)
+  // FP32 mode: the A-side and B-side amax words and term counts of the
+  // packs, to undo their scales in the epilogue
+  const uint32_t *amax;  // [2]: A side, B side
+  int32_t terms_a, terms_b;
 };
+
+// FP32 mode operand scale: a power of two s with |x s| < 2^14 for every
+// value the pack writes (|x| <= terms * amax), so that hi = fp16(x s) and
+// lo = fp16(x s - hi) stay in fp16's normal range; 1 for a zero or
+// non-finite bound.
+__host__ __device__ inline float fp16_scale(uint32_t amax_bits, int terms) {
+  float a;
+  memcpy(&a, &amax_bits, 4);
+  const float bound = a * (float)terms;
+  if (!(bound > 0.f) || !(bound < 3.0e38f)) return 1.f;
+  int e;
+  frexpf(bound, &e);  // bound < 2^e
+  return ldexpf(1.f, 14 - e);
+}
+
+// max |x| over up to 4 views per side (side 0: A, side 1: B), atomically
+// maxed into amax[side] (float bits; the words must be zeroed first)
+struct AmaxArgs {
+  const char *src[2][kMaxSrc];
+  int64_t ld[2][kMaxSrc];
+  int64_t rows[2], cols[2];
+  int32_t nsrc[2];
+  uint32_t *amax;
+};
+cudaError_t launch_amax(const AmaxArgs &a, cudaStream_t s);
 
 // Encode a 2-D tensor map over a packed buffer (rows x kpad halves).
 bool make_tmap(CUtensorMap *map, const void *base, int64_t rows, int64_t kpad, int box_rows);

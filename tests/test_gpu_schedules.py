@@ -216,3 +216,30 @@ def test_tblock_rectangular_fp32(handle):
     handle.sync()
     err = probes.fp_error(host(dC), classical.muladd_f64(1.0, A, B, 1.0, C), A, B)["max_rel"]
     assert err <= probes.fp_bound(k), err
+
+
+@pytest.mark.parametrize("n,depth", [(2048, 4), (4096, 4)])
+def test_fp32_mode_depth4_within_bound(handle, n, depth):
+    """Four Winograd levels keep the FP32-mode error within 1e-5 n^0.6: the
+    leaves split each scaled operand into fp16 hi + lo (22 bits)."""
+    A, B, C = fp_inputs(n, n, n, tag=9)
+    dC = dev(C)
+    handle.muladd(1.0, dev(A), dev(B), 1.0, dC, S.Opts(mode=S.FP32, sched=S.T9_ACC, depth=depth))
+    handle.sync()
+    idx = np.linspace(0, n - 1, 32).astype(np.int64)
+    ref = A[idx].astype(np.float64) @ B.astype(np.float64) + C[idx].astype(np.float64)
+    err = np.abs(host(dC)[idx] - ref).max() / (np.abs(A).max() * np.abs(B).max())
+    assert err <= probes.fp_bound(n), err
+
+
+def test_fp32_scaling_handles_large_and_small_magnitudes(handle):
+    """Operands far outside fp16's range are scaled by a power of two."""
+    n = 1024
+    A, B, C = fp_inputs(n, n, n, tag=10)
+    for sa, sb in [(1e6, 1e-3), (1e-8, 1e-8), (3e4, 3e4)]:
+        A2, B2 = (A * sa).astype(np.float32), (B * sb).astype(np.float32)
+        dC = dev(C)
+        handle.muladd(1.0, dev(A2), dev(B2), 0.0, dC, S.Opts(mode=S.FP32, sched=S.T9_ACC, depth=2))
+        handle.sync()
+        err = probes.fp_error(host(dC), classical.mul_f64(A2, B2), A2, B2)["max_rel"]
+        assert err <= probes.fp_bound(n), (sa, sb, err)
