@@ -196,8 +196,10 @@ void Exec::leaf(Scalar alpha, bool acc, Scalar beta, View L, View R, View D) {
   if (fp32) fp32_amax(amax, &L, 1, &R, 1);
   PackArgs pa;
   std::memset(&pa, 0, sizeof(pa));
-  pa.src[0] = L.ptr;
-  pa.ld[0] = L.ld;
+  pa.src[0][0] = L.ptr;
+  pa.ld[0][0] = L.ld;
+  pa.tsign[0] = 1;
+  pa.nterm = 1;
   pa.nsrc = 1;
   pa.out[0] = Ap;
   pa.coef[0][0] = 1;
@@ -214,8 +216,8 @@ void Exec::leaf(Scalar alpha, bool acc, Scalar beta, View L, View R, View D) {
   cudaStream_t st = op_begin({rect_of(L), rh}, {ra});
   check(launch_pack(pa, mode, st), "pack A");
   op_end();
-  pa.src[0] = R.ptr;
-  pa.ld[0] = R.ld;
+  pa.src[0][0] = R.ptr;
+  pa.ld[0][0] = R.ld;
   pa.out[0] = Bp;
   pa.rows = (int)k;
   pa.cols = (int)n;
@@ -265,7 +267,12 @@ void Exec::leaf(Scalar alpha, bool acc, Scalar beta, View L, View R, View D) {
 // with S1 = A21 + A22, S2 = S1 - A11, S3 = A11 - A21, S4 = A12 - S2 and
 // T1 = B12 - B11, T2 = B22 - T1, T3 = B22 - B12, T4 = T2 - B21, i.e.
 // C11 = U1, C12 = U5, C21 = U6, C22 = U7.
-void Exec::fused_level(Scalar alpha, bool acc, Scalar beta, View L, View R, View D) {
+bool Exec::fuses(int64_t m, int64_t k, int64_t n, int depth) const {
+  return fused && depth == 1 && m >= 2 && k >= 2 && n >= 2 && m % 2 == 0 && k % 2 == 0 && n % 2 == 0;
+}
+
+void Exec::fused_level(Scalar alpha, bool acc, Scalar beta, const Lin &LL, const Lin &RL, View D) {
+  const View &L = LL.shape(), &R = RL.shape();
   // operand coefficients over (X11, X12, X21, X22)
   static const int8_t acoef[7][4] = {
       {1, 0, 0, 0},    // A11
@@ -290,8 +297,6 @@ void Exec::fused_level(Scalar alpha, bool acc, Scalar beta, View L, View R, View
       {1, 1, 1, 1}, {1, 0, 0, 0}, {0, 1, 0, 0}, {0, 0, -1, 0}, {0, 1, 0, 1}, {0, 1, 1, 1}, {0, 0, 1, 1},
   };
   const int64_t hm = L.rows / 2, hk = L.cols / 2, hn = R.cols / 2;
-  View Lq[4] = {L.quad(0, 0), L.quad(0, 1), L.quad(1, 0), L.quad(1, 1)};
-  View Rq[4] = {R.quad(0, 0), R.quad(0, 1), R.quad(1, 0), R.quad(1, 1)};
   View Dq[4] = {D.quad(0, 0), D.quad(0, 1), D.quad(1, 0), D.quad(1, 1)};
   leaf_flops += 7 * 2 * hm * hn * hk;
   leaf_products += 7;
@@ -318,6 +323,12 @@ void Exec::fused_level(Scalar alpha, bool acc, Scalar beta, View L, View R, View
   fill_common(P, *this, alpha, false, beta, EPI_REDUCE);
   if (simt) {
     if (!dry) {
+      if (LL.n != 1 || RL.n != 1 || LL.s[0] != 1 || RL.s[0] != 1) {
+        if (fail.empty()) fail = "SIMT fused level needs materialised operands";
+        return;
+      }
+      const View Lq[4] = {L.quad(0, 0), L.quad(0, 1), L.quad(1, 0), L.quad(1, 1)};
+      const View Rq[4] = {R.quad(0, 0), R.quad(0, 1), R.quad(1, 0), R.quad(1, 1)};
       for (int i = 0; i < 7; ++i) {
         SimtArgs S;
         std::memset(&S, 0, sizeof(S));
@@ -359,16 +370,34 @@ void Exec::fused_level(Scalar alpha, bool acc, Scalar beta, View L, View R, View
       char *stg = base + hdr;
       const Rect ra = rect_bytes(stg, 7 * abytes), rb = rect_bytes(stg + 7 * abytes, 7 * bbytes);
       const Rect rh = rect_bytes(base, 8);
-      if (fp32) fp32_amax(amax, Lq, 4, Rq, 4);
+      if (fp32) fp32_amax(amax, LL.v, LL.n, RL.v, RL.n);
       PackArgs pa, pb;
       std::memset(&pa, 0, sizeof(pa));
       std::memset(&pb, 0, sizeof(pb));
-      for (int q = 0; q < 4; ++q) {
-        pa.src[q] = Lq[q].ptr;
-        pa.ld[q] = Lq[q].ld;
-        pb.src[q] = Rq[q].ptr;
-        pb.ld[q] = Rq[q].ld;
+      // source q of the pack = quadrant q of every term of the operand
+      std::vector<Rect> rdA{rh}, rdB{rh};
+      for (int t = 0; t < LL.n; ++t) {
+        const View &v = LL.v[t];
+        const View qd[4] = {v.quad(0, 0), v.quad(0, 1), v.quad(1, 0), v.quad(1, 1)};
+        for (int q = 0; q < 4; ++q) {
+          pa.src[q][t] = qd[q].ptr;
+          pa.ld[q][t] = qd[q].ld;
+        }
+        pa.tsign[t] = LL.s[t];
+        rdA.push_back(rect_of(v));
       }
+      for (int t = 0; t < RL.n; ++t) {
+        const View &v = RL.v[t];
+        const View qd[4] = {v.quad(0, 0), v.quad(0, 1), v.quad(1, 0), v.quad(1, 1)};
+        for (int q = 0; q < 4; ++q) {
+          pb.src[q][t] = qd[q].ptr;
+          pb.ld[q][t] = qd[q].ld;
+        }
+        pb.tsign[t] = RL.s[t];
+        rdB.push_back(rect_of(v));
+      }
+      pa.nterm = LL.n;
+      pb.nterm = RL.n;
       pa.nsrc = pb.nsrc = 4;
       pa.nout = pb.nout = 7;
       pa.set = PACK_WINOGRAD_A;  // the chains of acoef / bcoef, formed once per element
@@ -395,14 +424,15 @@ void Exec::fused_level(Scalar alpha, bool acc, Scalar beta, View L, View R, View
       pb.pcol_pad = (int)Kp;
       pb.transpose = 1;
       pb.p = p;
-      // |S4|, |T4| <= 4 max|quadrant entry|: the largest sums of the sets
+      // |S4|, |T4| <= 4 max|source|, a source <= nterm max|term entry|
       pa.amax = amax;
       pb.amax = amax ? amax + 1 : nullptr;
-      pa.terms = pb.terms = 4;
-      cudaStream_t st = op_begin({rect_of(L), rh}, {ra});
+      pa.terms = 4 * LL.n;
+      pb.terms = 4 * RL.n;
+      cudaStream_t st = op_begin(rdA, {ra});
       check(launch_pack(pa, mode, st), "fused pack A");
       op_end();
-      st = op_begin({rect_of(R), rh}, {rb});
+      st = op_begin(rdB, {rb});
       check(launch_pack(pb, mode, st), "fused pack B");
       op_end();
       int tiles = 0;
@@ -437,7 +467,8 @@ void Exec::fused_level(Scalar alpha, bool acc, Scalar beta, View L, View R, View
       P.nprod = 7;
       P.total_tiles = tiles;
       P.amax = amax;
-      P.terms_a = P.terms_b = 4;
+      P.terms_a = pa.terms;
+      P.terms_b = pb.terms;
       st = op_begin({ra, rb, rh}, {rect_of(D)});
       if (timing) timing->begin(st);
       check(launch_gemm_tc(P, mode, num_sms, st), "fused gemm");
@@ -460,7 +491,7 @@ void Exec::call(Kind k, Scalar alpha, bool acc, Scalar beta, View L, View R, Vie
     return;
   }
   if (fused && depth == 1) {
-    fused_level(alpha, acc, beta, L, R, D);
+    fused_level(alpha, acc, beta, Lin::of(L), Lin::of(R), D);
     return;
   }
   table(k, alpha, acc, beta, L, R, D, depth, ar);
@@ -557,24 +588,131 @@ void Exec::table(Kind k, Scalar alpha, bool acc, Scalar beta, View L, View R, Vi
     }
     return one();
   };
+  // Pre-additions kept symbolic.  When every product of this level is a
+  // fused level, a row that writes a signed sum of operand quadrants into a
+  // temporary only records the sum (a Lin); the fused level forms it while
+  // packing.  A recorded sum is written out before any other kind of row
+  // reads the temporary, and before any row writes a block it refers to, so
+  // every value the table reads is the one its rows define.  Only for
+  // quadrants above kVirtMinBytes: smaller blocks stay in L2 between an
+  // addition and its reader, and re-reading several terms in the pack then
+  // costs more than the addition saves.
+  constexpr int64_t kVirtMinBytes = 32ll << 20;
+  const bool virt = !simt && fuses(hm, hk, hn, depth - 1) && 4 * hm * hk >= kVirtMinBytes &&
+                    4 * hk * hn >= kVirtMinBytes;
+  Lin sym[NLOC];
+  View symdst[NLOC];
+  bool has[NLOC] = {};
+  auto is_tmp = [](Loc l) { return l == LX || l == LY || l == LZ; };
+  auto operand_quad = [](Loc l, Shape sh) {
+    return (sh == SH_A && l >= A11 && l <= A22) || (sh == SH_B && l >= B11 && l <= B22);
+  };
+  auto sgn = [&](int v) { return v > 0 ? one() : neg(one()); };
+  auto materialize = [&](Loc l) {
+    if (!has[l]) return;
+    has[l] = false;
+    const Lin &v = sym[l];
+    const View &d = symdst[l];
+    if (v.n == 1) {
+      add(d, v.v[0], v.v[0], sgn(v.s[0]), Scalar{});
+      return;
+    }
+    add(d, v.v[0], v.v[1], sgn(v.s[0]), sgn(v.s[1]));
+    for (int t = 2; t < v.n; ++t) add(d, d, v.v[t], one(), sgn(v.s[t]));
+  };
+  auto before_write = [&](const View &w) {
+    const Rect rw = rect_of(w);
+    for (Loc l : {LX, LY, LZ}) {
+      if (!has[l]) continue;
+      for (int t = 0; t < sym[l].n; ++t)
+        if (overlaps(rect_of(sym[l].v[t]), rw)) {
+          materialize(l);
+          break;
+        }
+    }
+  };
+  auto same = [](const View &x, const View &y) {
+    return x.ptr == y.ptr && x.ld == y.ld && x.rows == y.rows && x.cols == y.cols;
+  };
+  // c1 x + c2 y as a Lin of at most kMaxTerm unit-coefficient terms
+  auto compose = [&](const Lin &x, int c1, const Lin &y, int c2, Lin &r) {
+    r = Lin();
+    int acc[2 * kMaxTerm];
+    View vs[2 * kMaxTerm];
+    int n = 0;
+    auto put = [&](const Lin &z, int c) {
+      for (int t = 0; t < z.n; ++t) {
+        int j = 0;
+        while (j < n && !same(vs[j], z.v[t])) ++j;
+        if (j == n) {
+          vs[n] = z.v[t];
+          acc[n++] = 0;
+        }
+        acc[j] += c * z.s[t];
+      }
+    };
+    put(x, c1);
+    put(y, c2);
+    for (int j = 0; j < n; ++j) {
+      if (acc[j] == 0) continue;
+      if (acc[j] != 1 && acc[j] != -1) return false;
+      if (r.n == kMaxTerm) return false;
+      r.v[r.n] = vs[j];
+      r.s[r.n++] = (int8_t)acc[j];
+    }
+    return r.n > 0;
+  };
   for (const Row &row : *K.table) {
     if (!ok()) return;
     if (row.op == OP_ADD) {
-      add(at(row.dst, row.shape), at(row.s1, row.shape), at(row.s2, row.shape), coef(row.c1), coef(row.c2));
+      const View d = at(row.dst, row.shape), a = at(row.s1, row.shape), b = at(row.s2, row.shape);
+      bool recorded = false;
+      const bool unit = (row.c1 == CF_ONE || row.c1 == CF_NEG) && (row.c2 == CF_ONE || row.c2 == CF_NEG);
+      if (virt && unit && is_tmp(row.dst) && row.shape != SH_C &&
+          (has[row.s1] || operand_quad(row.s1, row.shape)) && (has[row.s2] || operand_quad(row.s2, row.shape))) {
+        Lin r;
+        const Lin x = has[row.s1] ? sym[row.s1] : Lin::of(a), y = has[row.s2] ? sym[row.s2] : Lin::of(b);
+        if (compose(x, row.c1 == CF_ONE ? 1 : -1, y, row.c2 == CF_ONE ? 1 : -1, r)) {
+          sym[row.dst] = r;
+          symdst[row.dst] = d;
+          has[row.dst] = true;
+          recorded = true;
+        }
+      }
+      if (!recorded) {
+        materialize(row.s1);
+        materialize(row.s2);
+        before_write(d);
+        has[row.dst] = false;
+        add(d, a, b, coef(row.c1), coef(row.c2));
+      }
     } else if (row.op == OP_COPY) {
       View d = at(row.dst, row.shape);
+      const View src = at(row.s1, row.shape);
+      materialize(row.s1);
+      before_write(d);
+      has[row.dst] = false;
       ++ew_launches;
       add_elems += d.rows * d.cols;
       if (!dry) {
-        const View src = at(row.s1, row.shape);
         cudaStream_t st = op_begin({rect_of(src)}, {rect_of(d)});
         check(launch_copy(d, src, st), "copy");
         op_end();
       }
     } else {
       const KindInfo &S = kind_info(row.kind);
-      call(row.kind, coef(row.c1), S.accumulate, row.acc ? coef(row.cacc) : Scalar{}, at(row.s1, SH_A),
-           at(row.s2, SH_B), at(row.dst, SH_C), depth - 1, sub);
+      const View a = at(row.s1, SH_A), b = at(row.s2, SH_B), d = at(row.dst, SH_C);
+      const Scalar al = coef(row.c1), be = row.acc ? coef(row.cacc) : Scalar{};
+      before_write(d);
+      if (virt) {
+        // a fused level reads its operands (symbolic or not) and writes d
+        const Lin la = has[row.s1] ? sym[row.s1] : Lin::of(a), lb = has[row.s2] ? sym[row.s2] : Lin::of(b);
+        has[row.dst] = false;
+        fused_level(al, S.accumulate, be, la, lb, d);
+      } else {
+        has[row.dst] = false;
+        call(row.kind, al, S.accumulate, be, a, b, d, depth - 1, sub);
+      }
     }
   }
   if (!ar.carve) {

@@ -19,6 +19,23 @@ struct Scalar {
   float f = 0.f;   // FP32 mode value
 };
 
+// An operand given as a signed sum of up to kMaxTerm blocks of one shape:
+// a pre-addition of the level above that is formed while the fused level
+// packs its operands, instead of being written to a temporary.
+struct Lin {
+  int n = 0;
+  View v[kMaxTerm];
+  int8_t s[kMaxTerm] = {0, 0, 0, 0};
+  static Lin of(const View &x) {
+    Lin l;
+    l.n = 1;
+    l.v[0] = x;
+    l.s[0] = 1;
+    return l;
+  }
+  const View &shape() const { return v[0]; }
+};
+
 // Where a recursion level takes its temporaries X, Y, Z from.
 struct Arena {
   bool carve = false;  // true: quadrants of `region` (Algorithm 2 carves C22)
@@ -81,7 +98,9 @@ struct Exec {
   void tblock(Scalar alpha, Scalar beta, View L, View R, View D, int t, int depth, Kind acc_kind);
 
  private:
-  void fused_level(Scalar alpha, bool acc, Scalar beta, View L, View R, View D);
+  void fused_level(Scalar alpha, bool acc, Scalar beta, const Lin &L, const Lin &R, View D);
+  // would call() with these sizes and depth run a fused level?
+  bool fuses(int64_t m, int64_t k, int64_t n, int depth) const;
   void peel(Kind k, Scalar alpha, bool acc, Scalar beta, View L, View R, View D, int depth, const Arena &ar);
   void table(Kind k, Scalar alpha, bool acc, Scalar beta, View L, View R, View D, int depth, const Arena &ar);
   void add(View d, View s1, View s2, Scalar c1, Scalar c2);

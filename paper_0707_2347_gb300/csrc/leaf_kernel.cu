@@ -216,6 +216,48 @@ __device__ __forceinline__ void emit_all(const PackArgs &a, const uint32_t (&v)[
   }
 }
 
+// n consecutive elements (n = 8 or 4) of row r from column c of one block;
+// 0 outside rows x cols; 16-byte loads when aligned
+template <int N>
+__device__ __forceinline__ void load_row(const char *blk, int64_t ld, int r, int c, int rows, int cols, uint32_t *w) {
+  const char *base = blk + 4 * ((int64_t)r * ld + c);
+  if (r < rows && c + N <= cols && ((uintptr_t)base & 15) == 0) {
+#pragma unroll
+    for (int i = 0; i < N / 4; ++i) {
+      const uint4 x = *reinterpret_cast<const uint4 *>(base + 16 * i);
+      w[4 * i] = x.x;
+      w[4 * i + 1] = x.y;
+      w[4 * i + 2] = x.z;
+      w[4 * i + 3] = x.w;
+    }
+  } else {
+#pragma unroll
+    for (int e = 0; e < N; ++e) w[e] = (r < rows && c + e < cols) ? reinterpret_cast<const uint32_t *>(base)[e] : 0u;
+  }
+}
+
+// source q at (r, c..c+N): sum_t tsign[t] * term t, every term reduced first
+template <int MODE, int N>
+__device__ __forceinline__ void load_source(const PackArgs &a, int q, int r, int c, uint32_t *v) {
+  load_row<N>(a.src[q][0], a.ld[q][0], r, c, a.rows, a.cols, v);
+#pragma unroll
+  for (int e = 0; e < N; ++e) v[e] = source_value<MODE>(v[e], a.p, a.barrett);
+  if (a.nterm == 1 && a.tsign[0] > 0) return;  // one plain block (every launch but symbolic sums)
+  if (a.tsign[0] < 0) {
+#pragma unroll
+    for (int e = 0; e < N; ++e) v[e] = lin_sub<MODE>(MODE == MODE_FP32 ? __float_as_uint(0.f) : 0u, v[e], a.p);
+  }
+  for (int t = 1; t < a.nterm; ++t) {
+    uint32_t w[N];
+    load_row<N>(a.src[q][t], a.ld[q][t], r, c, a.rows, a.cols, w);
+#pragma unroll
+    for (int e = 0; e < N; ++e) {
+      const uint32_t x = source_value<MODE>(w[e], a.p, a.barrett);
+      v[e] = a.tsign[t] > 0 ? lin_add<MODE>(v[e], x, a.p) : lin_sub<MODE>(v[e], x, a.p);
+    }
+  }
+}
+
 // ------------------------------------------------------------------ pack
 // plain layout: thread = 8 consecutive columns of one row; every source
 // value is loaded and reduced once, then combined for each output.
@@ -231,19 +273,7 @@ __global__ void __launch_bounds__(256) pack_rows_kernel(const __grid_constant__ 
 #pragma unroll
     for (int q = 0; q < kMaxSrc; ++q) {
       if (q < a.nsrc) {
-        const char *base = a.src[q] + 4 * ((int64_t)r * a.ld[q] + c0);
-        const bool fast = r < a.rows && c0 + 8 <= a.cols && ((uintptr_t)base & 15) == 0;
-        if (fast) {
-          uint4 x0 = *reinterpret_cast<const uint4 *>(base), x1 = *reinterpret_cast<const uint4 *>(base + 16);
-          v[q][0] = x0.x; v[q][1] = x0.y; v[q][2] = x0.z; v[q][3] = x0.w;
-          v[q][4] = x1.x; v[q][5] = x1.y; v[q][6] = x1.z; v[q][7] = x1.w;
-        } else {
-#pragma unroll
-          for (int e = 0; e < 8; ++e)
-            v[q][e] = (r < a.rows && c0 + e < a.cols) ? reinterpret_cast<const uint32_t *>(base)[e] : 0u;
-        }
-#pragma unroll
-        for (int e = 0; e < 8; ++e) v[q][e] = source_value<MODE>(v[q][e], a.p, a.barrett);
+        load_source<MODE, 8>(a, q, r, c0, v[q]);
       } else {
 #pragma unroll
         for (int e = 0; e < 8; ++e) v[q][e] = 0;
@@ -269,19 +299,10 @@ __global__ void __launch_bounds__(256) pack_cols_kernel(const __grid_constant__ 
     for (int i = 0; i < 2; ++i) {
       const int vi = t + 256 * i;
       const int rr = vi >> 4, cc = (vi & 15) * 4;
-      const int gr = r0 + rr, gc = c0 + cc;
-      const char *base = a.src[q] + 4 * ((int64_t)gr * a.ld[q] + gc);
       uint32_t w[4];
-      if (gr < a.rows && gc + 4 <= a.cols && ((uintptr_t)base & 15) == 0) {
-        uint4 x = *reinterpret_cast<const uint4 *>(base);
-        w[0] = x.x; w[1] = x.y; w[2] = x.z; w[3] = x.w;
-      } else {
+      load_source<MODE, 4>(a, q, r0 + rr, c0 + cc, w);
 #pragma unroll
-        for (int e = 0; e < 4; ++e)
-          w[e] = (gr < a.rows && gc + e < a.cols) ? reinterpret_cast<const uint32_t *>(base)[e] : 0u;
-      }
-#pragma unroll
-      for (int e = 0; e < 4; ++e) tile[q][rr][cc + e] = source_value<MODE>(w[e], a.p, a.barrett);
+      for (int e = 0; e < 4; ++e) tile[q][rr][cc + e] = w[e];
     }
   }
   __syncthreads();
@@ -468,6 +489,14 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const float *v) {
       : "memory");
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+// After tcgen05.wait::ld: ties 16 loaded registers to the wait so that no
+// arithmetic on them is scheduled before it.
+__device__ __forceinline__ void reg_fence16(float (&v)[16]) {
+  asm volatile(""
+               : "+f"(v[0]), "+f"(v[1]), "+f"(v[2]), "+f"(v[3]), "+f"(v[4]), "+f"(v[5]), "+f"(v[6]), "+f"(v[7]),
+                 "+f"(v[8]), "+f"(v[9]), "+f"(v[10]), "+f"(v[11]), "+f"(v[12]), "+f"(v[13]), "+f"(v[14]),
+                 "+f"(v[15]));
+}
 __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 __device__ __forceinline__ uint4 lds128(uint32_t a) {
   uint4 v;
@@ -544,6 +573,61 @@ struct Epi {
   }
 };
 
+// 2^16 hh + 2^8 (hl + lh) + ll mod p for 16 columns, every intermediate an
+// exact fp32 integer; q = {hh, hl, lh, ll}
+__device__ __forceinline__ void modp2_recombine(const Epi &E, const float (&q)[4][16], uint32_t *v) {
+#pragma unroll
+  for (int e = 0; e < 16; ++e) {
+    const float s = E.fr(E.fr(q[1][e]) + E.fr(q[2][e]));
+    const float t1 = E.fr(__fmaf_rn(256.f, E.fr(q[0][e]), s));
+    v[e] = E.canon(E.fr(__fmaf_rn(256.f, t1, E.fr(q[3][e]))));
+  }
+}
+
+// alpha and the sign of a reduction target on 16 mod-p results
+__device__ __forceinline__ void modp_finish(const GemmParams &P, const Epi &E, int sign, uint32_t *v) {
+#pragma unroll
+  for (int e = 0; e < 16; ++e) {
+    uint32_t x = v[e];
+    if (P.alpha_u != 1) x = E.mulmod(P.alpha_u, x);
+    if (P.epilogue == EPI_REDUCE && sign < 0) x = x == 0 ? 0u : E.p - x;
+    v[e] = x;
+  }
+}
+
+// p < 2^16, one accumulator buffer: the thread's four 16-column groups
+// (tile columns hsel*32 + {0, 16} of both 64-column chunks), with the
+// tensor-memory reads of group g + 1 in flight while group g is recombined.
+__device__ __forceinline__ void modp2_drain_all(const GemmParams &P, const Epi &E, uint32_t d, int hsel, int sign,
+                                                uint32_t (&vals)[2][32]) {
+  float cur[4][16], nxt[4][16];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) tmem_ld16(d + 128 * i + hsel * 32, cur[i]);
+  tmem_wait_ld();
+#pragma unroll
+  for (int i = 0; i < 4; ++i) reg_fence16(cur[i]);
+#pragma unroll
+  for (int g = 0; g < 4; ++g) {
+    if (g < 3) {
+      const int col = ((g + 1) >> 1) * 64 + hsel * 32 + ((g + 1) & 1) * 16;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) tmem_ld16(d + 128 * i + col, nxt[i]);
+    }
+    uint32_t *v = vals[g >> 1] + (g & 1) * 16;
+    modp2_recombine(E, cur, v);
+    modp_finish(P, E, sign, v);
+    if (g < 3) {
+      tmem_wait_ld();
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        reg_fence16(nxt[i]);
+#pragma unroll
+        for (int e = 0; e < 16; ++e) cur[i][e] = nxt[i][e];
+      }
+    }
+  }
+}
+
 // Values of 16 consecutive columns of one row before any beta term: mod p
 // results (alpha applied; REDUCE: the signed contribution p - v for a
 // negative target) or floats (FP32: alpha applied, sign folded for REDUCE).
@@ -551,23 +635,20 @@ template <int MODE>
 __device__ __forceinline__ void tile_values(const GemmParams &P, const Epi &E, uint32_t d, int col, int sign,
                                             uint32_t *v) {
   if (MODE == MODE_MODP2) {
-    float hh[16], hl[16], lh[16], ll[16];
-    tmem_ld16(d + col, hh);
-    tmem_ld16(d + 128 + col, hl);
-    tmem_ld16(d + 256 + col, lh);
-    tmem_ld16(d + 384 + col, ll);
+    float q[4][16];
+    tmem_ld16(d + col, q[0]);
+    tmem_ld16(d + 128 + col, q[1]);
+    tmem_ld16(d + 256 + col, q[2]);
+    tmem_ld16(d + 384 + col, q[3]);
     tmem_wait_ld();
 #pragma unroll
-    for (int e = 0; e < 16; ++e) {
-      // 2^16 hh + 2^8 (hl + lh) + ll, every intermediate an exact fp32 integer
-      const float s = E.fr(E.fr(hl[e]) + E.fr(lh[e]));
-      const float t1 = E.fr(__fmaf_rn(256.f, E.fr(hh[e]), s));
-      v[e] = E.canon(E.fr(__fmaf_rn(256.f, t1, E.fr(ll[e]))));
-    }
+    for (int i = 0; i < 4; ++i) reg_fence16(q[i]);
+    modp2_recombine(E, q, v);
   } else if (MODE == MODE_MODP1) {
     float a[16];
     tmem_ld16(d + col, a);
     tmem_wait_ld();
+    reg_fence16(a);
 #pragma unroll
     for (int e = 0; e < 16; ++e) v[e] = E.canon(E.fr(a[e]));
   } else {
@@ -575,6 +656,8 @@ __device__ __forceinline__ void tile_values(const GemmParams &P, const Epi &E, u
     tmem_ld16(d + col, a);
     tmem_ld16(d + 128 + col, b);
     tmem_wait_ld();
+    reg_fence16(a);
+    reg_fence16(b);
 #pragma unroll
     for (int e = 0; e < 16; ++e) {
       float f = E.fsc * (a[e] + b[e]);
@@ -583,13 +666,7 @@ __device__ __forceinline__ void tile_values(const GemmParams &P, const Epi &E, u
     }
     return;
   }
-#pragma unroll
-  for (int e = 0; e < 16; ++e) {
-    uint32_t x = v[e];
-    if (P.alpha_u != 1) x = E.mulmod(P.alpha_u, x);
-    if (P.epilogue == EPI_REDUCE && sign < 0) x = x == 0 ? 0u : E.p - x;
-    v[e] = x;
-  }
+  modp_finish(P, E, sign, v);
 }
 
 // value + beta * c for a STORE with beta (c may be any representative mod p)
@@ -824,10 +901,14 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_kernel(const __grid_constant
       constexpr int HOLD = C::ACC_BUFS == 1 ? NCH : 1;
       uint32_t vals[HOLD][32];
       if (HOLD > 1) {
+        if (MODE == MODE_MODP2 && HOLD == 2) {
+          modp2_drain_all(P, E, d, hsel, sign, *reinterpret_cast<uint32_t(*)[2][32]>(vals));
+        } else {
 #pragma unroll
-        for (int ch = 0; ch < HOLD; ++ch) {
-          tile_values<MODE>(P, E, d, ch * 64 + hsel * 32, sign, vals[ch]);
-          tile_values<MODE>(P, E, d, ch * 64 + hsel * 32 + 16, sign, vals[ch] + 16);
+          for (int ch = 0; ch < HOLD; ++ch) {
+            tile_values<MODE>(P, E, d, ch * 64 + hsel * 32, sign, vals[ch]);
+            tile_values<MODE>(P, E, d, ch * 64 + hsel * 32 + 16, sign, vals[ch] + 16);
+          }
         }
         tc_fence_before();
         mbar_arrive(&acc_empty[buf]);  // accumulators free for the next tile

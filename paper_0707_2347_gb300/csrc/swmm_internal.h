@@ -46,11 +46,16 @@ constexpr int kBK = 64;   // leaf k-block (64 halves = one 128-byte row)
 // planes of 16-bit values.  Plain layout: plane-major, then rows_pad rows of
 // cols_pad halves (K contiguous).  Transposed layout (B operands): the
 // packed row index is the source column.  Entries outside rows x cols are 0.
+// Each source may itself be a signed sum of up to kMaxTerm blocks (a
+// pre-addition of the level above): Q_s = sum_t tsign[t] * src[s][t].
 constexpr int kMaxSrc = 4;
 constexpr int kMaxOut = 7;
+constexpr int kMaxTerm = 4;
 struct PackArgs {
-  const char *src[kMaxSrc];
-  int64_t ld[kMaxSrc];
+  const char *src[kMaxSrc][kMaxTerm];
+  int64_t ld[kMaxSrc][kMaxTerm];
+  int8_t tsign[kMaxTerm];
+  int32_t nterm;  // >= 1
   int32_t nsrc;
   uint16_t *out[kMaxOut];
   int8_t coef[kMaxOut][kMaxSrc];
@@ -141,8 +146,8 @@ __host__ __device__ inline float fp16_scale(uint32_t amax_bits, int terms) {
 // max |x| over up to 4 views per side (side 0: A, side 1: B), atomically
 // maxed into amax[side] (float bits; the words must be zeroed first)
 struct AmaxArgs {
-  const char *src[2][kMaxSrc];
-  int64_t ld[2][kMaxSrc];
+  const char *src[2][kMaxTerm];
+  int64_t ld[2][kMaxTerm];
   int64_t rows[2], cols[2];
   int32_t nsrc[2];
   uint32_t *amax;
