@@ -45,6 +45,8 @@ WORKLOADS = {
                             m=16384, k=16384, n=16384, mode=MODP, p=65521, sched=T9, depth=2, entry="muladd"),
     "t9_16384_p65521_d1": dict(desc="C<-AB+C over Z/65521, 16384^2, Table 9 (Acc) depth 1 (fused level)",
                                m=16384, k=16384, n=16384, mode=MODP, p=65521, sched=T9, depth=1, entry="muladd"),
+    "t9_2048_p65521_d1": dict(desc="C<-AB+C over Z/65521, 2048^2, Table 9 (Acc) depth 1: one fused level, 7 x 1024^3",
+                              m=2048, k=2048, n=2048, mode=MODP, p=65521, sched=T9, depth=1, entry="muladd"),
     "t9_4096_p65521_d2": dict(desc="C<-AB+C over Z/65521, 4096^2, Table 9 (Acc) depth 2, fused last level",
                               m=4096, k=4096, n=4096, mode=MODP, p=65521, sched=T9, depth=2, entry="muladd"),
     "classical_4096_p65521": dict(desc="C<-AB+C over Z/65521, 4096^2, classical tcgen05 product",
@@ -82,9 +84,10 @@ WORKLOADS = {
 DEFAULT = "t9_8192_p65521"
 
 # DRAM bytes (read + write) per leaf GEMM launch from one ncu capture of the
-# same kernel on a launch of the same shape (7 products of 1024^3);
-# see profiles/gemm_kernel_fused_level_7x1024_p65521.md.
-TRAFFIC = {"t9_8192_p65521": 77.5e6}
+# same kernel build on a launch of the same shape (7 products of 1024^3,
+# the 2048^2 depth-1 workload); see
+# profiles/gemm_kernel_fused_level_7x1024_p65521.md.
+TRAFFIC = {"t9_8192_p65521": 77.1e6, "t9_2048_p65521_d1": 77.1e6}
 
 
 def peaks():
@@ -466,7 +469,8 @@ def main():
         "dtype": "i32 mod p (fp16 limbs, fp32 accum)" if mode == MODP else "f32 (3 fp16 split products)",
         "data": "synthetic",
         "config": {"workload": w["desc"], "m": m, "k": k, "n": n, "p": p, "schedule": S.SCHED_NAMES[w["sched"]],
-                   "depth": w["depth"], "l2": f"inputs {3 * m * n * 4 / 1e6:.0f} MB > 129 MB L2, no flush",
+                   "depth": w["depth"], "l2": (f"inputs {(m * k + k * n + m * n) * 4 / 1e6:.0f} MB "
+                          + ("> 129 MB L2, no flush" if (m * k + k * n + m * n) * 4 > 129e6 else "fit in L2")),
                    "parallelism": f"replicas x{world}"},
         "gpu_launches": int((st["leaf_launches"] + st["ew_launches"]) * args.steps),
         "cuda_graph": not args.no_graph,
