@@ -245,11 +245,14 @@ struct Plan {
   Kind ipmm_acc = K_T2;  // accumulation kind of IPMM and of the Section 7.2 blocks
   int tblock = 2;
   int64_t paper = 0;
+  std::vector<LeafJob> jobs;  // a grouped launch of classical problems (batched calls)
 };
 
 void execute(const Plan &P, Exec &e) {
   if (!P.ne) return;
-  if (P.sched == SWMM_IPMM)
+  if (!P.jobs.empty())
+    e.leaf_group(P.alpha, P.accum, P.beta, P.jobs.data(), (int)P.jobs.size());
+  else if (P.sched == SWMM_IPMM)
     e.ipmm(P.L, P.R, P.D, P.depth, P.cutoff, P.ipmm_acc);
   else if (P.sched == SWMM_IP0VMM)
     e.ip0vmm(P.alpha, P.L, P.R, P.D, P.depth);
@@ -492,7 +495,7 @@ int run_plans(swmm_t h, const std::vector<Plan> &plans, uint32_t flags, const Sc
       // the capture starts
       size_t need = 2;
       for (const Plan &P : plans)
-        need = std::max<size_t>(need, (size_t)(8 * P.x.leaf_launches + P.x.ew_launches + 2));
+        need = std::max<size_t>(need, (size_t)(8 * P.x.leaf_launches + 2 * P.x.ew_launches + 16));
       for (cudaStream_t &s : h->flow_streams)
         if (!s && cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
           cudaGetLastError();
@@ -568,6 +571,64 @@ int run(swmm_t h, const Req &q, const swmm_opts *o, const Scratch *ext = nullptr
   int rc = make_plan(h, q, o, true, plans[0]);
   if (rc != SWMM_OK) return rc;
   return run_plans(h, plans, o->flags, ext, key);
+}
+
+// Classical problems with the same arithmetic (mode, modulus, scalars)
+// become plans with grouped leaf launches of up to kMaxProducts products
+// (operand staging of a group capped at 2 GiB), grouped by decreasing inner
+// dimension; the problems are independent, so any order gives the same
+// results.
+std::vector<Plan> group_classical(std::vector<Plan> &each) {
+  constexpr int64_t kGroupStageBytes = 2ll << 30;
+  auto groupable = [](const Plan &P) {
+    return P.sched == SWMM_CLASSICAL && P.ne && P.q.k > 0 && !P.x.simt && P.jobs.empty();
+  };
+  auto same = [](const Plan &a, const Plan &b) {
+    return a.x.mode == b.x.mode && a.x.p == b.x.p && a.accum == b.accum && a.alpha.u == b.alpha.u &&
+           a.beta.u == b.beta.u && a.alpha.f == b.alpha.f && a.beta.f == b.beta.f;
+  };
+  std::vector<Plan> out;
+  out.reserve(each.size());
+  std::vector<std::vector<size_t>> kinds;  // indices of groupable plans per arithmetic
+  for (size_t i = 0; i < each.size(); ++i) {
+    if (!groupable(each[i])) {
+      out.push_back(std::move(each[i]));
+      continue;
+    }
+    size_t c = 0;
+    while (c < kinds.size() && !same(each[kinds[c][0]], each[i])) ++c;
+    if (c == kinds.size()) kinds.emplace_back();
+    kinds[c].push_back(i);
+  }
+  for (std::vector<size_t> &idx : kinds) {
+    // problems of similar inner dimension share a launch (similar tile times)
+    std::stable_sort(idx.begin(), idx.end(), [&](size_t x, size_t y) { return each[x].q.k > each[y].q.k; });
+    for (size_t a = 0; a < idx.size();) {
+      size_t b = a + 1;
+      int64_t bytes = each[idx[a]].x.stage_need;
+      while (b < idx.size() && b - a < (size_t)kMaxProducts && bytes + each[idx[b]].x.stage_need <= kGroupStageBytes)
+        bytes += each[idx[b++]].x.stage_need;
+      Plan G = each[idx[a]];
+      if (b - a > 1) {
+        for (size_t t = a; t < b; ++t) G.jobs.push_back(LeafJob{each[idx[t]].L, each[idx[t]].R, each[idx[t]].D});
+        // longest inner dimension first: the persistent launch deals tiles
+        // out in order, so the tiles that take longest start first
+        std::stable_sort(G.jobs.begin(), G.jobs.end(),
+                         [](const LeafJob &x, const LeafJob &y) { return x.L.cols > y.L.cols; });
+        // plan the group: sizes and counts of the grouped launch
+        Exec &x = G.x;
+        x.ws_top = x.ws_peak = x.stage_need = 0;
+        x.tmp_elems = x.tmp_peak_elems = 0;
+        x.add_elems = x.leaf_flops = x.leaf_launches = x.ew_launches = x.leaf_products = 0;
+        x.lazy = false;
+        x.dry = true;
+        execute(G, x);
+      }
+      out.push_back(std::move(G));
+      a = b;
+    }
+  }
+  return out;
 }
 
 // ---------------------------------------------------------------- autotuner
@@ -754,7 +815,7 @@ int swmm_muladd_batched(swmm_t h, int count, swmm_problem *probs, uint32_t flags
       return launch_graph(h, g);
     }
   }
-  std::vector<Plan> plans(count);
+  std::vector<Plan> each(count);
   for (int i = 0; i < count; ++i) {
     swmm_problem &pb = probs[i];
     int32_t s = pb.sched, d = pb.depth;
@@ -774,9 +835,10 @@ int swmm_muladd_batched(swmm_t h, int count, swmm_problem *probs, uint32_t flags
     const void *al = pb.mode == SWMM_FP32 ? (const void *)&pb.alpha_f : (const void *)&pb.alpha_u;
     const void *be = pb.mode == SWMM_FP32 ? (const void *)&pb.beta_f : (const void *)&pb.beta_u;
     Req q{1, pb.m, pb.k, pb.n, pb.A, pb.B, pb.C, pb.lda, pb.ldb, pb.ldc, al, be};
-    int rc = make_plan(h, q, &o, true, plans[i]);
+    int rc = make_plan(h, q, &o, true, each[i]);
     if (rc != SWMM_OK) return fail(h, rc, "problem " + std::to_string(i) + ": " + h->last_error);
   }
+  const std::vector<Plan> plans = group_classical(each);
   GraphEntry *g = nullptr;
   int rc = run_plans(h, plans, flags, nullptr, key, &g);
   if (rc == SWMM_OK && g) {

@@ -152,109 +152,154 @@ void Exec::leaf(Scalar alpha, bool acc, Scalar beta, View L, View R, View D) {
     scale(D, acc, beta);
     return;
   }
+  if (!simt) {
+    const LeafJob job{L, R, D};
+    leaf_group(alpha, acc, beta, &job, 1);
+    return;
+  }
   leaf_flops += 2 * m * n * k;
   ++leaf_products;
   ++leaf_launches;
+  if (dry) return;
   GemmParams P;
   fill_common(P, *this, alpha, acc, beta, EPI_STORE);
-  if (simt) {
-    if (dry) return;
-    SimtArgs S;
-    std::memset(&S, 0, sizeof(S));
-    S.a[0] = L.ptr;
-    S.lda[0] = L.ld;
-    S.sa[0] = 1;
-    S.na = 1;
-    S.b[0] = R.ptr;
-    S.ldb[0] = R.ld;
-    S.sb[0] = 1;
-    S.nb = 1;
-    S.t[0].ptr = D.ptr;
-    S.t[0].ld = D.ld;
-    S.t[0].sign = 1;
-    S.ntargets = 1;
-    S.M = (int)m;
-    S.N = (int)n;
-    S.K = (int)k;
-    cudaStream_t st = op_begin({rect_of(L), rect_of(R)}, {rect_of(D)});
-    check(launch_leaf_simt(S, P, mode, st), "simt leaf");
-    op_end();
+  SimtArgs S;
+  std::memset(&S, 0, sizeof(S));
+  S.a[0] = L.ptr;
+  S.lda[0] = L.ld;
+  S.sa[0] = 1;
+  S.na = 1;
+  S.b[0] = R.ptr;
+  S.ldb[0] = R.ld;
+  S.sb[0] = 1;
+  S.nb = 1;
+  S.t[0].ptr = D.ptr;
+  S.t[0].ld = D.ld;
+  S.t[0].sign = 1;
+  S.ntargets = 1;
+  S.M = (int)m;
+  S.N = (int)n;
+  S.K = (int)k;
+  cudaStream_t st = op_begin({rect_of(L), rect_of(R)}, {rect_of(D)});
+  check(launch_leaf_simt(S, P, mode, st), "simt leaf");
+  op_end();
+}
+
+// Classical leaf products of independent problems (same mode, modulus and
+// scalars, every dimension > 0) in one persistent grouped GEMM launch: each
+// product's operands are packed into its own part of one staging slot, and
+// the launch's tiles cover every product, so problems too small to fill the
+// GPU on their own fill it together.
+void Exec::leaf_group(Scalar alpha, bool acc, Scalar beta, const LeafJob *jobs, int njobs) {
+  if (njobs <= 0) return;
+  if (njobs > kMaxProducts) {
+    if (fail.empty()) fail = "too many products in one grouped launch";
     return;
   }
   const int pl = planes_of(mode), bn = bn_of(mode);
-  const int64_t Mp = rup(m, kBM), Np = rup(n, bn), Kp = rup(k, kBK);
-  const int64_t abytes = rup(pl * Mp * Kp * 2, 1024), bbytes = rup(pl * Np * Kp * 2, 1024);
   const int64_t hdr = fp32 ? 1024 : 0;  // FP32 mode: the operands' amax words
-  stage_need = std::max(stage_need, hdr + abytes + bbytes);
-  ew_launches += fp32 ? 3 : 2;
-  if (dry) return;
-  char *stg = next_stage();
-  uint32_t *amax = fp32 ? reinterpret_cast<uint32_t *>(stg) : nullptr;
-  uint16_t *Ap = reinterpret_cast<uint16_t *>(stg + hdr);
-  uint16_t *Bp = reinterpret_cast<uint16_t *>(stg + hdr + abytes);
-  const Rect ra = rect_bytes(Ap, abytes), rb = rect_bytes(Bp, bbytes), rh = rect_bytes(stg, 8);
-  if (fp32) fp32_amax(amax, &L, 1, &R, 1);
-  PackArgs pa;
-  std::memset(&pa, 0, sizeof(pa));
-  pa.src[0][0] = L.ptr;
-  pa.ld[0][0] = L.ld;
-  pa.tsign[0] = 1;
-  pa.nterm = 1;
-  pa.nsrc = 1;
-  pa.out[0] = Ap;
-  pa.coef[0][0] = 1;
-  pa.nout = 1;
-  pa.rows = (int)m;
-  pa.cols = (int)k;
-  pa.prow_pad = (int)Mp;
-  pa.pcol_pad = (int)Kp;
-  pa.transpose = 0;
-  pa.p = p;
-  pa.barrett = p ? (uint32_t)(0x100000000ull / p) : 0;
-  pa.amax = amax;
-  pa.terms = 1;
-  cudaStream_t st = op_begin({rect_of(L), rh}, {ra});
-  check(launch_pack(pa, mode, st), "pack A");
-  op_end();
-  pa.src[0][0] = R.ptr;
-  pa.ld[0][0] = R.ld;
-  pa.out[0] = Bp;
-  pa.rows = (int)k;
-  pa.cols = (int)n;
-  pa.prow_pad = (int)Np;
-  pa.pcol_pad = (int)Kp;
-  pa.transpose = 1;
-  pa.amax = amax ? amax + 1 : nullptr;
-  st = op_begin({rect_of(R), rh}, {rb});
-  check(launch_pack(pa, mode, st), "pack B");
-  op_end();
-  Product &pr = P.prod[0];
-  if (!make_tmap(&pr.ta, Ap, pl * Mp, Kp, kBM) || !make_tmap(&pr.tb, Bp, pl * Np, Kp, bn)) {
-    if (fail.empty()) fail = "tensor map encoding failed";
-    return;
+  int64_t Mp[kMaxProducts], Np[kMaxProducts], Kp[kMaxProducts], ab[kMaxProducts], bb[kMaxProducts],
+      off[kMaxProducts];
+  int64_t total = 0;
+  double tflops = 0.0;
+  for (int i = 0; i < njobs; ++i) {
+    const int64_t m = jobs[i].L.rows, k = jobs[i].L.cols, n = jobs[i].R.cols;
+    Mp[i] = rup(m, kBM);
+    Np[i] = rup(n, bn);
+    Kp[i] = rup(k, kBK);
+    ab[i] = rup(pl * Mp[i] * Kp[i] * 2, 1024);
+    bb[i] = rup(pl * Np[i] * Kp[i] * 2, 1024);
+    off[i] = total;
+    total += hdr + ab[i] + bb[i];
+    leaf_flops += 2 * m * n * k;
+    ++leaf_products;
+    tflops += 2.0 * m * n * k * limb_products();
   }
-  pr.t[0].ptr = D.ptr;
-  pr.t[0].ld = D.ld;
-  pr.t[0].sign = 1;
-  pr.t[0].vec_ok = aligned16(D.ptr, D.ld);
-  pr.ntargets = 1;
-  pr.tma_epi = make_target_tmap(&pr.tmap[0], D.ptr, m, n, D.ld, fp32) ? 1 : 0;
-  pr.M = (int)m;
-  pr.N = (int)n;
-  pr.Kpad = (int)Kp;
-  pr.a_plane_rows = (int)Mp;
-  pr.b_plane_rows = (int)Np;
-  pr.tiles_m = (int)(Mp / kBM);
-  pr.tiles_n = (int)(Np / bn);
-  pr.tile_begin = 0;
-  P.nprod = 1;
-  P.total_tiles = pr.tiles_m * pr.tiles_n;
-  P.amax = amax;
-  P.terms_a = P.terms_b = 1;
-  st = op_begin({ra, rb, rh}, {rect_of(D)});
+  ++leaf_launches;
+  stage_need = std::max(stage_need, total);
+  ew_launches += njobs * (fp32 ? 3 : 2);
+  if (dry) return;
+  char *base = next_stage();
+  GemmParams P;
+  fill_common(P, *this, alpha, acc, beta, EPI_STORE);
+  std::vector<Rect> grd, gwr;
+  int tiles = 0;
+  for (int i = 0; i < njobs; ++i) {
+    const View &L = jobs[i].L, &R = jobs[i].R, &D = jobs[i].D;
+    const int64_t m = L.rows, k = L.cols, n = R.cols;
+    char *stg = base + off[i];
+    uint32_t *amax = fp32 ? reinterpret_cast<uint32_t *>(stg) : nullptr;
+    uint16_t *Ap = reinterpret_cast<uint16_t *>(stg + hdr);
+    uint16_t *Bp = reinterpret_cast<uint16_t *>(stg + hdr + ab[i]);
+    const Rect ra = rect_bytes(Ap, ab[i]), rb = rect_bytes(Bp, bb[i]), rh = rect_bytes(stg, 8);
+    if (fp32) fp32_amax(amax, &L, 1, &R, 1);
+    PackArgs pa;
+    std::memset(&pa, 0, sizeof(pa));
+    pa.src[0][0] = L.ptr;
+    pa.ld[0][0] = L.ld;
+    pa.tsign[0] = 1;
+    pa.nterm = 1;
+    pa.nsrc = 1;
+    pa.out[0] = Ap;
+    pa.coef[0][0] = 1;
+    pa.nout = 1;
+    pa.rows = (int)m;
+    pa.cols = (int)k;
+    pa.prow_pad = (int)Mp[i];
+    pa.pcol_pad = (int)Kp[i];
+    pa.transpose = 0;
+    pa.p = p;
+    pa.barrett = p ? (uint32_t)(0x100000000ull / p) : 0;
+    pa.amax = amax;
+    pa.terms = 1;
+    cudaStream_t st = op_begin({rect_of(L), rh}, {ra});
+    check(launch_pack(pa, mode, st), "pack A");
+    op_end();
+    pa.src[0][0] = R.ptr;
+    pa.ld[0][0] = R.ld;
+    pa.out[0] = Bp;
+    pa.rows = (int)k;
+    pa.cols = (int)n;
+    pa.prow_pad = (int)Np[i];
+    pa.pcol_pad = (int)Kp[i];
+    pa.transpose = 1;
+    pa.amax = amax ? amax + 1 : nullptr;
+    st = op_begin({rect_of(R), rh}, {rb});
+    check(launch_pack(pa, mode, st), "pack B");
+    op_end();
+    Product &pr = P.prod[i];
+    if (!make_tmap(&pr.ta, Ap, pl * Mp[i], Kp[i], kBM) || !make_tmap(&pr.tb, Bp, pl * Np[i], Kp[i], bn)) {
+      if (fail.empty()) fail = "tensor map encoding failed";
+      return;
+    }
+    pr.t[0].ptr = D.ptr;
+    pr.t[0].ld = D.ld;
+    pr.t[0].sign = 1;
+    pr.t[0].vec_ok = aligned16(D.ptr, D.ld);
+    pr.ntargets = 1;
+    pr.tma_epi = make_target_tmap(&pr.tmap[0], D.ptr, m, n, D.ld, fp32) ? 1 : 0;
+    pr.M = (int)m;
+    pr.N = (int)n;
+    pr.Kpad = (int)Kp[i];
+    pr.a_plane_rows = (int)Mp[i];
+    pr.b_plane_rows = (int)Np[i];
+    pr.tiles_m = (int)(Mp[i] / kBM);
+    pr.tiles_n = (int)(Np[i] / bn);
+    pr.tile_begin = tiles;
+    pr.amax = amax;
+    pr.terms_a = pr.terms_b = 1;
+    tiles += pr.tiles_m * pr.tiles_n;
+    grd.push_back(ra);
+    grd.push_back(rb);
+    grd.push_back(rh);
+    gwr.push_back(rect_of(D));
+  }
+  P.nprod = njobs;
+  P.total_tiles = tiles;
+  cudaStream_t st = op_begin(grd, gwr);
   if (timing) timing->begin(st);
   check(launch_gemm_tc(P, mode, num_sms, st), "leaf gemm");
-  if (timing) timing->end(st, 2.0 * m * n * k * limb_products());
+  if (timing) timing->end(st, tflops);
   op_end();
 }
 
@@ -462,13 +507,13 @@ void Exec::fused_level(Scalar alpha, bool acc, Scalar beta, const Lin &LL, const
         pr.tiles_m = (int)(Mp / kBM);
         pr.tiles_n = (int)(Np / bn);
         pr.tile_begin = tiles;
+        pr.amax = amax;
+        pr.terms_a = pa.terms;
+        pr.terms_b = pb.terms;
         tiles += pr.tiles_m * pr.tiles_n;
       }
       P.nprod = 7;
       P.total_tiles = tiles;
-      P.amax = amax;
-      P.terms_a = pa.terms;
-      P.terms_b = pb.terms;
       st = op_begin({ra, rb, rh}, {rect_of(D)});
       if (timing) timing->begin(st);
       check(launch_gemm_tc(P, mode, num_sms, st), "fused gemm");

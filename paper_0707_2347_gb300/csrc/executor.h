@@ -36,6 +36,11 @@ struct Lin {
   const View &shape() const { return v[0]; }
 };
 
+// One classical product of a grouped leaf launch: D <- alpha L R (+ beta D).
+struct LeafJob {
+  View L, R, D;
+};
+
 // Where a recursion level takes its temporaries X, Y, Z from.
 struct Arena {
   bool carve = false;  // true: quadrants of `region` (Algorithm 2 carves C22)
@@ -90,6 +95,8 @@ struct Exec {
   void call(Kind k, Scalar alpha, bool acc, Scalar beta, View L, View R, View D, int depth, const Arena &ar);
   // classical leaf product (one tensor-core launch)
   void leaf(Scalar alpha, bool acc, Scalar beta, View L, View R, View D);
+  // classical products of independent problems in one grouped launch
+  void leaf_group(Scalar alpha, bool acc, Scalar beta, const LeafJob *jobs, int njobs);
   // Algorithm 2 (IPMM)
   void ipmm(View L, View R, View D, int depth, int64_t cutoff, Kind acc_kind);
   // Algorithm 1 (IP0vMM): D <- alpha L R for n < m, n <= k, n | m, n | k

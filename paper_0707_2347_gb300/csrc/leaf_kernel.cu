@@ -503,6 +503,11 @@ __device__ __forceinline__ uint4 lds128(uint32_t a) {
   asm volatile("ld.shared.v4.b32 {%0,%1,%2,%3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(a));
   return v;
 }
+__device__ __forceinline__ uint32_t lds32(uint32_t a) {
+  uint32_t v;
+  asm volatile("ld.shared.b32 %0, [%1];" : "=r"(v) : "r"(a));
+  return v;
+}
 __device__ __forceinline__ void sts128(uint32_t a, uint4 v) {
   asm volatile("st.shared.v4.b32 [%0], {%1,%2,%3,%4};" ::"r"(a), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w) : "memory");
 }
@@ -846,9 +851,7 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_kernel(const __grid_constant
     E.m = P.barrett;
     E.pf = (float)P.p;
     E.inv_p = P.inv_p;
-    E.fsc = MODE == MODE_FP32
-                ? P.alpha_f / (fp16_scale(P.amax[0], P.terms_a) * fp16_scale(P.amax[1], P.terms_b))
-                : 0.f;
+    E.fsc = 0.f;
     uint32_t tcount = 0, dcount = 0, cphase = 0;
     for (int g = blockIdx.x; g < P.total_tiles; g += gridDim.x, ++tcount) {
       const TileInfo ti = decode<BN>(P, g);
@@ -857,10 +860,11 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_kernel(const __grid_constant
       const int buf = C::ACC_BUFS == 2 ? (int)(tcount & 1) : 0;
       const uint32_t use = C::ACC_BUFS == 2 ? (tcount >> 1) : tcount;
       const uint32_t d = tmem + lane_addr + (uint32_t)(buf * C::BUF_COLS);
+      if (MODE == MODE_FP32)
+        E.fsc = P.alpha_f / (fp16_scale(pr.amax[0], pr.terms_a) * fp16_scale(pr.amax[1], pr.terms_b));
       const bool tma = pr.tma_epi != 0;
       const bool with_beta = P.epilogue == EPI_STORE && P.use_beta;
       const int sign = pr.t[0].sign;
-      const int gr = ti.m0 + row;
       bool bad = false;
       if (modp && nkb > 16) {
         const int ndrain = (nkb - 1) / kChunkKB;
@@ -925,7 +929,6 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_kernel(const __grid_constant
             mbar_arrive(&acc_empty[buf]);  // accumulators free for the next tile
           }
         }
-        const int gc0 = ti.n0 + tc0;
         if (tma) {
           if (issuer) {
             bulk_wait_read0();  // the previous chunk's TMA has read the buffer
@@ -975,22 +978,43 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_kernel(const __grid_constant
             }
             bulk_commit();
           }
-        } else if (gr < pr.M) {
-          // direct path for targets TMA cannot address (misaligned leading dimension)
+        } else {
+          // Targets TMA cannot address (row pitch or base not 16-byte
+          // aligned): the chunk goes through the staging buffer so that each
+          // warp then writes whole row segments (32 consecutive columns per
+          // instruction) with plain stores or reductions.
+          if (issuer) bulk_wait_read0();  // an earlier TMA tile has read the buffer
+          epi_sync();
+          {
+            const uint32_t rowbase = eb + hsel * 16384 + row * 128;
 #pragma unroll
-          for (int e = 0; e < 32; ++e) {
-            const int gc = gc0 + e;
-            if (gc >= pr.N) continue;
-            if (P.epilogue == EPI_STORE) {
-              uint32_t *dst = reinterpret_cast<uint32_t *>((char *)pr.t[0].ptr) + (int64_t)gr * pr.t[0].ld + gc;
-              *dst = with_beta ? add_beta<MODE>(P, E, v[e], *dst) : v[e];
-            } else {
-              for (int t = 0; t < pr.ntargets; ++t) {
-                if (modp)
-                  atomicAdd(reinterpret_cast<unsigned int *>((char *)pr.t[t].ptr) + (int64_t)gr * pr.t[t].ld + gc, v[e]);
-                else
-                  atomicAdd(reinterpret_cast<float *>((char *)pr.t[t].ptr) + (int64_t)gr * pr.t[t].ld + gc,
-                            __uint_as_float(v[e]));
+            for (int j = 0; j < 8; ++j)
+              sts128(rowbase + ((j ^ (row & 7)) << 4), make_uint4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]));
+          }
+          epi_sync();
+          const int wi = et >> 5;
+          for (int rr = wi; rr < kBM; rr += kEpiThreads / 32) {
+            const int g_r = ti.m0 + rr;
+            if (g_r >= pr.M) break;
+#pragma unroll
+            for (int h2 = 0; h2 < 2; ++h2) {
+              const int c = h2 * 32 + lane;
+              const int g_c = ti.n0 + ch * 64 + c;
+              if (g_c >= pr.N) continue;
+              const uint32_t x =
+                  lds32(eb + h2 * 16384 + rr * 128 + ((((c & 31) >> 2) ^ (rr & 7)) << 4) + (c & 3) * 4);
+              if (P.epilogue == EPI_STORE) {
+                uint32_t *dst = reinterpret_cast<uint32_t *>((char *)pr.t[0].ptr) + (int64_t)g_r * pr.t[0].ld + g_c;
+                *dst = with_beta ? add_beta<MODE>(P, E, x, *dst) : x;
+              } else {
+                for (int t = 0; t < pr.ntargets; ++t) {
+                  if (modp)
+                    atomicAdd(reinterpret_cast<unsigned int *>((char *)pr.t[t].ptr) + (int64_t)g_r * pr.t[t].ld + g_c,
+                              x);
+                  else
+                    atomicAdd(reinterpret_cast<float *>((char *)pr.t[t].ptr) + (int64_t)g_r * pr.t[t].ld + g_c,
+                              __uint_as_float(x));
+                }
               }
             }
           }

@@ -86,7 +86,7 @@ cudaError_t launch_pack(const PackArgs &a, int mode, cudaStream_t s);
 // canonical contribution, p - v for a negative sign, added as an unsigned
 // integer, so targets hold representatives that are reduced later).
 constexpr int kMaxTargets = 4;
-constexpr int kMaxProducts = 7;
+constexpr int kMaxProducts = 16;  // 7 for a fused level; up to 16 classical leaves of a batch
 
 struct Target {
   void *ptr;
@@ -106,6 +106,10 @@ struct Product {
   int32_t a_plane_rows, b_plane_rows;  // M_pad, N_pad
   int32_t tiles_m, tiles_n;
   int32_t tile_begin;  // first global tile index of this product
+  // FP32 mode: the A-side and B-side amax words and term counts of this
+  // product's packs, to undo their scales in the epilogue
+  const uint32_t *amax;  // [2]: A side, B side
+  int32_t terms_a, terms_b;
 };
 
 enum Epilogue : int { EPI_STORE = 0, EPI_REDUCE = 1 };
@@ -123,11 +127,8 @@ struct GemmParams {
   float inv_p;       // 1/p rounded to float
   int32_t use_beta;  // STORE: read T0 and add beta * T0
   int *err;          // device error word (bounded waits)
-  // FP32 mode: the A-side and B-side amax words and term counts of the
-  // packs, to undo their scales in the epilogue
-  const uint32_t *amax;  // [2]: A side, B side
-  int32_t terms_a, terms_b;
 };
+static_assert(sizeof(GemmParams) <= 32764, "kernel parameter space");
 
 // FP32 mode operand scale: a power of two s with |x s| < 2^14 for every
 // value the pack writes (|x| <= terms * amax), so that hi = fp16(x s) and

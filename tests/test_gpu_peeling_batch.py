@@ -121,3 +121,17 @@ def test_graph_replay_single_call(handle):
     handle.muladd(4, dA, dB, 5, dC, o)
     handle.sync()
     assert np.array_equal(host(dC), classical.muladd_modp(4, A, B, 5, C, p))
+
+
+@pytest.mark.parametrize("graph", [False, True], ids=["eager", "graph"])
+def test_batched_classical_grouped(handle, graph):
+    """Classical problems of one kind run as grouped launches (up to 16
+    products each): 40 problems of two kinds need at most 2 + 2 launches."""
+    probs, refs = _batch(40, 64, 700, seed=43)
+    for q in probs:
+        q["sched"] = S.CLASSICAL
+        q["depth"] = 0
+    handle.muladd_batched(probs, S.FLAG_GRAPH if graph else 0)
+    handle.sync()
+    _check(probs, refs)
+    assert handle.stats()["leaf_launches"] <= 4
