@@ -232,6 +232,17 @@ struct Scratch {
   int64_t bytes;
 };
 
+// operand staging per slot up to which leaf launches are merged
+constexpr int64_t kMergeStageBytes = 96ll << 20;
+
+void reset_counts(Exec &x) {
+  x.ws_top = x.ws_peak = x.stage_need = 0;
+  x.tmp_elems = x.tmp_peak_elems = 0;
+  x.add_elems = x.leaf_flops = x.leaf_launches = x.ew_launches = x.leaf_products = 0;
+  x.lazy = false;
+  x.stage_turn = 0;
+}
+
 // A validated, planned call.
 struct Plan {
   Req q;
@@ -358,7 +369,17 @@ int make_plan(swmm_t h, const Req &q, const swmm_opts *o, bool check_ptrs, Plan 
   // planning pass: sizes and counts, no launches
   x.dry = true;
   execute(P, x);
+  x.flush();
   if (!x.fail.empty()) return fail(h, SWMM_EINVAL, x.fail);
+  // small leaf launches share launches (four staging slots in turn)
+  if (x.stage_need > 0 && x.stage_need <= kMergeStageBytes && !x.simt && x.leaf_launches > 1) {
+    reset_counts(x);
+    x.merge = true;
+    x.stage_slots = 4;
+    execute(P, x);
+    x.flush();
+    if (!x.fail.empty()) return fail(h, SWMM_EINVAL, x.fail);
+  }
   // levels that materialise temporaries: all but a fused last one
   const int tmp_levels = (x.fused && lv > 0 && sched != SWMM_IPMM) ? lv - 1 : lv;
   if (sched == SWMM_TBLOCK)  // one block call's temporaries (Section 7.2)
@@ -375,7 +396,8 @@ int enqueue(swmm_t h, const Plan &P, cudaStream_t stream, TimingHook *timing, co
             bool use_flow = false) {
   const Exec &x = P.x;
   Exec r = x;
-  r.stage_slots = use_flow ? 2 : 1;
+  r.merge = x.merge && !ext;
+  r.stage_slots = r.merge ? 4 : (use_flow ? 2 : 1);
   const int64_t stage_bytes = r.stage_slots * ((x.stage_need + 1023) / 1024 * 1024);
   r.dry = false;
   r.lazy = false;
@@ -409,6 +431,7 @@ int enqueue(swmm_t h, const Plan &P, cudaStream_t stream, TimingHook *timing, co
     Flow flow(stream, h->flow_streams, h->flow_events);
     r.flow = &flow;
     execute(P, r);
+    r.flush();
     flow.join();
     r.flow = nullptr;
     if (flow.error() != cudaSuccess && r.cuda_err == cudaSuccess) {
@@ -417,6 +440,7 @@ int enqueue(swmm_t h, const Plan &P, cudaStream_t stream, TimingHook *timing, co
     }
   } else {
     execute(P, r);
+    r.flush();
   }
   if (r.lazy && r.ok()) {
     // fused levels leave unreduced representatives: one canonicalising pass
@@ -495,7 +519,8 @@ int run_plans(swmm_t h, const std::vector<Plan> &plans, uint32_t flags, const Sc
       // the capture starts
       size_t need = 2;
       for (const Plan &P : plans)
-        need = std::max<size_t>(need, (size_t)(8 * P.x.leaf_launches + 2 * P.x.ew_launches + 16));
+        need = std::max<size_t>(need, (size_t)(8 * P.x.leaf_launches + 2 * P.x.leaf_products +
+                                               2 * P.x.ew_launches + 16));
       for (cudaStream_t &s : h->flow_streams)
         if (!s && cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
           cudaGetLastError();
@@ -617,12 +642,12 @@ std::vector<Plan> group_classical(std::vector<Plan> &each) {
                          [](const LeafJob &x, const LeafJob &y) { return x.L.cols > y.L.cols; });
         // plan the group: sizes and counts of the grouped launch
         Exec &x = G.x;
-        x.ws_top = x.ws_peak = x.stage_need = 0;
-        x.tmp_elems = x.tmp_peak_elems = 0;
-        x.add_elems = x.leaf_flops = x.leaf_launches = x.ew_launches = x.leaf_products = 0;
-        x.lazy = false;
+        reset_counts(x);
+        x.merge = false;
+        x.stage_slots = 1;
         x.dry = true;
         execute(G, x);
+        x.flush();
       }
       out.push_back(std::move(G));
       a = b;

@@ -61,13 +61,81 @@ View Exec::alloc_tmp(int64_t rows, int64_t cols) {
   return v;
 }
 
+static bool any_overlap(const std::vector<Rect> &a, const std::vector<Rect> &b) {
+  for (const Rect &x : a)
+    for (const Rect &y : b)
+      if (overlaps(x, y)) return true;
+  return false;
+}
+
 cudaStream_t Exec::op_begin(const std::vector<Rect> &rd, const std::vector<Rect> &wr) {
+  // a deferred GEMM launch goes out before anything that touches its memory
+  if (pend.n > 0 && !flushing &&
+      (any_overlap(rd, pend.wr) || any_overlap(wr, pend.rd) || any_overlap(wr, pend.wr)))
+    flush();
   if (!flow) return stream;
   return flow->begin(rd.data(), (int)rd.size(), wr.data(), (int)wr.size());
 }
 
 void Exec::op_end() {
   if (flow) flow->end();
+}
+
+// Queue the products of one leaf group or fused level (P: its parameters,
+// null in a dry run) for a GEMM launch; they join the pending launch unless
+// it is full or they depend on it (reduce-adds into a common target commute
+// and may share it).
+void Exec::queue_gemm(const GemmParams *P, const std::vector<Rect> &rd, const std::vector<Rect> &wr, bool additive,
+                      double flops, int nprod) {
+  if (pend.n > 0) {
+    const bool fits = pend.n + nprod <= kMaxProducts;
+    const bool dep = any_overlap(rd, pend.wr) || any_overlap(wr, pend.rd) ||
+                     (any_overlap(wr, pend.wr) && !(additive && pend.additive));
+    if (!fits || dep) flush();
+  }
+  if (pend.n == 0) {
+    if (P) pend.P = *P;
+    pend.tiles = 0;
+    pend.flops = 0.0;
+    pend.additive = true;
+    pend.rd.clear();
+    pend.wr.clear();
+  }
+  if (P) {
+    for (int i = 0; i < nprod; ++i) {
+      Product &q = pend.P.prod[pend.n + i];
+      q = P->prod[i];
+      q.tile_begin = pend.tiles;
+      pend.tiles += q.tiles_m * q.tiles_n;
+    }
+  }
+  pend.n += nprod;
+  pend.flops += flops;
+  pend.additive = pend.additive && additive;
+  pend.rd.insert(pend.rd.end(), rd.begin(), rd.end());
+  pend.wr.insert(pend.wr.end(), wr.begin(), wr.end());
+  if (!merge) flush();
+}
+
+void Exec::flush() {
+  if (pend.n == 0) return;
+  ++leaf_launches;
+  if (!dry) {
+    pend.P.nprod = pend.n;
+    pend.P.total_tiles = pend.tiles;
+    flushing = true;
+    cudaStream_t st = op_begin(pend.rd, pend.wr);
+    flushing = false;
+    if (timing) timing->begin(st);
+    check(launch_gemm_tc(pend.P, mode, num_sms, st), "leaf gemm");
+    if (timing) timing->end(st, pend.flops);
+    op_end();
+  }
+  pend.n = 0;
+  pend.tiles = 0;
+  pend.flops = 0.0;
+  pend.rd.clear();
+  pend.wr.clear();
 }
 
 char *Exec::next_stage() {
@@ -145,6 +213,15 @@ static void fill_common(GemmParams &P, const Exec &x, Scalar alpha, bool acc, Sc
   P.err = x.err;
 }
 
+static void set_scalars(Product &pr, Scalar alpha, bool acc, Scalar beta, int epi) {
+  pr.epilogue = epi;
+  pr.use_beta = acc ? 1 : 0;
+  pr.alpha_u = alpha.u;
+  pr.beta_u = beta.u;
+  pr.alpha_f = alpha.f;
+  pr.beta_f = beta.f;
+}
+
 void Exec::leaf(Scalar alpha, bool acc, Scalar beta, View L, View R, View D) {
   const int64_t m = L.rows, k = L.cols, n = R.cols;
   if (m == 0 || n == 0) return;
@@ -215,10 +292,12 @@ void Exec::leaf_group(Scalar alpha, bool acc, Scalar beta, const LeafJob *jobs, 
     ++leaf_products;
     tflops += 2.0 * m * n * k * limb_products();
   }
-  ++leaf_launches;
   stage_need = std::max(stage_need, total);
   ew_launches += njobs * (fp32 ? 3 : 2);
-  if (dry) return;
+  if (dry) {
+    queue_gemm(nullptr, {}, {}, false, tflops, njobs);
+    return;
+  }
   char *base = next_stage();
   GemmParams P;
   fill_common(P, *this, alpha, acc, beta, EPI_STORE);
@@ -288,6 +367,7 @@ void Exec::leaf_group(Scalar alpha, bool acc, Scalar beta, const LeafJob *jobs, 
     pr.tile_begin = tiles;
     pr.amax = amax;
     pr.terms_a = pr.terms_b = 1;
+    set_scalars(pr, alpha, acc, beta, EPI_STORE);
     tiles += pr.tiles_m * pr.tiles_n;
     grd.push_back(ra);
     grd.push_back(rb);
@@ -296,11 +376,7 @@ void Exec::leaf_group(Scalar alpha, bool acc, Scalar beta, const LeafJob *jobs, 
   }
   P.nprod = njobs;
   P.total_tiles = tiles;
-  cudaStream_t st = op_begin(grd, gwr);
-  if (timing) timing->begin(st);
-  check(launch_gemm_tc(P, mode, num_sms, st), "leaf gemm");
-  if (timing) timing->end(st, tflops);
-  op_end();
+  queue_gemm(&P, grd, gwr, false, tflops, njobs);
 }
 
 // One whole Winograd level (Section 2) with fused pre- and post-additions.
@@ -345,7 +421,6 @@ void Exec::fused_level(Scalar alpha, bool acc, Scalar beta, const Lin &LL, const
   View Dq[4] = {D.quad(0, 0), D.quad(0, 1), D.quad(1, 0), D.quad(1, 1)};
   leaf_flops += 7 * 2 * hm * hn * hk;
   leaf_products += 7;
-  ++leaf_launches;
   // prologue: D <- beta D; nothing when beta = 1, zeros for C <- alpha AB.
   // The products are then added as unreduced representatives (mod p), so D
   // stays lazy until a consumer or the final pass reduces it.
@@ -367,6 +442,7 @@ void Exec::fused_level(Scalar alpha, bool acc, Scalar beta, const Lin &LL, const
   GemmParams P;
   fill_common(P, *this, alpha, false, beta, EPI_REDUCE);
   if (simt) {
+    ++leaf_launches;
     if (!dry) {
       if (LL.n != 1 || RL.n != 1 || LL.s[0] != 1 || RL.s[0] != 1) {
         if (fail.empty()) fail = "SIMT fused level needs materialised operands";
@@ -510,15 +586,14 @@ void Exec::fused_level(Scalar alpha, bool acc, Scalar beta, const Lin &LL, const
         pr.amax = amax;
         pr.terms_a = pa.terms;
         pr.terms_b = pb.terms;
+        set_scalars(pr, alpha, false, beta, EPI_REDUCE);
         tiles += pr.tiles_m * pr.tiles_n;
       }
       P.nprod = 7;
       P.total_tiles = tiles;
-      st = op_begin({ra, rb, rh}, {rect_of(D)});
-      if (timing) timing->begin(st);
-      check(launch_gemm_tc(P, mode, num_sms, st), "fused gemm");
-      if (timing) timing->end(st, 7 * 2.0 * hm * hn * hk * limb_products());
-      op_end();
+      queue_gemm(&P, {ra, rb, rh}, {rect_of(D)}, true, 7 * 2.0 * hm * hn * hk * limb_products(), 7);
+    } else {
+      queue_gemm(nullptr, {}, {}, true, 7 * 2.0 * hm * hn * hk * limb_products(), 7);
     }
   }
 }

@@ -79,6 +79,21 @@ struct Exec {
   int stage_turn = 0;
   // dataflow ordering over capture streams (null: every launch on `stream`)
   Flow *flow = nullptr;
+  // Deferred leaf GEMM launches: products of leaf groups and fused levels
+  // wait in `pend` and independent ones share one launch (merge = true), so
+  // the fixed cost of a launch is paid once for several small levels.  The
+  // pending launch is issued before any operation that touches its memory.
+  bool merge = false;
+  struct Pending {
+    GemmParams P;
+    int n = 0, tiles = 0;
+    double flops = 0.0;
+    bool additive = true;  // every product only reduce-adds into its targets
+    std::vector<Rect> rd, wr;
+  };
+  Pending pend;
+  bool flushing = false;
+  void flush();
 
   // statistics
   int64_t tmp_elems = 0, tmp_peak_elems = 0;
@@ -115,6 +130,8 @@ struct Exec {
   cudaStream_t op_begin(const std::vector<Rect> &rd, const std::vector<Rect> &wr);
   void op_end();
   char *next_stage();
+  void queue_gemm(const GemmParams *P, const std::vector<Rect> &rd, const std::vector<Rect> &wr, bool additive,
+                  double flops, int nprod);
   void fp32_amax(uint32_t *amax, const View *a, int na, const View *b, int nb);
   void scale(View d, bool keep, Scalar beta);  // d <- beta d, or 0
   void check(cudaError_t e, const char *what);

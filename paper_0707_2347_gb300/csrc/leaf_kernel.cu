@@ -590,12 +590,12 @@ __device__ __forceinline__ void modp2_recombine(const Epi &E, const float (&q)[4
 }
 
 // alpha and the sign of a reduction target on 16 mod-p results
-__device__ __forceinline__ void modp_finish(const GemmParams &P, const Epi &E, int sign, uint32_t *v) {
+__device__ __forceinline__ void modp_finish(const Product &pr, const Epi &E, int sign, uint32_t *v) {
 #pragma unroll
   for (int e = 0; e < 16; ++e) {
     uint32_t x = v[e];
-    if (P.alpha_u != 1) x = E.mulmod(P.alpha_u, x);
-    if (P.epilogue == EPI_REDUCE && sign < 0) x = x == 0 ? 0u : E.p - x;
+    if (pr.alpha_u != 1) x = E.mulmod(pr.alpha_u, x);
+    if (pr.epilogue == EPI_REDUCE && sign < 0) x = x == 0 ? 0u : E.p - x;
     v[e] = x;
   }
 }
@@ -603,7 +603,7 @@ __device__ __forceinline__ void modp_finish(const GemmParams &P, const Epi &E, i
 // p < 2^16, one accumulator buffer: the thread's four 16-column groups
 // (tile columns hsel*32 + {0, 16} of both 64-column chunks), with the
 // tensor-memory reads of group g + 1 in flight while group g is recombined.
-__device__ __forceinline__ void modp2_drain_all(const GemmParams &P, const Epi &E, uint32_t d, int hsel, int sign,
+__device__ __forceinline__ void modp2_drain_all(const Product &pr, const Epi &E, uint32_t d, int hsel, int sign,
                                                 uint32_t (&vals)[2][32]) {
   float cur[4][16], nxt[4][16];
 #pragma unroll
@@ -620,7 +620,7 @@ __device__ __forceinline__ void modp2_drain_all(const GemmParams &P, const Epi &
     }
     uint32_t *v = vals[g >> 1] + (g & 1) * 16;
     modp2_recombine(E, cur, v);
-    modp_finish(P, E, sign, v);
+    modp_finish(pr, E, sign, v);
     if (g < 3) {
       tmem_wait_ld();
 #pragma unroll
@@ -637,7 +637,7 @@ __device__ __forceinline__ void modp2_drain_all(const GemmParams &P, const Epi &
 // results (alpha applied; REDUCE: the signed contribution p - v for a
 // negative target) or floats (FP32: alpha applied, sign folded for REDUCE).
 template <int MODE>
-__device__ __forceinline__ void tile_values(const GemmParams &P, const Epi &E, uint32_t d, int col, int sign,
+__device__ __forceinline__ void tile_values(const Product &pr, const Epi &E, uint32_t d, int col, int sign,
                                             uint32_t *v) {
   if (MODE == MODE_MODP2) {
     float q[4][16];
@@ -666,19 +666,19 @@ __device__ __forceinline__ void tile_values(const GemmParams &P, const Epi &E, u
 #pragma unroll
     for (int e = 0; e < 16; ++e) {
       float f = E.fsc * (a[e] + b[e]);
-      if (P.epilogue == EPI_REDUCE && sign < 0) f = -f;
+      if (pr.epilogue == EPI_REDUCE && sign < 0) f = -f;
       v[e] = __float_as_uint(f);
     }
     return;
   }
-  modp_finish(P, E, sign, v);
+  modp_finish(pr, E, sign, v);
 }
 
 // value + beta * c for a STORE with beta (c may be any representative mod p)
 template <int MODE>
-__device__ __forceinline__ uint32_t add_beta(const GemmParams &P, const Epi &E, uint32_t v, uint32_t c) {
-  if (MODE == MODE_FP32) return __float_as_uint(__uint_as_float(v) + P.beta_f * __uint_as_float(c));
-  const uint32_t w = v + E.mulmod(P.beta_u, E.red(c));
+__device__ __forceinline__ uint32_t add_beta(const Product &pr, const Epi &E, uint32_t v, uint32_t c) {
+  if (MODE == MODE_FP32) return __float_as_uint(__uint_as_float(v) + pr.beta_f * __uint_as_float(c));
+  const uint32_t w = v + E.mulmod(pr.beta_u, E.red(c));
   return min(w, w - E.p);
 }
 
@@ -861,9 +861,9 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_kernel(const __grid_constant
       const uint32_t use = C::ACC_BUFS == 2 ? (tcount >> 1) : tcount;
       const uint32_t d = tmem + lane_addr + (uint32_t)(buf * C::BUF_COLS);
       if (MODE == MODE_FP32)
-        E.fsc = P.alpha_f / (fp16_scale(pr.amax[0], pr.terms_a) * fp16_scale(pr.amax[1], pr.terms_b));
+        E.fsc = pr.alpha_f / (fp16_scale(pr.amax[0], pr.terms_a) * fp16_scale(pr.amax[1], pr.terms_b));
       const bool tma = pr.tma_epi != 0;
-      const bool with_beta = P.epilogue == EPI_STORE && P.use_beta;
+      const bool with_beta = pr.epilogue == EPI_STORE && pr.use_beta;
       const int sign = pr.t[0].sign;
       bool bad = false;
       if (modp && nkb > 16) {
@@ -906,12 +906,12 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_kernel(const __grid_constant
       uint32_t vals[HOLD][32];
       if (HOLD > 1) {
         if (MODE == MODE_MODP2 && HOLD == 2) {
-          modp2_drain_all(P, E, d, hsel, sign, *reinterpret_cast<uint32_t(*)[2][32]>(vals));
+          modp2_drain_all(pr, E, d, hsel, sign, *reinterpret_cast<uint32_t(*)[2][32]>(vals));
         } else {
 #pragma unroll
           for (int ch = 0; ch < HOLD; ++ch) {
-            tile_values<MODE>(P, E, d, ch * 64 + hsel * 32, sign, vals[ch]);
-            tile_values<MODE>(P, E, d, ch * 64 + hsel * 32 + 16, sign, vals[ch] + 16);
+            tile_values<MODE>(pr, E, d, ch * 64 + hsel * 32, sign, vals[ch]);
+            tile_values<MODE>(pr, E, d, ch * 64 + hsel * 32 + 16, sign, vals[ch] + 16);
           }
         }
         tc_fence_before();
@@ -922,8 +922,8 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_kernel(const __grid_constant
         const int tc0 = ch * 64 + hsel * 32;  // tile column of this thread's first value
         uint32_t *v = vals[HOLD > 1 ? ch : 0];
         if (HOLD == 1) {
-          tile_values<MODE>(P, E, d, tc0, sign, v);
-          tile_values<MODE>(P, E, d, tc0 + 16, sign, v + 16);
+          tile_values<MODE>(pr, E, d, tc0, sign, v);
+          tile_values<MODE>(pr, E, d, tc0 + 16, sign, v + 16);
           if (ch == NCH - 1) {
             tc_fence_before();
             mbar_arrive(&acc_empty[buf]);  // accumulators free for the next tile
@@ -953,10 +953,10 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_kernel(const __grid_constant
             uint4 w = make_uint4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
             if (with_beta) {
               const uint4 c = lds128(a);
-              w.x = add_beta<MODE>(P, E, w.x, c.x);
-              w.y = add_beta<MODE>(P, E, w.y, c.y);
-              w.z = add_beta<MODE>(P, E, w.z, c.z);
-              w.w = add_beta<MODE>(P, E, w.w, c.w);
+              w.x = add_beta<MODE>(pr, E, w.x, c.x);
+              w.y = add_beta<MODE>(pr, E, w.y, c.y);
+              w.z = add_beta<MODE>(pr, E, w.z, c.z);
+              w.w = add_beta<MODE>(pr, E, w.w, c.w);
             }
             sts128(a, w);
           }
@@ -970,7 +970,7 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_kernel(const __grid_constant
             for (int b = 0; b < 2; ++b) {
               const int x = ti.n0 + ch * 64 + 32 * b;
               if (x >= pr.N) break;
-              if (P.epilogue == EPI_STORE) {
+              if (pr.epilogue == EPI_STORE) {
                 tma_store(&pr.tmap[0], x, ti.m0, eb + b * 16384);
               } else {
                 for (int t = 0; t < pr.ntargets; ++t) tma_reduce_add(&pr.tmap[t], x, ti.m0, eb + b * 16384);
@@ -1003,9 +1003,9 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_kernel(const __grid_constant
               if (g_c >= pr.N) continue;
               const uint32_t x =
                   lds32(eb + h2 * 16384 + rr * 128 + ((((c & 31) >> 2) ^ (rr & 7)) << 4) + (c & 3) * 4);
-              if (P.epilogue == EPI_STORE) {
+              if (pr.epilogue == EPI_STORE) {
                 uint32_t *dst = reinterpret_cast<uint32_t *>((char *)pr.t[0].ptr) + (int64_t)g_r * pr.t[0].ld + g_c;
-                *dst = with_beta ? add_beta<MODE>(P, E, x, *dst) : x;
+                *dst = with_beta ? add_beta<MODE>(pr, E, x, *dst) : x;
               } else {
                 for (int t = 0; t < pr.ntargets; ++t) {
                   if (modp)

@@ -86,7 +86,7 @@ cudaError_t launch_pack(const PackArgs &a, int mode, cudaStream_t s);
 // canonical contribution, p - v for a negative sign, added as an unsigned
 // integer, so targets hold representatives that are reduced later).
 constexpr int kMaxTargets = 4;
-constexpr int kMaxProducts = 16;  // 7 for a fused level; up to 16 classical leaves of a batch
+constexpr int kMaxProducts = 21;  // 7 per fused level (3 merged), or up to 21 classical leaves
 
 struct Target {
   void *ptr;
@@ -110,10 +110,18 @@ struct Product {
   // product's packs, to undo their scales in the epilogue
   const uint32_t *amax;  // [2]: A side, B side
   int32_t terms_a, terms_b;
+  // scalars and epilogue of this product (one launch may hold products of
+  // different calls): STORE t0 <- alpha P (+ beta t0 when use_beta), or
+  // REDUCE every target += sign alpha P
+  int32_t epilogue, use_beta;
+  uint32_t alpha_u, beta_u;
+  float alpha_f, beta_f;
 };
 
 enum Epilogue : int { EPI_STORE = 0, EPI_REDUCE = 1 };
 
+// The scalar and epilogue fields here serve the SIMT diagnostic leaf; the
+// tensor-core kernel reads the per-product copies.
 struct GemmParams {
   Product prod[kMaxProducts];
   int32_t nprod;

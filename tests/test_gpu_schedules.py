@@ -243,3 +243,20 @@ def test_fp32_scaling_handles_large_and_small_magnitudes(handle):
         handle.sync()
         err = probes.fp_error(host(dC), classical.mul_f64(A2, B2), A2, B2)["max_rel"]
         assert err <= probes.fp_bound(n), (sa, sb, err)
+
+
+@pytest.mark.parametrize("graph", [False, True], ids=["eager", "graph"])
+def test_small_fused_levels_share_launches(handle, graph):
+    """Table 9 depth 3 at 2048^2: 49 fused levels of 7 x 256^3 products; the
+    independent ones (different targets, or reduce-adds into one target)
+    share grouped launches, and the result stays exact."""
+    p, n = 65521, 2048
+    A, B, C = modp_inputs(n, n, n, p, tag=31)
+    dC = dev(C)
+    o = S.Opts(mode=S.MODP, p=p, sched=S.T9_ACC, depth=3, flags=S.FLAG_GRAPH if graph else 0)
+    handle.muladd(3, dev(A), dev(B), 5, dC, o)
+    handle.sync()
+    assert np.array_equal(host(dC), classical.muladd_modp(3, A, B, 5, C, p))
+    st = handle.stats()
+    assert st["leaf_products"] == 343
+    assert st["leaf_launches"] < 49
