@@ -359,7 +359,6 @@ constexpr int kEpiThreads = 256;
 constexpr int kChunkKB = 15;                  // k-blocks between in-place reductions
 constexpr uint64_t kWaitNs = 4000000000ull;  // bounded wait: 4 s
 constexpr int kPlaneBytes = kBM * kBK * 2;    // 16 KB
-constexpr int kBBytes = 256 * kBK * 2;        // 32 KB
 constexpr int kEpiBytes = 2 * kBM * 32 * 4;   // 32 KB: 128 rows x 64 columns, 2 boxes of 32
 
 template <int MODE>
@@ -370,15 +369,20 @@ struct Cfg<MODE_MODP1> {
 };
 template <>
 struct Cfg<MODE_MODP2> {
-  static constexpr int BN = 128, A_PLANES = 2, STAGES = 3, ACC_BUFS = 1, BUF_COLS = 512;
+  static constexpr int BN = kModp2BN, A_PLANES = 2, STAGES = kModp2BN == 64 ? 4 : 3;
+  static constexpr int ACC_BUFS = kModp2BN == 64 ? 2 : 1, BUF_COLS = 4 * kModp2BN;
 };
 template <>
 struct Cfg<MODE_FP32> {
   static constexpr int BN = 128, A_PLANES = 2, STAGES = 3, ACC_BUFS = 2, BUF_COLS = 256;
 };
 template <int MODE>
+__host__ __device__ constexpr int b_rows() {  // B rows per stage: one plane (p <= 256) or [hi | lo]
+  return MODE == MODE_MODP1 ? Cfg<MODE>::BN : 2 * Cfg<MODE>::BN;
+}
+template <int MODE>
 __host__ __device__ constexpr int stage_bytes() {
-  return Cfg<MODE>::A_PLANES * kPlaneBytes + kBBytes;
+  return Cfg<MODE>::A_PLANES * kPlaneBytes + b_rows<MODE>() * kBK * 2;
 }
 template <int MODE>
 __host__ __device__ constexpr int smem_bytes() {
@@ -607,7 +611,7 @@ __device__ __forceinline__ void modp2_drain_all(const Product &pr, const Epi &E,
                                                 uint32_t (&vals)[2][32]) {
   float cur[4][16], nxt[4][16];
 #pragma unroll
-  for (int i = 0; i < 4; ++i) tmem_ld16(d + 128 * i + hsel * 32, cur[i]);
+  for (int i = 0; i < 4; ++i) tmem_ld16(d + kModp2BN * i + hsel * 32, cur[i]);
   tmem_wait_ld();
 #pragma unroll
   for (int i = 0; i < 4; ++i) reg_fence16(cur[i]);
@@ -616,7 +620,7 @@ __device__ __forceinline__ void modp2_drain_all(const Product &pr, const Epi &E,
     if (g < 3) {
       const int col = ((g + 1) >> 1) * 64 + hsel * 32 + ((g + 1) & 1) * 16;
 #pragma unroll
-      for (int i = 0; i < 4; ++i) tmem_ld16(d + 128 * i + col, nxt[i]);
+      for (int i = 0; i < 4; ++i) tmem_ld16(d + kModp2BN * i + col, nxt[i]);
     }
     uint32_t *v = vals[g >> 1] + (g & 1) * 16;
     modp2_recombine(E, cur, v);
@@ -642,9 +646,9 @@ __device__ __forceinline__ void tile_values(const Product &pr, const Epi &E, uin
   if (MODE == MODE_MODP2) {
     float q[4][16];
     tmem_ld16(d + col, q[0]);
-    tmem_ld16(d + 128 + col, q[1]);
-    tmem_ld16(d + 256 + col, q[2]);
-    tmem_ld16(d + 384 + col, q[3]);
+    tmem_ld16(d + kModp2BN + col, q[1]);
+    tmem_ld16(d + 2 * kModp2BN + col, q[2]);
+    tmem_ld16(d + 3 * kModp2BN + col, q[3]);
     tmem_wait_ld();
 #pragma unroll
     for (int i = 0; i < 4; ++i) reg_fence16(q[i]);
@@ -757,7 +761,7 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_kernel(const __grid_constant
             tma_load(sB, &pr.tb, k0, ti.n0, &full[stage]);  // 256-row box
           } else {
             tma_load(sB, &pr.tb, k0, ti.n0, &full[stage]);
-            tma_load(sB + kPlaneBytes, &pr.tb, k0, pr.b_plane_rows + ti.n0, &full[stage]);
+            tma_load(sB + C::BN * kBK * 2, &pr.tb, k0, pr.b_plane_rows + ti.n0, &full[stage]);
           }
           if (++stage == C::STAGES) {
             stage = 0;
@@ -774,6 +778,7 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_kernel(const __grid_constant
       const uint32_t fmt = 0;  // fp16 operands in every mode
       const uint32_t id256 = idesc_f16(fmt, kBM, 256);
       const uint32_t id128 = idesc_f16(fmt, kBM, 128);
+      const uint32_t idB2 = idesc_f16(fmt, kBM, 2 * BN);  // N = [hi | lo] rows of B
       int stage = 0;
       uint32_t phase = 0, tcount = 0, dcount = 0;
       for (int g = blockIdx.x; g < P.total_tiles; g += gridDim.x, ++tcount) {
@@ -803,8 +808,8 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_kernel(const __grid_constant
               tc_mma(d, a0, bd, id256, acc);
             } else if (MODE == MODE_MODP2) {
               const uint64_t a1 = sdesc(sA + kPlaneBytes + 32 * k);
-              tc_mma(d, a0, bd, id256, acc);        // [hh | hl]
-              tc_mma(d + 256, a1, bd, id256, acc);  // [lh | ll]
+              tc_mma(d, a0, bd, idB2, acc);           // [hh | hl]
+              tc_mma(d + 2 * BN, a1, bd, idB2, acc);  // [lh | ll]
             } else {
               const uint64_t a1 = sdesc(sA + kPlaneBytes + 32 * k);
               tc_mma(d, a0, bd, id256, acc);       // [hi*hi | hi*lo]
@@ -876,7 +881,7 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_kernel(const __grid_constant
             break;
           }
           tc_fence_after();
-          constexpr int cols = MODE == MODE_MODP2 ? 512 : 256;
+          constexpr int cols = MODE == MODE_MODP2 ? 4 * BN : 256;
           for (int c = hsel * (cols / 2); c < (hsel + 1) * (cols / 2); c += 32) {
             float v[32];
             tmem_ld16(d + c, v);

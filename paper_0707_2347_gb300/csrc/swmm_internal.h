@@ -31,11 +31,18 @@ struct View {
 };
 
 // Leaf arithmetic: one fp16 limb (p <= 256), two fp16 limbs (p < 2^16), or
-// bf16 hi/lo of a float (FP32 mode).
+// fp16 hi/lo of a scaled float (FP32 mode).
 enum Mode : int { MODE_MODP1 = 0, MODE_MODP2 = 1, MODE_FP32 = 2 };
 
+// Output columns of a leaf tile for p < 2^16.  Its four limb products need
+// 4 x BN tensor-memory columns: BN = 128 fills the 512 columns with one
+// accumulator (the next tile's MMAs wait for the epilogue to read it out);
+// BN = 64 leaves room for two, but its N = 128 MMAs and twice the A-tile
+// reloads ran the classical product at 1263 instead of 1788 TFLOP/s.
+constexpr int kModp2BN = 128;
+
 inline int planes_of(int mode) { return mode == MODE_MODP1 ? 1 : 2; }
-inline int bn_of(int mode) { return mode == MODE_MODP1 ? 256 : 128; }
+inline int bn_of(int mode) { return mode == MODE_MODP1 ? 256 : (mode == MODE_MODP2 ? kModp2BN : 128); }
 constexpr int kBM = 128;  // leaf tile rows
 constexpr int kBK = 64;   // leaf k-block (64 halves = one 128-byte row)
 
