@@ -293,7 +293,7 @@ void Exec::leaf_group(Scalar alpha, bool acc, Scalar beta, const LeafJob *jobs, 
     tflops += 2.0 * m * n * k * limb_products();
   }
   stage_need = std::max(stage_need, total);
-  ew_launches += njobs * (fp32 ? 3 : 2);
+  ew_launches += njobs * (fp32 ? 2 : 1);
   if (dry) {
     queue_gemm(nullptr, {}, {}, false, tflops, njobs);
     return;
@@ -331,20 +331,18 @@ void Exec::leaf_group(Scalar alpha, bool acc, Scalar beta, const LeafJob *jobs, 
     pa.barrett = p ? (uint32_t)(0x100000000ull / p) : 0;
     pa.amax = amax;
     pa.terms = 1;
-    cudaStream_t st = op_begin({rect_of(L), rh}, {ra});
-    check(launch_pack(pa, mode, st), "pack A");
-    op_end();
-    pa.src[0][0] = R.ptr;
-    pa.ld[0][0] = R.ld;
-    pa.out[0] = Bp;
-    pa.rows = (int)k;
-    pa.cols = (int)n;
-    pa.prow_pad = (int)Np[i];
-    pa.pcol_pad = (int)Kp[i];
-    pa.transpose = 1;
-    pa.amax = amax ? amax + 1 : nullptr;
-    st = op_begin({rect_of(R), rh}, {rb});
-    check(launch_pack(pa, mode, st), "pack B");
+    PackArgs pb = pa;
+    pb.src[0][0] = R.ptr;
+    pb.ld[0][0] = R.ld;
+    pb.out[0] = Bp;
+    pb.rows = (int)k;
+    pb.cols = (int)n;
+    pb.prow_pad = (int)Np[i];
+    pb.pcol_pad = (int)Kp[i];
+    pb.transpose = 1;
+    pb.amax = amax ? amax + 1 : nullptr;
+    cudaStream_t st = op_begin({rect_of(L), rect_of(R), rh}, {ra, rb});
+    check(launch_pack_pair(pa, pb, mode, st), "pack");
     op_end();
     Product &pr = P.prod[i];
     if (!make_tmap(&pr.ta, Ap, pl * Mp[i], Kp[i], kBM) || !make_tmap(&pr.tb, Bp, pl * Np[i], Kp[i], bn)) {
@@ -484,7 +482,7 @@ void Exec::fused_level(Scalar alpha, bool acc, Scalar beta, const Lin &LL, const
     const int64_t abytes = rup(pl * Mp * Kp * 2, 1024), bbytes = rup(pl * Np * Kp * 2, 1024);
     const int64_t hdr = fp32 ? 1024 : 0;  // FP32 mode: the operands' amax words
     stage_need = std::max(stage_need, hdr + 7 * (abytes + bbytes));
-    ew_launches += fp32 ? 3 : 2;
+    ew_launches += fp32 ? 2 : 1;
     if (!dry) {
       char *base = next_stage();
       uint32_t *amax = fp32 ? reinterpret_cast<uint32_t *>(base) : nullptr;
@@ -550,11 +548,10 @@ void Exec::fused_level(Scalar alpha, bool acc, Scalar beta, const Lin &LL, const
       pb.amax = amax ? amax + 1 : nullptr;
       pa.terms = 4 * LL.n;
       pb.terms = 4 * RL.n;
-      cudaStream_t st = op_begin(rdA, {ra});
-      check(launch_pack(pa, mode, st), "fused pack A");
-      op_end();
-      st = op_begin(rdB, {rb});
-      check(launch_pack(pb, mode, st), "fused pack B");
+      std::vector<Rect> rdAB = rdA;
+      rdAB.insert(rdAB.end(), rdB.begin(), rdB.end());
+      cudaStream_t st = op_begin(rdAB, {ra, rb});
+      check(launch_pack_pair(pa, pb, mode, st), "fused pack");
       op_end();
       int tiles = 0;
       for (int i = 0; i < 7; ++i) {

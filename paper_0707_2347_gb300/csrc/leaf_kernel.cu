@@ -262,11 +262,11 @@ __device__ __forceinline__ void load_source(const PackArgs &a, int q, int r, int
 // plain layout: thread = 8 consecutive columns of one row; every source
 // value is loaded and reduced once, then combined for each output.
 template <int MODE, int SET>
-__global__ void __launch_bounds__(256) pack_rows_kernel(const __grid_constant__ PackArgs a) {
+__device__ __forceinline__ void pack_rows_body(const PackArgs &a, int block, int nblocks) {
   const int64_t units = (int64_t)a.prow_pad * (a.pcol_pad / 8);
   const int64_t plane = (int64_t)a.prow_pad * a.pcol_pad;
   const float fs = MODE == MODE_FP32 ? fp16_scale(*a.amax, a.terms) : 1.f;
-  for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < units; u += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t u = block * (int64_t)blockDim.x + threadIdx.x; u < units; u += (int64_t)nblocks * blockDim.x) {
     const int r = (int)(u / (a.pcol_pad / 8));
     const int c0 = (int)(u - (int64_t)r * (a.pcol_pad / 8)) * 8;
     uint32_t v[kMaxSrc][8];
@@ -282,15 +282,18 @@ __global__ void __launch_bounds__(256) pack_rows_kernel(const __grid_constant__ 
     emit_all<MODE, SET>(a, v, (int64_t)r * a.pcol_pad + c0, plane, fs);
   }
 }
+template <int MODE, int SET>
+__global__ void __launch_bounds__(256) pack_rows_kernel(const __grid_constant__ PackArgs a) {
+  pack_rows_body<MODE, SET>(a, blockIdx.x, gridDim.x);
+}
 
 // transposed layout: a CTA stages a 32 (source rows) x 64 (source cols) tile
 // of every source in shared memory (reduced once), then each thread reads
 // its 8 source rows of one source column and writes packed row = column.
 template <int MODE, int SET>
-__global__ void __launch_bounds__(256) pack_cols_kernel(const __grid_constant__ PackArgs a) {
-  __shared__ uint32_t tile[kMaxSrc][32][65];
-  const int r0 = blockIdx.y * 32;  // source rows = packed columns (K)
-  const int c0 = blockIdx.x * 64;  // source cols = packed rows (N)
+__device__ __forceinline__ void pack_cols_body(const PackArgs &a, uint32_t (&tile)[kMaxSrc][32][65], int bx, int by) {
+  const int r0 = by * 32;  // source rows = packed columns (K)
+  const int c0 = bx * 64;  // source cols = packed rows (N)
   const int t = threadIdx.x;
   const int64_t plane = (int64_t)a.prow_pad * a.pcol_pad;
   const float fs = MODE == MODE_FP32 ? fp16_scale(*a.amax, a.terms) : 1.f;
@@ -314,6 +317,25 @@ __global__ void __launch_bounds__(256) pack_cols_kernel(const __grid_constant__ 
     for (int e = 0; e < 8; ++e) v[q][e] = q < a.nsrc ? tile[q][pr8 + e][pc] : 0u;
   }
   emit_all<MODE, SET>(a, v, (int64_t)(c0 + pc) * a.pcol_pad + r0 + pr8, plane, fs);
+}
+template <int MODE, int SET>
+__global__ void __launch_bounds__(256) pack_cols_kernel(const __grid_constant__ PackArgs a) {
+  __shared__ uint32_t tile[kMaxSrc][32][65];
+  pack_cols_body<MODE, SET>(a, tile, blockIdx.x, blockIdx.y);
+}
+
+// both operands of a product (or of a fused level) in one launch: blocks
+// [0, na) pack a (plain layout), the rest pack b (transposed), tile by tile
+template <int MODE, int SA, int SB>
+__global__ void __launch_bounds__(256) pack_pair_kernel(const __grid_constant__ PackArgs a,
+                                                        const __grid_constant__ PackArgs b, int na, int tiles_x) {
+  __shared__ uint32_t tile[kMaxSrc][32][65];
+  if ((int)blockIdx.x < na) {
+    pack_rows_body<MODE, SA>(a, blockIdx.x, na);
+  } else {
+    const int i = (int)blockIdx.x - na;
+    pack_cols_body<MODE, SB>(b, tile, i % tiles_x, i / tiles_x);
+  }
 }
 
 // FP32 mode: max |x| over the sources of each side (blockIdx.y), one row per
@@ -560,6 +582,15 @@ struct Epi {
   uint32_t p, m;
   float pf, inv_p;
   float fsc;  // FP32 mode: alpha / (s_A s_B), undoing the operand scales
+  // mod p, reductions with alpha = +-1: the contribution sign (+1 / -1) folded
+  // into a lazy representative p +- r in [p/2, 3p/2]; 0: canonical value,
+  // then alpha and the sign
+  int lsg;
+  __device__ __forceinline__ uint32_t out(float r) const {  // r = fr(...) in [-p/2, p/2]
+    if (lsg == 0) return canon(r);
+    const float x = lsg > 0 ? pf + r : pf - r;
+    return __float_as_uint(x + 12582912.0f) - 0x4B400000u;
+  }
   __device__ __forceinline__ float fr(float f) const {  // centred residue, exact |f| <= 2^24
     const float MAGIC = 12582912.0f;                     // 1.5 * 2^23: rint via addition
     float q = __fmaf_rn(f, inv_p, MAGIC) - MAGIC;
@@ -589,12 +620,14 @@ __device__ __forceinline__ void modp2_recombine(const Epi &E, const float (&q)[4
   for (int e = 0; e < 16; ++e) {
     const float s = E.fr(E.fr(q[1][e]) + E.fr(q[2][e]));
     const float t1 = E.fr(__fmaf_rn(256.f, E.fr(q[0][e]), s));
-    v[e] = E.canon(E.fr(__fmaf_rn(256.f, t1, E.fr(q[3][e]))));
+    v[e] = E.out(E.fr(__fmaf_rn(256.f, t1, E.fr(q[3][e]))));
   }
 }
 
-// alpha and the sign of a reduction target on 16 mod-p results
+// alpha and the sign of a reduction target on 16 mod-p results (nothing
+// left to do when they were folded into lazy representatives)
 __device__ __forceinline__ void modp_finish(const Product &pr, const Epi &E, int sign, uint32_t *v) {
+  if (E.lsg != 0) return;
 #pragma unroll
   for (int e = 0; e < 16; ++e) {
     uint32_t x = v[e];
@@ -659,7 +692,7 @@ __device__ __forceinline__ void tile_values(const Product &pr, const Epi &E, uin
     tmem_wait_ld();
     reg_fence16(a);
 #pragma unroll
-    for (int e = 0; e < 16; ++e) v[e] = E.canon(E.fr(a[e]));
+    for (int e = 0; e < 16; ++e) v[e] = E.out(E.fr(a[e]));
   } else {
     float a[16], b[16];
     tmem_ld16(d + col, a);
@@ -857,6 +890,7 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_kernel(const __grid_constant
     E.pf = (float)P.p;
     E.inv_p = P.inv_p;
     E.fsc = 0.f;
+    E.lsg = 0;
     uint32_t tcount = 0, dcount = 0, cphase = 0;
     for (int g = blockIdx.x; g < P.total_tiles; g += gridDim.x, ++tcount) {
       const TileInfo ti = decode<BN>(P, g);
@@ -867,6 +901,10 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_kernel(const __grid_constant
       const uint32_t d = tmem + lane_addr + (uint32_t)(buf * C::BUF_COLS);
       if (MODE == MODE_FP32)
         E.fsc = pr.alpha_f / (fp16_scale(pr.amax[0], pr.terms_a) * fp16_scale(pr.amax[1], pr.terms_b));
+      if (modp) {
+        const bool unit = pr.alpha_u == 1 || pr.alpha_u == P.p - 1;
+        E.lsg = (pr.epilogue == EPI_REDUCE && unit) ? (((pr.t[0].sign < 0) != (pr.alpha_u != 1)) ? -1 : 1) : 0;
+      }
       const bool tma = pr.tma_epi != 0;
       const bool with_beta = pr.epilogue == EPI_STORE && pr.use_beta;
       const int sign = pr.t[0].sign;
@@ -1125,6 +1163,36 @@ static cudaError_t pack_mode(const PackArgs &a, cudaStream_t s) {
   if (a.set == PACK_WINOGRAD_B && quads) return pack_set<MODE, PACK_WINOGRAD_B>(a, s);
   if (a.set != PACK_GENERIC) return cudaErrorInvalidValue;
   return pack_set<MODE, PACK_GENERIC>(a, s);
+}
+
+template <int MODE, int SA, int SB>
+static cudaError_t pair_sets(const PackArgs &a, const PackArgs &b, cudaStream_t s) {
+  const int64_t units = (int64_t)a.prow_pad * (a.pcol_pad / 8);
+  const int64_t want = (units + 255) / 256;
+  const int na = (int)(want > 152 * 16 ? 152 * 16 : want);
+  const int tiles_x = b.prow_pad / 64, tiles = tiles_x * (b.pcol_pad / 32);
+  if (na + tiles <= 0) return cudaSuccess;
+  dev::pack_pair_kernel<MODE, SA, SB><<<na + tiles, 256, 0, s>>>(a, b, na, tiles_x);
+  return cudaGetLastError();
+}
+template <int MODE>
+static cudaError_t pair_mode(const PackArgs &a, const PackArgs &b, cudaStream_t s) {
+  const bool quads = a.nsrc == 4 && a.nout == 7 && b.nsrc == 4 && b.nout == 7;
+  if (a.set == PACK_WINOGRAD_A && b.set == PACK_WINOGRAD_B && quads)
+    return pair_sets<MODE, PACK_WINOGRAD_A, PACK_WINOGRAD_B>(a, b, s);
+  if (a.set != PACK_GENERIC || b.set != PACK_GENERIC) return cudaErrorInvalidValue;
+  return pair_sets<MODE, PACK_GENERIC, PACK_GENERIC>(a, b, s);
+}
+
+cudaError_t launch_pack_pair(const PackArgs &a, const PackArgs &b, int mode, cudaStream_t s) {
+  if (a.transpose || !b.transpose || a.prow_pad == 0 || a.pcol_pad == 0 || b.prow_pad == 0 || b.pcol_pad == 0)
+    return cudaErrorInvalidValue;
+  switch (mode) {
+    case MODE_MODP1: return pair_mode<MODE_MODP1>(a, b, s);
+    case MODE_MODP2: return pair_mode<MODE_MODP2>(a, b, s);
+    case MODE_FP32: return pair_mode<MODE_FP32>(a, b, s);
+  }
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_amax(const AmaxArgs &a, cudaStream_t s) {
