@@ -670,6 +670,51 @@ __device__ __forceinline__ void modp2_drain_all(const Product &pr, const Epi &E,
   }
 }
 
+// p < 2^16, one accumulator buffer, released in two halves: columns
+// [0, 2 BN) hold hh | hl and [2 BN, 4 BN) hold lh | ll.  First every
+// X = fr(2^8 fr(hh) + fr(hl)) of the thread's 64 columns is formed and the
+// first half released (the next tile's A_h products may start), then
+// v = fr(2^8 fr(X + fr(lh)) + fr(ll)) = 2^16 hh + 2^8 (hl + lh) + ll mod p
+// and the second half released.  Every intermediate is an exact fp32
+// integer (below 2^24).
+__device__ __forceinline__ void modp2_drain_split(const Product &pr, const Epi &E, uint32_t d, int hsel, int sign,
+                                                  uint32_t (&vals)[2][32], uint64_t *half0, uint64_t *half1) {
+  float X[4][16];
+#pragma unroll
+  for (int g = 0; g < 4; ++g) {
+    const int col = (g >> 1) * 64 + hsel * 32 + (g & 1) * 16;
+    float a[16], b[16];
+    tmem_ld16(d + col, a);
+    tmem_ld16(d + kModp2BN + col, b);
+    tmem_wait_ld();
+    reg_fence16(a);
+    reg_fence16(b);
+#pragma unroll
+    for (int e = 0; e < 16; ++e) X[g][e] = E.fr(__fmaf_rn(256.f, E.fr(a[e]), E.fr(b[e])));
+  }
+  tc_fence_before();
+  mbar_arrive(half0);
+#pragma unroll
+  for (int g = 0; g < 4; ++g) {
+    const int col = (g >> 1) * 64 + hsel * 32 + (g & 1) * 16;
+    float a[16], b[16];
+    tmem_ld16(d + 2 * kModp2BN + col, a);
+    tmem_ld16(d + 3 * kModp2BN + col, b);
+    tmem_wait_ld();
+    reg_fence16(a);
+    reg_fence16(b);
+    uint32_t *v = vals[g >> 1] + (g & 1) * 16;
+#pragma unroll
+    for (int e = 0; e < 16; ++e) {
+      const float y = E.fr(X[g][e] + E.fr(a[e]));
+      v[e] = E.out(E.fr(__fmaf_rn(256.f, y, E.fr(b[e]))));
+    }
+    modp_finish(pr, E, sign, v);
+  }
+  tc_fence_before();
+  mbar_arrive(half1);
+}
+
 // Values of 16 consecutive columns of one row before any beta term: mod p
 // results (alpha applied; REDUCE: the signed contribution p - v for a
 // negative target) or floats (FP32: alpha applied, sign folded for REDUCE).
@@ -726,6 +771,8 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_kernel(const __grid_constant
   constexpr int BN = C::BN;
   constexpr int SB = stage_bytes<MODE>();
   constexpr bool modp = MODE != MODE_FP32;
+  // p < 2^16 with one accumulator buffer: released in two halves
+  constexpr bool SPLIT = MODE == MODE_MODP2 && C::ACC_BUFS == 1;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   unsigned char *ebuf = smem + C::STAGES * SB;  // epilogue tile, 4 swizzled boxes
@@ -824,7 +871,51 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_kernel(const __grid_constant
         tc_fence_after();
         const uint32_t d = tmem + (uint32_t)(buf * C::BUF_COLS);
         bool bad = false;
-        for (int kb = 0; kb < nkb; ++kb) {
+        int kb = 0;
+        if (SPLIT) {
+          // The first half (hh | hl) is free: issue the A_h products of the
+          // k-blocks already staged, then wait for the second half (lh | ll)
+          // and issue their A_l products, releasing the stages.
+          const int pre = nkb < C::STAGES ? nkb : C::STAGES;
+          const int stage0 = stage;
+          const uint32_t phase0 = phase;
+          for (int j = 0; j < pre && !bad; ++j) {
+            if (!wait_bar(&full[stage], phase, ctl, P.err)) {
+              bad = true;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t sA = smem_u32(smem + stage * SB);
+            const uint32_t sB = sA + C::A_PLANES * kPlaneBytes;
+#pragma unroll
+            for (int k = 0; k < kBK / 16; ++k)
+              tc_mma(d, sdesc(sA + 32 * k), sdesc(sB + 32 * k), idB2, (j > 0 || k > 0) ? 1u : 0u);
+            if (++stage == C::STAGES) {
+              stage = 0;
+              phase ^= 1;
+            }
+          }
+          if (!bad && !wait_bar(&acc_empty[1], (use & 1) ^ 1, ctl, P.err)) bad = true;
+          if (bad) break;
+          tc_fence_after();
+          stage = stage0;
+          phase = phase0;
+          for (int j = 0; j < pre; ++j) {
+            const uint32_t sA = smem_u32(smem + stage * SB);
+            const uint32_t sB = sA + C::A_PLANES * kPlaneBytes;
+#pragma unroll
+            for (int k = 0; k < kBK / 16; ++k)
+              tc_mma(d + 2 * BN, sdesc(sA + kPlaneBytes + 32 * k), sdesc(sB + 32 * k), idB2,
+                     (j > 0 || k > 0) ? 1u : 0u);
+            tc_commit(&empty[stage]);
+            if (++stage == C::STAGES) {
+              stage = 0;
+              phase ^= 1;
+            }
+          }
+          kb = pre;
+        }
+        for (; kb < nkb; ++kb) {
           if (!wait_bar(&full[stage], phase, ctl, P.err)) {
             bad = true;
             break;
@@ -948,17 +1039,19 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_kernel(const __grid_constant
       constexpr int HOLD = C::ACC_BUFS == 1 ? NCH : 1;
       uint32_t vals[HOLD][32];
       if (HOLD > 1) {
-        if (MODE == MODE_MODP2 && HOLD == 2) {
-          modp2_drain_all(pr, E, d, hsel, sign, *reinterpret_cast<uint32_t(*)[2][32]>(vals));
+        if (SPLIT) {
+          // the two halves of the accumulator are released one after the other
+          modp2_drain_split(pr, E, d, hsel, sign, *reinterpret_cast<uint32_t(*)[2][32]>(vals), &acc_empty[0],
+                            &acc_empty[1]);
         } else {
 #pragma unroll
           for (int ch = 0; ch < HOLD; ++ch) {
             tile_values<MODE>(pr, E, d, ch * 64 + hsel * 32, sign, vals[ch]);
             tile_values<MODE>(pr, E, d, ch * 64 + hsel * 32 + 16, sign, vals[ch] + 16);
           }
+          tc_fence_before();
+          mbar_arrive(&acc_empty[buf]);  // accumulators free for the next tile
         }
-        tc_fence_before();
-        mbar_arrive(&acc_empty[buf]);  // accumulators free for the next tile
       }
 #pragma unroll
       for (int ch = 0; ch < NCH; ++ch) {
