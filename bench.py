@@ -83,11 +83,13 @@ WORKLOADS = {
 }
 DEFAULT = "t9_8192_p65521"
 
-# DRAM bytes (read + write) per leaf GEMM launch from one ncu capture of the
-# same kernel build on a launch of the same shape (7 products of 1024^3,
-# the 2048^2 depth-1 workload); see
-# profiles/gemm_kernel_fused_level_7x1024_p65521.md.
-TRAFFIC = {"t9_8192_p65521": 77.1e6, "t9_2048_p65521_d1": 77.1e6}
+# DRAM bytes (read + write) per leaf GEMM launch.  One ncu capture of the
+# same kernel build on one fused level (7 products of 1024^3, the 2048^2
+# depth-1 workload) read 75.6 MB and wrote 2.2 MB; the 8192^2 depth-3 step
+# merges its 49 fused levels into 27 launches, and the traffic per fused
+# level is the same operands and targets, so the average launch moves
+# 77.8 MB x 49 / 27.  See profiles/gemm_kernel_fused_level_7x1024_p65521.md.
+TRAFFIC = {"t9_8192_p65521": 77.8e6 * 49 / 27, "t9_2048_p65521_d1": 77.8e6}
 
 
 def peaks():
