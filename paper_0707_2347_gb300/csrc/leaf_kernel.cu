@@ -282,10 +282,6 @@ __device__ __forceinline__ void pack_rows_body(const PackArgs &a, int block, int
     emit_all<MODE, SET>(a, v, (int64_t)r * a.pcol_pad + c0, plane, fs);
   }
 }
-template <int MODE, int SET>
-__global__ void __launch_bounds__(256) pack_rows_kernel(const __grid_constant__ PackArgs a) {
-  pack_rows_body<MODE, SET>(a, blockIdx.x, gridDim.x);
-}
 
 // transposed layout: a CTA stages a 32 (source rows) x 64 (source cols) tile
 // of every source in shared memory (reduced once), then each thread reads
@@ -317,11 +313,6 @@ __device__ __forceinline__ void pack_cols_body(const PackArgs &a, uint32_t (&til
     for (int e = 0; e < 8; ++e) v[q][e] = q < a.nsrc ? tile[q][pr8 + e][pc] : 0u;
   }
   emit_all<MODE, SET>(a, v, (int64_t)(c0 + pc) * a.pcol_pad + r0 + pr8, plane, fs);
-}
-template <int MODE, int SET>
-__global__ void __launch_bounds__(256) pack_cols_kernel(const __grid_constant__ PackArgs a) {
-  __shared__ uint32_t tile[kMaxSrc][32][65];
-  pack_cols_body<MODE, SET>(a, tile, blockIdx.x, blockIdx.y);
 }
 
 // both operands of a product (or of a fused level) in one launch: blocks
@@ -634,39 +625,6 @@ __device__ __forceinline__ void modp_finish(const Product &pr, const Epi &E, int
     if (pr.alpha_u != 1) x = E.mulmod(pr.alpha_u, x);
     if (pr.epilogue == EPI_REDUCE && sign < 0) x = x == 0 ? 0u : E.p - x;
     v[e] = x;
-  }
-}
-
-// p < 2^16, one accumulator buffer: the thread's four 16-column groups
-// (tile columns hsel*32 + {0, 16} of both 64-column chunks), with the
-// tensor-memory reads of group g + 1 in flight while group g is recombined.
-__device__ __forceinline__ void modp2_drain_all(const Product &pr, const Epi &E, uint32_t d, int hsel, int sign,
-                                                uint32_t (&vals)[2][32]) {
-  float cur[4][16], nxt[4][16];
-#pragma unroll
-  for (int i = 0; i < 4; ++i) tmem_ld16(d + kModp2BN * i + hsel * 32, cur[i]);
-  tmem_wait_ld();
-#pragma unroll
-  for (int i = 0; i < 4; ++i) reg_fence16(cur[i]);
-#pragma unroll
-  for (int g = 0; g < 4; ++g) {
-    if (g < 3) {
-      const int col = ((g + 1) >> 1) * 64 + hsel * 32 + ((g + 1) & 1) * 16;
-#pragma unroll
-      for (int i = 0; i < 4; ++i) tmem_ld16(d + kModp2BN * i + col, nxt[i]);
-    }
-    uint32_t *v = vals[g >> 1] + (g & 1) * 16;
-    modp2_recombine(E, cur, v);
-    modp_finish(pr, E, sign, v);
-    if (g < 3) {
-      tmem_wait_ld();
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        reg_fence16(nxt[i]);
-#pragma unroll
-        for (int e = 0; e < 16; ++e) cur[i][e] = nxt[i][e];
-      }
-    }
   }
 }
 
@@ -1235,29 +1193,6 @@ __global__ void leaf_simt_kernel(const __grid_constant__ SimtArgs A, const __gri
 }  // namespace dev
 
 // ================================================================= host side
-template <int MODE, int SET>
-static cudaError_t pack_set(const PackArgs &a, cudaStream_t s) {
-  if (a.transpose) {
-    dim3 grid(a.prow_pad / 64, a.pcol_pad / 32);
-    dev::pack_cols_kernel<MODE, SET><<<grid, 256, 0, s>>>(a);
-  } else {
-    int64_t units = (int64_t)a.prow_pad * (a.pcol_pad / 8);
-    int64_t b = (units + 255) / 256;
-    int blocks = (int)(b > 152 * 16 ? 152 * 16 : b);
-    dev::pack_rows_kernel<MODE, SET><<<blocks, 256, 0, s>>>(a);
-  }
-  return cudaGetLastError();
-}
-template <int MODE>
-static cudaError_t pack_mode(const PackArgs &a, cudaStream_t s) {
-  if (a.prow_pad == 0 || a.pcol_pad == 0) return cudaSuccess;
-  const bool quads = a.nsrc == 4 && a.nout == 7;
-  if (a.set == PACK_WINOGRAD_A && quads) return pack_set<MODE, PACK_WINOGRAD_A>(a, s);
-  if (a.set == PACK_WINOGRAD_B && quads) return pack_set<MODE, PACK_WINOGRAD_B>(a, s);
-  if (a.set != PACK_GENERIC) return cudaErrorInvalidValue;
-  return pack_set<MODE, PACK_GENERIC>(a, s);
-}
-
 template <int MODE, int SA, int SB>
 static cudaError_t pair_sets(const PackArgs &a, const PackArgs &b, cudaStream_t s) {
   const int64_t units = (int64_t)a.prow_pad * (a.pcol_pad / 8);
@@ -1296,14 +1231,6 @@ cudaError_t launch_amax(const AmaxArgs &a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_pack(const PackArgs &a, int mode, cudaStream_t s) {
-  switch (mode) {
-    case MODE_MODP1: return pack_mode<MODE_MODP1>(a, s);
-    case MODE_MODP2: return pack_mode<MODE_MODP2>(a, s);
-    case MODE_FP32: return pack_mode<MODE_FP32>(a, s);
-  }
-  return cudaErrorInvalidValue;
-}
 
 template <int MODE>
 static cudaError_t gemm_mode(const GemmParams &P, int num_sms, cudaStream_t s) {

@@ -84,8 +84,7 @@ struct PackArgs {
 // (A side) or B11, B21, B22, T4, T1, T2, T3 (B side), forming the chains
 // S2 = S1 - A11, S4 = A12 - S2 and T2 = B22 - T1, T4 = T2 - B21 once.
 enum PackSet : int { PACK_GENERIC = 0, PACK_WINOGRAD_A = 1, PACK_WINOGRAD_B = 2 };
-cudaError_t launch_pack(const PackArgs &a, int mode, cudaStream_t s);
-// a (plain layout) and b (transposed) in one launch
+// a (plain layout) and b (transposed: packed row = source column) in one launch
 cudaError_t launch_pack_pair(const PackArgs &a, const PackArgs &b, int mode, cudaStream_t s);
 
 // ---------------------------------------------------------------- leaf GEMM
