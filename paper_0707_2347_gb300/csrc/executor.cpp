@@ -14,13 +14,31 @@
 // Algorithm 2, are carved from C22.
 #include "executor.h"
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <algorithm>
+#include <cstdio>
 #include <cstring>
 
 namespace swmm {
 
 namespace {
 int64_t rup(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+// NVTX range over the issue of one table level / fused level / driver (the
+// launches it enqueues; visible to profilers, free when none is attached)
+struct Range {
+  bool on;
+  Range(bool active, const char *what, int64_t m, int64_t k, int64_t n, int depth) : on(active) {
+    if (!on) return;
+    char buf[96];
+    snprintf(buf, sizeof(buf), "%s %lldx%lldx%lld d%d", what, (long long)m, (long long)k, (long long)n, depth);
+    nvtxRangePushA(buf);
+  }
+  ~Range() {
+    if (on) nvtxRangePop();
+  }
+};
 bool aligned16(const void *p, int64_t ld) { return ((uintptr_t)p % 16 == 0) && (ld % 4 == 0); }
 }  // namespace
 
@@ -392,6 +410,7 @@ bool Exec::fuses(int64_t m, int64_t k, int64_t n, int depth) const {
 
 void Exec::fused_level(Scalar alpha, bool acc, Scalar beta, const Lin &LL, const Lin &RL, View D) {
   const View &L = LL.shape(), &R = RL.shape();
+  const Range nv(!dry, "fused level", L.rows, L.cols, R.cols, 1);
   // operand coefficients over (X11, X12, X21, X22)
   static const int8_t acoef[7][4] = {
       {1, 0, 0, 0},    // A11
@@ -635,6 +654,7 @@ void Exec::peel(Kind k, Scalar alpha, bool acc, Scalar beta, View L, View R, Vie
 void Exec::table(Kind k, Scalar alpha, bool acc, Scalar beta, View L, View R, View D, int depth,
                  const Arena &ar) {
   const KindInfo &K = kind_info(k);
+  const Range nv(!dry, K.name, L.rows, L.cols, R.cols, depth);
   const int64_t hm = L.rows / 2, hk = L.cols / 2, hn = R.cols / 2;
   auto dims = [&](Shape s, int64_t &r, int64_t &c) {
     r = s == SH_B ? hk : hm;
@@ -843,6 +863,7 @@ void Exec::table(Kind k, Scalar alpha, bool acc, Scalar beta, View L, View R, Vi
 // temporaries carved from C22; then C22 recursively; classical base case.
 void Exec::ipmm(View L, View R, View D, int depth, int64_t cutoff, Kind acc_kind) {
   if (!ok()) return;
+  const Range nv(!dry, "IPMM", L.rows, L.cols, R.cols, depth);
   const int64_t n = D.rows, k = L.cols;
   if (n <= cutoff || n % 2 || n < 2 || k % (n / 2)) {
     leaf(one(), false, Scalar{}, L, R, D);
@@ -878,6 +899,7 @@ void Exec::ipmm(View L, View R, View D, int depth, int64_t cutoff, Kind acc_kind
 // C_1 is formed.  A is overwritten; B is read-only; no extra memory.
 void Exec::ip0vmm(Scalar alpha, View L, View R, View D, int depth) {
   if (!ok()) return;
+  const Range nv(!dry, "IP0vMM", L.rows, L.cols, R.cols, depth);
   const int64_t m = L.rows, k = L.cols, n = R.cols;
   const int64_t m0 = m / n, k0 = k / n;
   int d = 0;
@@ -905,6 +927,7 @@ void Exec::ip0vmm(Scalar alpha, View L, View R, View D, int depth) {
 // Table 2, 2 (n/t)^2 / 3 with Table 9.
 void Exec::tblock(Scalar alpha, Scalar beta, View L, View R, View D, int t, int depth, Kind acc_kind) {
   if (!ok()) return;
+  const Range nv(!dry, "t-blocks", L.rows, L.cols, R.cols, depth);
   const int64_t mt = L.rows / t, kt = L.cols / t, nt = R.cols / t;
   for (int i = 0; i < t; ++i)
     for (int j = 0; j < t; ++j)
