@@ -38,7 +38,7 @@ MODP, FP32 = 0, 1
 CLASSICAL, T1, T2, IP, T9, IPMM, IP0VMM, TBLOCK = 0, 1, 2, 3, 9, 10, 12, 13
 
 WORKLOADS = {
-    # configs[1]: the accumulate schedule at 8192 (default)
+    # the accumulate schedule at 8192^2, three levels (default)
     "t9_8192_p65521": dict(desc="C<-AB+C over Z/65521, 8192^2, Table 9 (Acc) depth 3, fused last level",
                            m=8192, k=8192, n=8192, mode=MODP, p=65521, sched=T9, depth=3, entry="muladd"),
     "t9_16384_p65521": dict(desc="C<-AB+C over Z/65521, 16384^2, Table 9 (Acc) depth 2, fused last level",
@@ -75,7 +75,7 @@ WORKLOADS = {
     "ip0vmm_16384x8192x4096_p251": dict(desc="C<-AB over Z/251, m=16384 k=8192 n=4096, Algorithm 1 (IP0vMM) depth 2",
                                         m=16384, k=8192, n=4096, mode=MODP, p=251, sched=IP0VMM, depth=2,
                                         entry="inplace"),
-    # configs[3]: FP32 mode error and speed per depth
+    # FP32 mode: error and speed per size and depth
     "fp32_sweep": dict(desc="C<-AB+C FP32 mode (3 fp16 split products), n in {4096, 8192, 16384}, "
                             "Table 9 depth 1-4 vs classical",
                        m=16384, k=16384, n=16384, mode=FP32, p=0, sched=T9, depth=0, entry="sweep",
