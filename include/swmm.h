@@ -36,6 +36,13 @@
  *     records SWMM_ETIMEOUT, reported by swmm_sync.
  *   - A and B must not overlap C.  A and B may overlap each other only for
  *     the read-only schedules.
+ *   - Execution order: the rows of a table are issued in order; the leaf
+ *     products of independent fused levels (those touching different
+ *     blocks, or only adding into a common one) may share one grouped
+ *     launch when their operand staging is small (at most 96 MiB per level),
+ *     and on quadrants above 32 MiB the pre-additions that only feed a fused
+ *     level are formed while its operands are packed.  Results are those of
+ *     the rows in order; over Z/pZ they are bit-identical.
  */
 #ifndef SWMM_H
 #define SWMM_H
@@ -99,7 +106,8 @@ extern "C" {
                                   launch waits only for earlier launches
                                   whose blocks it reads or writes, so
                                   independent rows of a schedule may overlap
-                                  (operand staging is then double-buffered) */
+                                  (operand staging then uses at least two
+                                  areas in turn) */
 #define SWMM_FLAG_SERIAL 16u   /* with SWMM_FLAG_GRAPH: capture every launch
                                   in row order on one stream */
 
