@@ -186,6 +186,22 @@ int swmm_muladd(swmm_t h, int64_t m, int64_t k, int64_t n, const void *alpha,
                 const void *A, int64_t lda, const void *B, int64_t ldb,
                 const void *beta, void *C, int64_t ldc, const swmm_opts *opts);
 
+/* C <- alpha A B + beta C with A, B and C in HOST memory (the paper has no
+ * counterpart: the operands of a product that does not start on the GPU).
+ * The handle copies A, B and C into device buffers it keeps (grown on demand,
+ * freed by swmm_destroy), runs the same schedules as swmm_muladd, and copies
+ * C back.  The copies go block by block (the 2 x 2 blocks of A, B and C) in
+ * the order the top level's table first reads them, and C's blocks return as
+ * soon as each is final; with SWMM_FLAG_GRAPH the product starts before the
+ * last copy ends.  Page-locked host memory lets the copies overlap the work;
+ * pageable memory works but copies synchronously.  A, B, C: host pointers,
+ * row-major, leading dimensions in elements.  Asynchronous on the handle's
+ * stream: C holds the result after swmm_sync.  Errors as swmm_muladd, plus
+ * SWMM_ENOMEM when the device copies cannot be allocated. */
+int swmm_muladd_host(swmm_t h, int64_t m, int64_t k, int64_t n, const void *alpha,
+                     const void *A, int64_t lda, const void *B, int64_t ldb,
+                     const void *beta, void *C, int64_t ldc, const swmm_opts *opts);
+
 /* The same operation as swmm_muladd for callers that cannot allocate device
  * memory (the paper has no counterpart: it is a deployment variant).  Code
  * running where cudaMalloc/cudaMallocAsync are unavailable or forbidden --

@@ -137,6 +137,11 @@ struct swmm_ctx {
   // dataflow capture: side streams and an event per launch of a captured call
   cudaStream_t flow_streams[kFlowStreams - 1] = {};
   std::vector<cudaEvent_t> flow_events;
+  // swmm_muladd_host: device copies of the operands (grown on demand) and
+  // two host bytes whose addresses order the copies of each direction
+  char *io_buf = nullptr;
+  size_t io_bytes = 0;
+  char io_token[2] = {0, 0};
   // autotuner decisions: (m, k, n, mode, p) -> (sched, depth, est_us, elems)
   std::vector<std::pair<std::array<int64_t, 5>, std::tuple<int32_t, int32_t, double, int64_t>>> tuned;
   ~swmm_ctx() {
@@ -144,6 +149,7 @@ struct swmm_ctx {
     for (cudaStream_t s : flow_streams)
       if (s) cudaStreamDestroy(s);
     for (cudaEvent_t e : flow_events) cudaEventDestroy(e);
+    if (io_buf) cudaFree(io_buf);
     if (cap) cudaStreamDestroy(cap);
     if (ev_in) cudaEventDestroy(ev_in);
     if (ev_out) cudaEventDestroy(ev_out);
@@ -257,7 +263,44 @@ struct Plan {
   int tblock = 2;
   int64_t paper = 0;
   std::vector<LeafJob> jobs;  // a grouped launch of classical problems (batched calls)
+  // host operands (swmm_muladd_host): L, R, D are the handle's device copies
+  bool host_io = false;
+  const char *hA = nullptr, *hB = nullptr;
+  char *hC = nullptr;
+  int64_t hlda = 0, hldb = 0, hldc = 0;
 };
+
+// The 2 x 2 blocks of A, B and C in the order the top level's table first
+// reads them (A, B, C in order for the other drivers), so that copies to
+// the device arrive in the order the work needs them.
+std::vector<Loc> first_use(int sched) {
+  std::vector<Loc> order;
+  auto add = [&](Loc l) {
+    if (l <= C22 && std::find(order.begin(), order.end(), l) == order.end()) order.push_back(l);
+  };
+  const Kind k = kind_of(sched);
+  if (k != NKIND) {
+    for (const Row &row : *kind_info(k).table) {
+      if (row.op == OP_MUL) {
+        add(row.s1);
+        add(row.s2);
+        if (row.acc) add(row.dst);
+      } else {
+        add(row.s1);
+        if (row.op == OP_ADD) add(row.s2);
+      }
+    }
+  }
+  for (int l = A11; l <= C22; ++l) add((Loc)l);
+  return order;
+}
+
+// 2 x 2 split of a block that also covers odd sizes
+View block_of(const View &v, int i, int j) {
+  const int64_t r0 = i ? v.rows / 2 : 0, c0 = j ? v.cols / 2 : 0;
+  const int64_t nr = i ? v.rows - v.rows / 2 : v.rows / 2, nc = j ? v.cols - v.cols / 2 : v.cols / 2;
+  return v.sub(r0, c0, nr, nc);
+}
 
 void execute(const Plan &P, Exec &e) {
   if (!P.ne) return;
@@ -427,11 +470,39 @@ int enqueue(swmm_t h, const Plan &P, cudaStream_t stream, TimingHook *timing, co
       return fail(h, SWMM_ENOMEM, "staging allocation failed");
     }
   }
+  // host operands: the blocks go to the device in the order the table reads
+  // them, and C's blocks come back as soon as they are final
+  const Rect tok_in = rect_bytes(&h->io_token[0], 1), tok_out = rect_bytes(&h->io_token[1], 1);
+  auto host_in = [&]() {
+    if (!P.host_io) return;
+    for (Loc l : first_use(P.sched)) {
+      const int q = (l - A11) % 4, i = q / 2, j = q % 2;
+      const View &dv = l <= A22 ? P.L : (l <= B22 ? P.R : P.D);
+      const char *hp = l <= A22 ? P.hA : (l <= B22 ? P.hB : P.hC);
+      const int64_t hld = l <= A22 ? P.hlda : (l <= B22 ? P.hldb : P.hldc);
+      const View b = block_of(dv, i, j);
+      const int64_t r0 = i ? dv.rows / 2 : 0, c0 = j ? dv.cols / 2 : 0;
+      r.copy_in(b, hp + 4 * (r0 * hld + c0), hld, tok_in);
+    }
+  };
+  auto host_out = [&]() {
+    if (!P.host_io) return;
+    for (int q = 0; q < 4; ++q) {
+      const int i = q / 2, j = q % 2;
+      const View b = block_of(P.D, i, j);
+      if (r.lazy) r.canon(b);
+      const int64_t r0 = i ? P.D.rows / 2 : 0, c0 = j ? P.D.cols / 2 : 0;
+      r.copy_out(P.hC + 4 * (r0 * P.hldc + c0), P.hldc, b, tok_out);
+    }
+    r.lazy = false;
+  };
   if (use_flow) {
     Flow flow(stream, h->flow_streams, h->flow_events);
     r.flow = &flow;
+    host_in();
     execute(P, r);
     r.flush();
+    host_out();
     flow.join();
     r.flow = nullptr;
     if (flow.error() != cudaSuccess && r.cuda_err == cudaSuccess) {
@@ -439,8 +510,10 @@ int enqueue(swmm_t h, const Plan &P, cudaStream_t stream, TimingHook *timing, co
       r.fail = std::string("dataflow ordering: ") + cudaGetErrorString(flow.error());
     }
   } else {
+    host_in();
     execute(P, r);
     r.flush();
+    host_out();
   }
   if (r.lazy && r.ok()) {
     // fused levels leave unreduced representatives: one canonicalising pass
@@ -520,7 +593,7 @@ int run_plans(swmm_t h, const std::vector<Plan> &plans, uint32_t flags, const Sc
       size_t need = 2;
       for (const Plan &P : plans)
         need = std::max<size_t>(need, (size_t)(8 * P.x.leaf_launches + 2 * P.x.leaf_products +
-                                               2 * P.x.ew_launches + 16));
+                                               2 * P.x.ew_launches + 48));
       for (cudaStream_t &s : h->flow_streams)
         if (!s && cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
           cudaGetLastError();
@@ -738,6 +811,64 @@ int swmm_muladd(swmm_t h, int64_t m, int64_t k, int64_t n, const void *alpha, co
   if (!alpha || !beta) return fail(h, SWMM_EINVAL, "alpha and beta are required");
   Req q{1, m, k, n, A, B, C, lda, ldb, ldc, alpha, beta};
   return run(h, q, opts);
+}
+
+int swmm_muladd_host(swmm_t h, int64_t m, int64_t k, int64_t n, const void *alpha, const void *A, int64_t lda,
+                     const void *B, int64_t ldb, const void *beta, void *C, int64_t ldc, const swmm_opts *opts) {
+  if (!h) return SWMM_EINVAL;
+  h->last_error.clear();
+  if (!alpha || !beta) return fail(h, SWMM_EINVAL, "alpha and beta are required");
+  if (!opts) return fail(h, SWMM_EINVAL, "opts is NULL");
+  if (m < 0 || k < 0 || n < 0) return fail(h, SWMM_EINVAL, "negative dimension");
+  if (m > (1 << 30) || k > (1 << 30) || n > (1 << 30)) return fail(h, SWMM_EINVAL, "dimension too large");
+  if (m == 0 || n == 0) return SWMM_OK;
+  if (!C || (k > 0 && (!A || !B))) return fail(h, SWMM_EINVAL, "NULL pointer");
+  if (lda < std::max<int64_t>(k, 1) || ldb < std::max<int64_t>(n, 1) || ldc < std::max<int64_t>(n, 1))
+    return fail(h, SWMM_EINVAL, "leading dimension smaller than the number of columns");
+  // device copies: leading dimensions rounded to 16 bytes, blocks 256-byte aligned
+  const int64_t dla = (k + 3) / 4 * 4, dlb = (n + 3) / 4 * 4, dlc = dlb;
+  auto r256 = [](int64_t b) { return (b + 255) / 256 * 256; };
+  const int64_t bA = r256(4 * m * dla), bB = r256(4 * k * dlb), bC = r256(4 * m * dlc);
+  const size_t need = (size_t)(bA + bB + bC);
+  if (need > h->io_bytes) {
+    // the cached graphs refer to the old copies: drop them
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e == cudaSuccess && h->cap) e = cudaStreamSynchronize(h->cap);
+    if (e != cudaSuccess) return fail(h, SWMM_ECUDA, cudaGetErrorString(e));
+    h->graphs.clear();
+    if (h->io_buf) cudaFree(h->io_buf);
+    h->io_buf = nullptr;
+    h->io_bytes = 0;
+    if (cudaMalloc((void **)&h->io_buf, need) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(h, SWMM_ENOMEM, "device copies of the operands");
+    }
+    h->io_bytes = need;
+  }
+  char *dA = h->io_buf, *dB = h->io_buf + bA, *dC = h->io_buf + bA + bB;
+  Req q{1, m, k, n, dA, dB, dC, dla, dlb, dlc, alpha, beta};
+  std::string key;
+  if (opts->flags & SWMM_FLAG_GRAPH) {
+    key = call_key(q, opts);
+    key.append("host");
+    const void *hp[4] = {A, B, C, h->io_buf};
+    key_append(key, hp, sizeof(hp));
+    const int64_t hl[3] = {lda, ldb, ldc};
+    key_append(key, hl, sizeof(hl));
+    if (GraphEntry *g = find_graph(h, key)) return launch_graph(h, g);
+  }
+  std::vector<Plan> plans(1);
+  int rc = make_plan(h, q, opts, true, plans[0]);
+  if (rc != SWMM_OK) return rc;
+  Plan &P = plans[0];
+  P.host_io = true;
+  P.hA = static_cast<const char *>(A);
+  P.hB = static_cast<const char *>(B);
+  P.hC = static_cast<char *>(C);
+  P.hlda = lda;
+  P.hldb = ldb;
+  P.hldc = ldc;
+  return run_plans(h, plans, opts->flags, nullptr, key);
 }
 
 int swmm_mul_inplace(swmm_t h, int64_t m, int64_t k, int64_t n, void *A, int64_t lda, void *B, int64_t ldb, void *C,

@@ -936,4 +936,28 @@ void Exec::tblock(Scalar alpha, Scalar beta, View L, View R, View D, int t, int 
              D.sub(i * mt, j * nt, mt, nt), depth, Arena{});
 }
 
+void Exec::copy_in(View dv, const char *host, int64_t hld, const Rect &token) {
+  if (dry || dv.rows == 0 || dv.cols == 0) return;
+  cudaStream_t st = op_begin({token}, {rect_of(dv), token});
+  check(cudaMemcpy2DAsync(dv.ptr, 4 * dv.ld, host, 4 * hld, 4 * dv.cols, dv.rows, cudaMemcpyHostToDevice, st),
+        "copy to device");
+  op_end();
+}
+
+void Exec::copy_out(char *host, int64_t hld, View dv, const Rect &token) {
+  if (dry || dv.rows == 0 || dv.cols == 0) return;
+  cudaStream_t st = op_begin({rect_of(dv), token}, {token});
+  check(cudaMemcpy2DAsync(host, 4 * hld, dv.ptr, 4 * dv.ld, 4 * dv.cols, dv.rows, cudaMemcpyDeviceToHost, st),
+        "copy to host");
+  op_end();
+}
+
+void Exec::canon(View v) {
+  ++ew_launches;
+  if (dry || v.rows == 0 || v.cols == 0) return;
+  cudaStream_t st = op_begin({}, {rect_of(v)});
+  check(launch_canon_modp(v, p, st), "canonical pass");
+  op_end();
+}
+
 }  // namespace swmm

@@ -118,6 +118,12 @@ struct Exec {
   void ip0vmm(Scalar alpha, View L, View R, View D, int depth);
   // Section 7.2: D <- alpha L R + beta D by t x t blocks of D
   void tblock(Scalar alpha, Scalar beta, View L, View R, View D, int t, int depth, Kind acc_kind);
+  // Host <-> device copies of a block and the canonical pass of a block, as
+  // ordered operations (under a Flow they wait only for the launches that
+  // touch the block; `token` chains copies of one direction in issue order)
+  void copy_in(View dv, const char *host, int64_t hld, const Rect &token);
+  void copy_out(char *host, int64_t hld, View dv, const Rect &token);
+  void canon(View v);
 
  private:
   void fused_level(Scalar alpha, bool acc, Scalar beta, const Lin &L, const Lin &R, View D);

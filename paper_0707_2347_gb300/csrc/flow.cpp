@@ -77,10 +77,12 @@ cudaStream_t Flow::begin(const Rect *rd, int nrd, const Rect *wr, int nwr) {
   for (int i = j - 1; i >= 0; --i)
     if (conflict(ops_[i], rd, nrd, wr, nwr)) deps.push_back(i);
   int s;
-  if (!deps.empty()) {
-    s = ops_[deps[0]].s;  // follow the latest conflicting launch
+  const int d0 = deps.empty() ? -1 : deps[0];
+  if (d0 >= 0 && vc_[ops_[d0].s][ops_[d0].s] == d0 + 1) {
+    s = ops_[d0].s;  // the latest conflicting launch ends its stream: follow it
   } else {
-    // no predecessor: the stream whose tail is oldest
+    // no predecessor, or later unrelated launches sit behind it on its
+    // stream: the stream whose tail is oldest (an event orders it after d0)
     s = 0;
     int best = vc_[0][0];
     for (int t = 1; t < kFlowStreams; ++t)

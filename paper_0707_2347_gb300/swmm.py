@@ -62,7 +62,7 @@ class Problem(ctypes.Structure):
 EXPORTS = ["swmm_create", "swmm_destroy", "swmm_set_stream", "swmm_mul", "swmm_muladd", "swmm_muladd_noalloc",
            "swmm_mul_inplace",
            "swmm_muladd_batched", "swmm_autotune", "swmm_workspace_elems", "swmm_leaf_timing", "swmm_get_stats",
-           "swmm_sync", "swmm_strerror", "swmm_last_error", "swmm_matvec", "swmm_residual"]
+           "swmm_sync", "swmm_strerror", "swmm_last_error", "swmm_matvec", "swmm_residual", "swmm_muladd_host"]
 
 _lib = None
 
@@ -97,6 +97,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
                                      ctypes.POINTER(ctypes.c_double)]
     lib.swmm_sync.argtypes = [vp]
     lib.swmm_matvec.argtypes = [vp, i64, i64, cvp, i64, cvp, vp, ctypes.POINTER(_Opts)]
+    lib.swmm_muladd_host.argtypes = [vp, i64, i64, i64, cvp, cvp, i64, cvp, i64, cvp, vp, i64,
+                                     ctypes.POINTER(_Opts)]
     lib.swmm_residual.argtypes = [vp, i64, i64, i64, cvp, cvp, i64, cvp, i64, cvp, cvp, cvp, i64, cvp, vp,
                                   ctypes.POINTER(_Opts)]
     lib.swmm_strerror.argtypes = [ctypes.c_int]
@@ -232,6 +234,22 @@ class Handle:
         n = B.shape[1]
         self._check(self.lib.swmm_muladd_noalloc(self.h, m, k, n, _scalar(opts.mode, alpha), a, lda, b, ldb,
                                                  _scalar(opts.mode, beta), c, ldc, ctypes.byref(opts.c())))
+        return C
+
+    def muladd_host(self, alpha, A, B, beta, C, opts: Opts):
+        """swmm_muladd_host: C <- alpha A B + beta C with A, B, C host (CPU)
+        tensors, page-locked for overlap; C holds the result after sync()."""
+        self._stream()
+        for t, what in ((A, "A"), (B, "B"), (C, "C")):
+            if t.is_cuda:
+                raise ValueError(f"{what} must be a host tensor")
+        a, lda = _mat(A, "A")
+        b, ldb = _mat(B, "B")
+        c, ldc = _mat(C, "C")
+        m, k = A.shape
+        n = B.shape[1]
+        self._check(self.lib.swmm_muladd_host(self.h, m, k, n, _scalar(opts.mode, alpha), a, lda, b, ldb,
+                                              _scalar(opts.mode, beta), c, ldc, ctypes.byref(opts.c())))
         return C
 
     def matvec(self, M, x, y, opts: Opts):
