@@ -453,9 +453,11 @@ def main():
     # Per-launch GEMM durations: the same K steps again with an event pair
     # around every leaf GEMM launch (recorded on the launching stream, inside
     # the graph).  The event nodes cost ~5 us each, so the value above is
-    # timed without them.
-    topts = S.Opts(mode=mode, p=p or 65521, sched=w["sched"], depth=w["depth"], flags=S.FLAG_TIMING | gflag,
-                   **extra)
+    # timed without them; and this pass captures in row order, so a GEMM's
+    # duration is its own, not shared with additions that overlap it in the
+    # dataflow capture of the value pass.
+    tflag = S.FLAG_TIMING | (gflag | S.FLAG_SERIAL if gflag else 0)
+    topts = S.Opts(mode=mode, p=p or 65521, sched=w["sched"], depth=w["depth"], flags=tflag, **extra)
     tms = timed(topts, args.steps, args.warmup)
     gemm_ms, gemm_launches, tensor_flops = h.leaf_timing(reset=True)
     st = h.stats()
@@ -483,7 +485,8 @@ def main():
                      "kernel": "gemm_kernel (leaf products, fp16 limb MMAs counted)",
                      "peak_kind": f"{peak_kind} bf16 sustained", "launches_per_step": st["leaf_launches"],
                      "gemm_ms_per_step": round(gemm_ms / max(gemm_launches, 1) * st["leaf_launches"], 4),
-                     "timing_pass_ms_per_step": round(tms, 4)},
+                     "timing_pass_ms_per_step": round(tms, 4),
+                     "timing_pass": "event pair per GEMM launch, graph captured in row order"},
     }
     line["clocks"] = clk.summary()
 
