@@ -86,13 +86,13 @@ static bool any_overlap(const std::vector<Rect> &a, const std::vector<Rect> &b) 
   return false;
 }
 
-cudaStream_t Exec::op_begin(const std::vector<Rect> &rd, const std::vector<Rect> &wr) {
+cudaStream_t Exec::op_begin(const std::vector<Rect> &rd, const std::vector<Rect> &wr, bool dma) {
   // a deferred GEMM launch goes out before anything that touches its memory
   if (pend.n > 0 && !flushing &&
       (any_overlap(rd, pend.wr) || any_overlap(wr, pend.rd) || any_overlap(wr, pend.wr)))
     flush();
   if (!flow) return stream;
-  return flow->begin(rd.data(), (int)rd.size(), wr.data(), (int)wr.size());
+  return flow->begin(rd.data(), (int)rd.size(), wr.data(), (int)wr.size(), dma);
 }
 
 void Exec::op_end() {
@@ -938,7 +938,7 @@ void Exec::tblock(Scalar alpha, Scalar beta, View L, View R, View D, int t, int 
 
 void Exec::copy_in(View dv, const char *host, int64_t hld, const Rect &token) {
   if (dry || dv.rows == 0 || dv.cols == 0) return;
-  cudaStream_t st = op_begin({token}, {rect_of(dv), token});
+  cudaStream_t st = op_begin({token}, {rect_of(dv), token}, true);
   check(cudaMemcpy2DAsync(dv.ptr, 4 * dv.ld, host, 4 * hld, 4 * dv.cols, dv.rows, cudaMemcpyHostToDevice, st),
         "copy to device");
   op_end();
@@ -946,7 +946,7 @@ void Exec::copy_in(View dv, const char *host, int64_t hld, const Rect &token) {
 
 void Exec::copy_out(char *host, int64_t hld, View dv, const Rect &token) {
   if (dry || dv.rows == 0 || dv.cols == 0) return;
-  cudaStream_t st = op_begin({rect_of(dv), token}, {token});
+  cudaStream_t st = op_begin({rect_of(dv), token}, {token}, true);
   check(cudaMemcpy2DAsync(host, 4 * hld, dv.ptr, 4 * dv.ld, 4 * dv.cols, dv.rows, cudaMemcpyDeviceToHost, st),
         "copy to host");
   op_end();

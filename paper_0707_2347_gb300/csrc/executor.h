@@ -133,7 +133,7 @@ struct Exec {
   void table(Kind k, Scalar alpha, bool acc, Scalar beta, View L, View R, View D, int depth, const Arena &ar);
   void add(View d, View s1, View s2, Scalar c1, Scalar c2);
   // stream for a launch reading rd and writing wr; op_end() after issuing it
-  cudaStream_t op_begin(const std::vector<Rect> &rd, const std::vector<Rect> &wr);
+  cudaStream_t op_begin(const std::vector<Rect> &rd, const std::vector<Rect> &wr, bool dma = false);
   void op_end();
   char *next_stage();
   void queue_gemm(const GemmParams *P, const std::vector<Rect> &rd, const std::vector<Rect> &wr, bool additive,

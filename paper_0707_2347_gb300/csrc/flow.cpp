@@ -67,7 +67,7 @@ bool Flow::conflict(const Op &o, const Rect *rd, int nrd, const Rect *wr, int nw
   return false;
 }
 
-cudaStream_t Flow::begin(const Rect *rd, int nrd, const Rect *wr, int nwr) {
+cudaStream_t Flow::begin(const Rect *rd, int nrd, const Rect *wr, int nwr, bool dma) {
   const int j = (int)ops_.size();
   if (err_ != cudaSuccess || j + 1 >= (int)ev_.size()) {
     if (err_ == cudaSuccess) err_ = cudaErrorInvalidValue;  // event pool too small
@@ -78,14 +78,17 @@ cudaStream_t Flow::begin(const Rect *rd, int nrd, const Rect *wr, int nwr) {
     if (conflict(ops_[i], rd, nrd, wr, nwr)) deps.push_back(i);
   int s;
   const int d0 = deps.empty() ? -1 : deps[0];
-  if (d0 >= 0 && vc_[ops_[d0].s][ops_[d0].s] == d0 + 1) {
+  if (dma) {
+    s = 0;
+  } else if (d0 >= 0 && vc_[ops_[d0].s][ops_[d0].s] == d0 + 1) {
     s = ops_[d0].s;  // the latest conflicting launch ends its stream: follow it
   } else {
     // no predecessor, or later unrelated launches sit behind it on its
-    // stream: the stream whose tail is oldest (an event orders it after d0)
-    s = 0;
-    int best = vc_[0][0];
-    for (int t = 1; t < kFlowStreams; ++t)
+    // stream: the kernel stream whose tail is oldest (an event orders it
+    // after d0)
+    s = 1;
+    int best = vc_[1][1];
+    for (int t = 2; t < kFlowStreams; ++t)
       if (vc_[t][t] < best) {
         best = vc_[t][t];
         s = t;

@@ -45,8 +45,11 @@ class Flow {
   // holds so far); extra: kFlowStreams - 1 streams owned by the caller;
   // events: a pool of at least (launches + 1) events created beforehand.
   Flow(cudaStream_t origin, const cudaStream_t *extra, const std::vector<cudaEvent_t> &events);
-  // Stream for the next launch, after the waits its conflicts need.
-  cudaStream_t begin(const Rect *rd, int nrd, const Rect *wr, int nwr);
+  // Stream for the next launch, after the waits its conflicts need.  Copies
+  // between host and device (dma) go to the origin stream, which kernels
+  // use only to follow a predecessor that ends it, so that no kernel waits
+  // behind copies it does not need.
+  cudaStream_t begin(const Rect *rd, int nrd, const Rect *wr, int nwr, bool dma = false);
   // The launch announced by begin() has been issued.
   void end();
   // The origin stream waits for every launch issued so far.
