@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libswmm.so")
 SOURCES = ["api.cpp", "executor.cpp", "schedules.cpp", "ew_kernels.cu", "leaf_kernel.cu", "noalloc.cu",
-           "probe_kernels.cu", "flow.cpp"]
+           "probe_kernels.cu", "flow.cpp", "pebble.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -39,7 +39,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     objs = []
     srcs = [os.path.join(CSRC, s) for s in SOURCES]
     headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".h")]
-    headers.append(os.path.join(ROOT, "include", "swmm.h"))
+    headers += [os.path.join(ROOT, "include", f) for f in os.listdir(os.path.join(ROOT, "include")) if f.endswith(".h")]
     newest_hdr = max(os.path.getmtime(h) for h in headers)
     jobs = []
     for s in srcs:

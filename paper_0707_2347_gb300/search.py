@@ -1,0 +1,141 @@
+"""Python binding of include/swmm_search.h: the pebble-game search for the
+memory schedules of one Winograd level (Section 4), and the replay of a
+given schedule under the same rules.  Host code of libswmm.so; no GPU.
+
+Locations are named as in the tables ("A11" ... "C22", "X", "Y", "Z");
+recursive call kinds are the schedule codes of swmm.py (T1_DHSS ...
+T9_ACC, T4M_OVL) or SELF, the schedule being searched for.
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass, field
+
+from . import swmm
+
+LOCS = ("A11", "A12", "A21", "A22", "B11", "B12", "B21", "B22",
+        "C11", "C12", "C21", "C22", "X", "Y", "Z")
+ADD, MUL, COPY = 0, 1, 2
+COEFS = (1, -1, "b", "-b")  # SWMM_COEF_ONE, NEG, BETA, NBETA
+SELF = 31
+MAX_ROWS = 64
+
+
+class _Spec(ctypes.Structure):
+    _fields_ = [("accumulate", ctypes.c_int32), ("preserve", ctypes.c_uint32), ("temps", ctypes.c_int32),
+                ("kinds", ctypes.c_uint32), ("max_written", ctypes.c_int32), ("max_copies", ctypes.c_int32),
+                ("recompute", ctypes.c_int32), ("max_rows", ctypes.c_int32), ("max_states", ctypes.c_int64)]
+
+
+class _Row(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_int32) for f in ("op", "dst", "s1", "s2", "coef", "accumulate", "sign", "kind", "node")]
+
+
+class _Result(ctypes.Structure):
+    _fields_ = [("found", ctypes.c_int32), ("exhausted", ctypes.c_int32), ("nrows", ctypes.c_int32),
+                ("written", ctypes.c_int32), ("temps_used", ctypes.c_int32), ("states", ctypes.c_int64)]
+
+
+@dataclass
+class Row:
+    op: int                 # ADD, MUL or COPY
+    dst: str                # location written
+    s1: str                 # ADD: first operand; MUL: left operand; COPY: source
+    s2: str | None = None   # ADD: second operand; MUL: right operand
+    coef: object = 1        # ADD: coefficient of s2; MUL accumulate: of dst's value (1, -1, "b", "-b")
+    accumulate: bool = False
+    sign: int = 1           # MUL: sign applied to alpha
+    kind: int = 0           # MUL: schedule code or SELF
+    value: str = ""         # name of the value written (filled by the library)
+
+
+@dataclass
+class Outcome:
+    found: bool
+    exhausted: bool
+    states: int
+    written: int            # blocks of A and B written or overwritten
+    temps_used: int
+    rows: list = field(default_factory=list)
+    first_bad_row: int = -1  # schedule_check: index of the first illegal row (-1: none)
+
+
+def _lib():
+    lib = swmm.load()
+    if not getattr(lib, "_search_typed", False):
+        lib.swmm_schedule_search.argtypes = [ctypes.POINTER(_Spec), ctypes.POINTER(_Row), ctypes.c_int32,
+                                             ctypes.POINTER(_Result)]
+        lib.swmm_schedule_check.argtypes = [ctypes.POINTER(_Spec), ctypes.POINTER(_Row), ctypes.c_int32,
+                                            ctypes.POINTER(_Result)]
+        lib.swmm_search_node_name.argtypes = [ctypes.c_int32, ctypes.c_int32]
+        lib.swmm_search_node_name.restype = ctypes.c_char_p
+        lib.swmm_search_node_count.argtypes = [ctypes.c_int32]
+        lib._search_typed = True
+    return lib
+
+
+def _spec(accumulate, preserve, temps, kinds, max_written, max_copies, recompute, max_rows, max_states):
+    pm = 0
+    for b in preserve:
+        i = LOCS.index(b)
+        if i >= 8:
+            raise ValueError(f"only blocks of A and B are preserved, not {b}")
+        pm |= 1 << i
+    km = 0
+    for k in kinds:
+        km |= 1 << int(k)
+    return _Spec(int(bool(accumulate)), pm, temps, km, max_written, max_copies, int(bool(recompute)), max_rows,
+                 max_states)
+
+
+def node_names(accumulate: bool) -> list:
+    lib = _lib()
+    a = int(bool(accumulate))
+    return [lib.swmm_search_node_name(a, i).decode() for i in range(lib.swmm_search_node_count(a))]
+
+
+def _rows_out(crows, n, accumulate):
+    names = node_names(accumulate)
+    out = []
+    for r in crows[:n]:
+        out.append(Row(op=r.op, dst=LOCS[r.dst], s1=LOCS[r.s1], s2=LOCS[r.s2] if r.op != COPY else None,
+                       coef=COEFS[r.coef], accumulate=bool(r.accumulate), sign=r.sign, kind=r.kind,
+                       value=names[r.node] if 0 <= r.node < len(names) else ""))
+    return out
+
+
+def schedule_search(*, accumulate=False, preserve=(), temps=0, kinds=(), max_written=-1, max_copies=0,
+                    recompute=False, max_rows=40, max_states=0) -> Outcome:
+    """Search for one level's schedule: C <- alpha AB (+ beta C when
+    `accumulate`), keeping the blocks named in `preserve`, with `temps`
+    temporaries, recursive products of the given `kinds`."""
+    lib = _lib()
+    spec = _spec(accumulate, preserve, temps, kinds, max_written, max_copies, recompute, max_rows, max_states)
+    rows = (_Row * MAX_ROWS)()
+    res = _Result()
+    rc = lib.swmm_schedule_search(ctypes.byref(spec), rows, MAX_ROWS, ctypes.byref(res))
+    if rc != swmm.OK:
+        raise swmm.SwmmError(rc, "schedule search failed")
+    return Outcome(bool(res.found), bool(res.exhausted), res.states, res.written, res.temps_used,
+                   _rows_out(rows, res.nrows, accumulate) if res.found else [])
+
+
+def schedule_check(rows, *, accumulate=False, preserve=(), temps=0, kinds=(), max_copies=0,
+                   recompute=False) -> Outcome:
+    """Replay `rows` (a list of Row) under the same rules; found is True when
+    every row is a legal move and the results end in place."""
+    lib = _lib()
+    spec = _spec(accumulate, preserve, temps, kinds, -1, max_copies, recompute, MAX_ROWS, 0)
+    n = len(rows)
+    crows = (_Row * max(n, 1))()
+    for i, r in enumerate(rows):
+        crows[i] = _Row(r.op, LOCS.index(r.dst), LOCS.index(r.s1), LOCS.index(r.s2) if r.s2 else -1,
+                        COEFS.index(r.coef), int(r.accumulate), r.sign, r.kind, -1)
+    res = _Result()
+    rc = lib.swmm_schedule_check(ctypes.byref(spec), crows, n, ctypes.byref(res))
+    if rc != swmm.OK:
+        raise swmm.SwmmError(rc, "schedule check failed")
+    legal = res.nrows
+    out = _rows_out(crows, legal, accumulate)
+    return Outcome(bool(res.found), False, 0, res.written, res.temps_used, out,
+                   -1 if legal == n else legal)

@@ -62,7 +62,9 @@ class Problem(ctypes.Structure):
 EXPORTS = ["swmm_create", "swmm_destroy", "swmm_set_stream", "swmm_mul", "swmm_muladd", "swmm_muladd_noalloc",
            "swmm_mul_inplace",
            "swmm_muladd_batched", "swmm_autotune", "swmm_workspace_elems", "swmm_leaf_timing", "swmm_get_stats",
-           "swmm_sync", "swmm_strerror", "swmm_last_error", "swmm_matvec", "swmm_residual", "swmm_muladd_host"]
+           "swmm_sync", "swmm_strerror", "swmm_last_error", "swmm_matvec", "swmm_residual", "swmm_muladd_host",
+           # include/swmm_search.h (host only, see search.py)
+           "swmm_schedule_search", "swmm_schedule_check", "swmm_search_node_name", "swmm_search_node_count"]
 
 _lib = None
 

@@ -22,7 +22,8 @@ def S():
 
 
 def declared_symbols():
-    text = open(os.path.join(ROOT, "include", "swmm.h")).read()
+    inc = os.path.join(ROOT, "include")
+    text = "".join(open(os.path.join(inc, f)).read() for f in sorted(os.listdir(inc)) if f.endswith(".h"))
     return sorted(set(re.findall(r"\b(swmm_[a-z_]+)\s*\(", text)))
 
 

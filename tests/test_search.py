@@ -1,0 +1,272 @@
+"""Pebble-game search for one level's memory schedule (Section 4), host code
+of the library (include/swmm_search.h).
+
+Pins:
+  * every schedule the search returns is run by the oracle's interpreter of
+    the tables (which checks liveness, clobbering, aliasing and restoration
+    on real matrices) as a new kind that recurses into itself, at depths 1 to
+    3, and must equal the plain product;
+  * every table of the paper (1-9 and the Section 5.1 variant of Table 4),
+    transcribed by the oracle, is a legal play of the game under its own
+    contract and memory, and mutated tables are rejected at the right row;
+  * the two results of the search that Section 5.1 states: no schedule
+    computes C <- AB overwriting only one of A and B without a temporary,
+    and none overwrites fewer than four input blocks; and the memory of
+    Tables 1, 4, 5, 6 and 7 is the least the game allows.
+"""
+import numpy as np
+import pytest
+
+import __graft_entry__ as g
+from oracle import classical, ring, schedules as OS
+
+
+@pytest.fixture(scope="module")
+def Z():
+    g.build()
+    from paper_0707_2347_gb300 import search, swmm
+    return search, swmm
+
+
+A_ALL = ("A11", "A12", "A21", "A22")
+B_ALL = ("B11", "B12", "B21", "B22")
+ORACLE_KIND = {1: "T1", 2: "T2", 3: "IP", 4: "OvL", 5: "OvR", 6: "AcLR", 7: "AccR", 8: "AcR", 9: "Acc",
+               11: "OvLM", 31: "Found"}
+
+
+def to_oracle(Z, rows):
+    """Rows of a found schedule -> the oracle's row format (value names made
+    unique per write; results written in place keep their names)."""
+    search, _ = Z
+    holds = {l: l for l in search.LOCS[:12]}
+    table = []
+    for i, r in enumerate(rows):
+        final = r.value in ("U1", "U5", "U6", "U7") and OS.FINAL.get(r.dst) == r.value
+        name = r.value if final else f"{r.value}@{i}"
+        if r.op == search.ADD:
+            table.append(OS.ADD(r.dst, name, [(1, holds[r.s1]), (r.coef, holds[r.s2])]))
+        elif r.op == search.COPY:
+            table.append(OS.COPY(r.dst, name, holds[r.s1]))
+        else:
+            acc = (r.coef, holds[r.dst]) if r.accumulate else None
+            table.append(OS.MUL(r.dst, name, ORACLE_KIND[r.kind], "a" if r.sign > 0 else "-a",
+                                holds[r.s1], holds[r.s2], acc))
+        holds[r.dst] = name
+    return table
+
+
+def run_found(Z, monkeypatch, rows, accumulate, preserve):
+    table = to_oracle(Z, rows)
+    blocks = {b: ("L" if b[0] == "A" else "R") + b[1:] for b in A_ALL + B_ALL}
+    keep = frozenset(blocks[b] for b in preserve)
+    kind = OS.Kind(table, accumulate, frozenset(blocks.values()) - keep, keep, True)
+    monkeypatch.setitem(OS.KINDS, "Found", kind)
+    for R, n, depth in [(ring.ModP(65521), 8, 1), (ring.ModP(251), 8, 2), (ring.ModP(65521), 16, 3),
+                        (ring.Real(), 16, 2)]:
+        rng = np.random.default_rng(n + depth)
+        if isinstance(R, ring.ModP):
+            A, B, C = (rng.integers(0, R.p, (n, n)) for _ in range(3))
+        else:
+            A, B, C = (rng.standard_normal((n, n)) for _ in range(3))
+        alpha, beta = 3, 5
+        out, A2, B2, _ = OS.run("Found", R, A, B, C, alpha=alpha, beta=beta, depth=depth)
+        if isinstance(R, ring.ModP):
+            ref = classical.muladd_modp(alpha, A, B, beta if accumulate else 0, C, R.p)
+            assert np.array_equal(out, ref)
+        else:
+            ref = alpha * classical.mul_f64(A, B) + (beta * C if accumulate else 0)
+            assert np.allclose(out, ref, rtol=1e-10, atol=1e-10)
+        h = n // 2
+        for b in preserve:
+            M, M2 = (A, A2) if b[0] == "A" else (B, B2)
+            i, j = int(b[1]) - 1, int(b[2]) - 1
+            assert np.array_equal(M[i * h:(i + 1) * h, j * h:(j + 1) * h], M2[i * h:(i + 1) * h, j * h:(j + 1) * h])
+
+
+CASES = {
+    # name: (accumulate, preserve, temps, kinds, max_written, copies)
+    "IP": (False, (), 0, ("IP",), -1, 0),
+    "IP-4-blocks": (False, (), 0, ("IP",), 4, 3),
+    "OvL": (False, B_ALL, 1, ("IP", "SELF"), -1, 0),
+    "OvR": (False, A_ALL, 1, ("IP", "SELF"), -1, 0),
+    "T1": (False, A_ALL + B_ALL, 2, ("SELF",), -1, 0),
+    "T2": (True, A_ALL + B_ALL, 3, ("T1", "SELF"), -1, 0),
+    "AcLR": (True, (), 2, ("IP", "SELF"), -1, 0),
+    "AccR": (True, A_ALL, 2, ("IP", "OvR", "SELF"), -1, 0),
+}
+
+
+def kinds_of(Z, names):
+    search, swmm = Z
+    code = {"T1": swmm.T1_DHSS, "IP": swmm.T3_IP, "OvR": swmm.T5_OVR, "AcLR": swmm.T6_ACLR,
+            "AccR": swmm.T7_ACCR, "SELF": search.SELF}
+    return tuple(code[n] for n in names)
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_found_schedule_runs_in_the_oracle(Z, monkeypatch, case):
+    search, _ = Z
+    acc, keep, temps, kinds, max_written, copies = CASES[case]
+    o = search.schedule_search(accumulate=acc, preserve=keep, temps=temps, kinds=kinds_of(Z, kinds),
+                               max_written=max_written, max_copies=copies)
+    assert o.found and o.temps_used <= temps
+    assert all(r.dst not in keep for r in o.rows)
+    if max_written >= 0:
+        assert o.written <= max_written
+    chk = search.schedule_check(o.rows, accumulate=acc, preserve=keep, temps=temps, kinds=kinds_of(Z, kinds),
+                                max_copies=copies)
+    assert chk.found and chk.first_bad_row == -1
+    assert [r.value for r in chk.rows] == [r.value for r in o.rows]
+    run_found(Z, monkeypatch, o.rows, acc, keep)
+
+
+def test_no_in_place_product_overwrites_only_one_operand(Z):
+    """Section 5.1: C <- AB overwriting only A (or only B) needs a temporary."""
+    search, swmm = Z
+    for keep in (B_ALL, A_ALL):
+        o = search.schedule_search(preserve=keep, temps=0, kinds=(swmm.T3_IP, search.SELF))
+        assert not o.found and o.exhausted
+        o = search.schedule_search(preserve=keep, temps=1, kinds=(swmm.T3_IP, search.SELF))
+        assert o.found and o.temps_used == 1
+
+
+def test_in_place_product_overwrites_at_least_four_blocks(Z):
+    """Section 5.1: no in-place C <- AB overwrites fewer than four blocks of
+    A and B.  In the game (a recursive in-place call overwrites the blocks
+    holding its operands) the least is 7 blocks without copies, 5 with two
+    copies, and 4 with three, where 3 blocks stay out of reach."""
+    search, swmm = Z
+    ip = (swmm.T3_IP,)
+    o = search.schedule_search(temps=0, kinds=ip, max_written=6)
+    assert not o.found and o.exhausted
+    o = search.schedule_search(temps=0, kinds=ip, max_written=7)
+    assert o.found and o.written == 7
+    o = search.schedule_search(temps=0, kinds=ip, max_written=4, max_copies=2)
+    assert not o.found and o.exhausted
+    o = search.schedule_search(temps=0, kinds=ip, max_written=5, max_copies=2)
+    assert o.found and o.written == 5
+    o = search.schedule_search(temps=0, kinds=ip, max_written=3, max_copies=3)
+    assert not o.found and o.exhausted
+    o = search.schedule_search(temps=0, kinds=ip, max_written=4, max_copies=3)
+    assert o.found and o.written == 4
+
+
+def test_read_only_product_needs_two_temporaries(Z):
+    """Table 1's two temporaries are the least for C <- AB with read-only A, B."""
+    search, _ = Z
+    o = search.schedule_search(preserve=A_ALL + B_ALL, temps=1, kinds=(search.SELF,))
+    assert not o.found and o.exhausted
+
+
+@pytest.mark.parametrize("case", ["AcLR", "AccR"])
+def test_overwriting_accumulation_needs_two_temporaries(Z, case):
+    """Tables 6 and 7 use two temporaries: in the game (candidate values of
+    Section 2 and of the accumulating tables) one is not enough."""
+    search, _ = Z
+    acc, keep, temps, kinds, _, _ = CASES[case]
+    for t in (0, 1):
+        o = search.schedule_search(accumulate=True, preserve=keep, temps=t, kinds=kinds_of(Z, kinds), max_rows=30)
+        assert not o.found and o.exhausted
+
+
+# ------------------------------------------------------------------ replay
+def from_oracle(Z, table, accumulate):
+    search, _ = Z
+    where = {f"{M}{i}{j}": f"{M}{i}{j}" for M in ("AB" + ("C" if accumulate else "")) for i in "12" for j in "12"}
+    code = {v: k for k, v in ORACLE_KIND.items()}
+    rows = []
+    for row in table:
+        if row[0] == "add":
+            _, loc, name, terms = row
+            (c1, v1), (c2, v2) = terms
+            if c1 != 1:
+                (c1, v1), (c2, v2) = (c2, v2), (c1, v1)
+            assert c1 == 1
+            rows.append(search.Row(search.ADD, loc, where[v1], where[v2], coef=c2))
+        elif row[0] == "copy":
+            _, loc, name, src = row
+            rows.append(search.Row(search.COPY, loc, where[src]))
+        else:
+            _, loc, name, kind, ac, left, right, acc = row
+            if acc is not None:
+                assert where[acc[1]] == loc
+            rows.append(search.Row(search.MUL, loc, where[left], where[right], coef=acc[0] if acc else 1,
+                                   accumulate=acc is not None, sign=-1 if ac == "-a" else 1, kind=code[kind]))
+        where[name] = loc
+    return rows
+
+
+TABLES = {
+    # oracle kind: (preserve, temps, kinds, copies, recompute)
+    "T1": (A_ALL + B_ALL, 2, (1,), 0, False),
+    "T2": (A_ALL + B_ALL, 3, (1, 2), 0, False),
+    "IP": ((), 0, (3,), 0, False),
+    "OvL": (B_ALL, 1, (3, 4), 0, False),
+    "OvLM": (B_ALL + ("A12", "A22"), 1, (3, 5, 11), 2, False),
+    "OvR": (A_ALL, 1, (3, 5), 0, False),
+    "AcLR": ((), 2, (3, 6), 0, False),
+    "AccR": (A_ALL, 2, (3, 5, 7), 0, False),
+    "AcR": (A_ALL + ("B11", "B22"), 2, (1, 8), 0, False),
+    "Acc": (A_ALL + B_ALL, 2, (1, 6, 7, 9), 0, True),
+}
+
+
+@pytest.mark.parametrize("kind", list(TABLES))
+def test_paper_tables_are_legal_plays(Z, kind):
+    search, _ = Z
+    keep, temps, kinds, copies, recompute = TABLES[kind]
+    K = OS.KINDS[kind]
+    rows = from_oracle(Z, K.table, K.accumulate)
+    o = search.schedule_check(rows, accumulate=K.accumulate, preserve=keep, temps=temps, kinds=kinds,
+                              max_copies=copies, recompute=recompute)
+    assert o.found and o.first_bad_row == -1, (kind, o.first_bad_row)
+    assert o.temps_used == temps
+    names = [r[2] for r in K.table]
+    # the values the library names agree with the oracle's where both use Section 2 names
+    sec2 = {f"S{i}" for i in range(1, 5)} | {f"T{i}" for i in range(1, 5)} | {f"U{i}" for i in range(1, 8)}
+    for r, nm in zip(o.rows, names):
+        if nm in sec2 and not K.accumulate:
+            assert r.value == nm
+    # one temporary less, or without the table's recursive kinds, it is not legal
+    if temps:
+        assert not search.schedule_check(rows, accumulate=K.accumulate, preserve=keep, temps=temps - 1,
+                                         kinds=kinds, max_copies=copies, recompute=recompute).found
+
+
+def test_check_rejects_broken_tables(Z):
+    search, _ = Z
+    keep, temps, kinds, copies, recompute = TABLES["IP"]
+    rows = from_oracle(Z, OS.KINDS["IP"].table, False)
+    # a wrong sign in row 1 (S3 = A11 + A21 is no candidate value)
+    bad = [search.Row(**{**r.__dict__}) for r in rows]
+    bad[0].coef = 1
+    o = search.schedule_check(bad, preserve=keep, temps=temps, kinds=kinds)
+    assert not o.found and o.first_bad_row == 0
+    # row 7 (P1 = IP(A11 B11) into C11) reading B12 instead: not a product of Section 2
+    bad = [search.Row(**{**r.__dict__}) for r in rows]
+    bad[6].s2 = "B12"
+    o = search.schedule_check(bad, preserve=keep, temps=temps, kinds=kinds)
+    assert not o.found and o.first_bad_row == 6
+    # Table 4 with read-only B: its OvL calls are legal, an IP call on B11 is not (B11 is preserved)
+    rows4 = from_oracle(Z, OS.KINDS["OvL"].table, False)
+    bad = [search.Row(**{**r.__dict__}) for r in rows4]
+    bad[4].kind = 3
+    o = search.schedule_check(bad, preserve=B_ALL, temps=1, kinds=(3, 4))
+    assert not o.found
+    # Table 9 without recomputation: T1' is computed twice
+    keep, temps, kinds, copies, _ = TABLES["Acc"]
+    rows9 = from_oracle(Z, OS.KINDS["Acc"].table, True)
+    o = search.schedule_check(rows9, accumulate=True, preserve=keep, temps=temps, kinds=kinds)
+    assert not o.found and o.first_bad_row == 20
+
+
+def test_search_spec_errors(Z):
+    search, swmm = Z
+    with pytest.raises(swmm.SwmmError):
+        search.schedule_search(temps=4, kinds=(swmm.T3_IP,))
+    with pytest.raises(swmm.SwmmError):
+        search.schedule_search(kinds=(swmm.IPMM,))
+    with pytest.raises(ValueError):
+        search.schedule_search(preserve=("C11",))
+    names = search.node_names(True)
+    assert names[:8] == list(A_ALL + B_ALL) and {"U1", "U5", "U6", "U7", "Z1", "Z3"} <= set(names)
