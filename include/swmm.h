@@ -85,6 +85,11 @@ extern "C" {
                             t x t blocks, each the sum of t products with
                             accumulation by Table 2 (or Table 9); the
                             temporaries of one block call at a time */
+#define SWMM_CUSTOM 14   /* the handle's own one-level schedule (swmm_set_schedule in
+                            swmm_search.h), square operands; its entry point
+                            follows its contract: swmm_mul (read-only C <- aAB),
+                            swmm_muladd (read-only C <- aAB + bC) or
+                            swmm_mul_inplace (it overwrites a block of A or B) */
 #define SWMM_AUTO (-1)   /* batched calls: the autotuner picks schedule and depth */
 
 /* flags */

@@ -42,6 +42,8 @@
 
 #include <stdint.h>
 
+#include "swmm.h"
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -140,6 +142,26 @@ int swmm_schedule_search(const swmm_search_spec *spec, swmm_search_row *rows, in
  * pointer. */
 int swmm_schedule_check(const swmm_search_spec *spec, swmm_search_row *rows, int32_t nrows,
                         swmm_search_result *res);
+
+/* Give handle h a schedule of its own: `rows` (nrows of them) are checked
+ * as swmm_schedule_check does under `spec` and kept by the handle; calls
+ * with opts->sched == SWMM_CUSTOM then run them at every Winograd level,
+ * with rows whose kind is SWMM_SEARCH_SELF recursing into the same
+ * schedule and other kinds into the paper's tables (the last level is the
+ * fused tensor-core level, as for the tables).  The operands must be
+ * square; the entry point follows the contract (see SWMM_CUSTOM).  Blocks
+ * of A and B the spec does not preserve may come back overwritten.  Cached
+ * graphs of earlier calls are dropped.  Returns SWMM_OK, or SWMM_EINVAL
+ * (reason in swmm_last_error) for an illegal or incomplete schedule. */
+int swmm_set_schedule(swmm_t h, const swmm_search_spec *spec, const swmm_search_row *rows, int32_t nrows);
+
+/* Plan a call of schedule `rows` without a handle or a device: what
+ * swmm_workspace_elems reports for it (paper_elems: the schedule's own
+ * temporaries over the levels that keep them; plan_elems: the planner's
+ * peak).  opts->sched must be SWMM_CUSTOM. */
+int swmm_schedule_workspace(const swmm_search_spec *spec, const swmm_search_row *rows, int32_t nrows, int64_t m,
+                            int64_t k, int64_t n, const swmm_opts *opts, int64_t *paper_elems,
+                            int64_t *plan_elems);
 
 /* Name of candidate value `node` of the graph for `accumulate` (0 or 1):
  * "A11" ... "B22" and "C11" ... "C22" for the inputs, "S1" ... "T4", "P1" ...

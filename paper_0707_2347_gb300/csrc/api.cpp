@@ -1,6 +1,7 @@
 // C ABI of the library (include/swmm.h): argument validation, planning,
 // workspace management, CUDA-graph capture and dispatch to the executor.
 #include "swmm.h"
+#include "swmm_search.h"
 
 #include <algorithm>
 #include <array>
@@ -142,6 +143,10 @@ struct swmm_ctx {
   char *io_buf = nullptr;
   size_t io_bytes = 0;
   char io_token[2] = {0, 0};
+  // the handle's own schedule (SWMM_CUSTOM, swmm_set_schedule)
+  CustomSchedule custom;
+  KindInfo custom_info{"custom", nullptr, false, true};
+  bool has_custom = false;
   // autotuner decisions: (m, k, n, mode, p) -> (sched, depth, est_us, elems)
   std::vector<std::pair<std::array<int64_t, 5>, std::tuple<int32_t, int32_t, double, int64_t>>> tuned;
   ~swmm_ctx() {
@@ -184,13 +189,14 @@ Kind kind_of(int sched) {
     case SWMM_T7_ACCR: return K_ACCR;
     case SWMM_T8_ACR: return K_ACR;
     case SWMM_T9_ACC: return K_ACC;
+    case SWMM_CUSTOM: return K_CUSTOM;
   }
   return NKIND;
 }
 
 // Temporaries per level the paper gives for each schedule (Section 3,
 // Section 5, Section 6), summed over `levels` levels: the Lemma 1 series.
-int64_t paper_elems(int sched, int64_t m, int64_t k, int64_t n, int levels) {
+int64_t paper_elems(int sched, int64_t m, int64_t k, int64_t n, int levels, int custom_temps = 0) {
   int64_t s = 0;
   for (int i = 0; i < levels; ++i) {
     m /= 2;
@@ -206,6 +212,7 @@ int64_t paper_elems(int sched, int64_t m, int64_t k, int64_t n, int levels) {
       case SWMM_T7_ACCR:
       case SWMM_T9_ACC: s += 2 * n * n; break;                  // Eq. (3), Sec. 6
       case SWMM_T8_ACR: s += std::max(m, k) * n + m * k; break;  // Sec. 5.3
+      case SWMM_CUSTOM: s += custom_temps * n * n; break;        // its own temporaries
       default: break;                                           // IP, IPMM, classical: 0
     }
   }
@@ -273,14 +280,14 @@ struct Plan {
 // The 2 x 2 blocks of A, B and C in the order the top level's table first
 // reads them (A, B, C in order for the other drivers), so that copies to
 // the device arrive in the order the work needs them.
-std::vector<Loc> first_use(int sched) {
+std::vector<Loc> first_use(swmm_t h, int sched) {
   std::vector<Loc> order;
   auto add = [&](Loc l) {
     if (l <= C22 && std::find(order.begin(), order.end(), l) == order.end()) order.push_back(l);
   };
   const Kind k = kind_of(sched);
   if (k != NKIND) {
-    for (const Row &row : *kind_info(k).table) {
+    for (const Row &row : k == K_CUSTOM ? h->custom.rows : *kind_info(k).table) {
       if (row.op == OP_MUL) {
         add(row.s1);
         add(row.s2);
@@ -336,6 +343,12 @@ int make_plan(swmm_t h, const Req &q, const swmm_opts *o, bool check_ptrs, Plan 
     okk = sched == SWMM_T3_IP || sched == SWMM_T4_OVL || sched == SWMM_T4M_OVL || sched == SWMM_T5_OVR ||
           sched == SWMM_IP0VMM;
   if (q.entry == 2 && accum) okk = sched == SWMM_T6_ACLR || sched == SWMM_T7_ACCR || sched == SWMM_T8_ACR;
+  if (sched == SWMM_CUSTOM) {
+    if (!h->has_custom) return fail(h, SWMM_EINVAL, "no schedule set on this handle (swmm_set_schedule)");
+    // the entry point that matches the schedule's contract
+    const bool ro = h->custom.preserve == 0xffu;
+    okk = h->custom.accumulate == accum && (q.entry == 2 ? !ro : ro && q.entry == (accum ? 1 : 0));
+  }
   if (!okk) return fail(h, SWMM_EINVAL, "schedule not valid for this entry point");
   const bool ne = q.m > 0 && q.n > 0;
   if (check_ptrs) {
@@ -361,7 +374,7 @@ int make_plan(swmm_t h, const Req &q, const swmm_opts *o, bool check_ptrs, Plan 
   const int lv = sched == SWMM_TBLOCK ? levels_possible(q.m / tb, q.k / tb, q.n / tb, depth)
                                       : levels_possible(q.m, q.k, q.n, depth);
   if (sched != SWMM_CLASSICAL && sched != SWMM_IPMM && sched != SWMM_IP0VMM && sched != SWMM_TBLOCK && lv > 0) {
-    const KindInfo &K = kind_info(kind_of(sched));
+    const KindInfo &K = sched == SWMM_CUSTOM ? h->custom_info : kind_info(kind_of(sched));
     if (K.square && !(q.m == q.k && q.k == q.n))
       return fail(h, SWMM_EINVAL, std::string(K.name) + " needs square operands (Section 5.3)");
     if (sched == SWMM_T3_IP && !(q.k == q.n && q.n <= q.m))
@@ -387,6 +400,7 @@ int make_plan(swmm_t h, const Req &q, const swmm_opts *o, bool check_ptrs, Plan 
   x.simt = (o->flags & SWMM_FLAG_SIMT_LEAF) != 0;
   x.num_sms = h->num_sms;
   x.err = h->d_err;
+  x.custom = h->has_custom ? &h->custom_info : nullptr;
   if (x.fp32) {
     P.alpha.f = q.alpha ? *(const float *)q.alpha : 1.f;
     P.beta.f = q.beta ? *(const float *)q.beta : 0.f;
@@ -429,7 +443,7 @@ int make_plan(swmm_t h, const Req &q, const swmm_opts *o, bool check_ptrs, Plan 
     P.paper = paper_elems(o->ipmm_acc == SWMM_T9_ACC ? SWMM_T9_ACC : SWMM_T2_HLJJTT, q.m / tb, q.k / tb, q.n / tb,
                           tmp_levels);
   else
-    P.paper = paper_elems(sched, q.m, q.k, q.n, tmp_levels);
+    P.paper = paper_elems(sched, q.m, q.k, q.n, tmp_levels, h->custom.temps);
   return SWMM_OK;
 }
 
@@ -475,7 +489,7 @@ int enqueue(swmm_t h, const Plan &P, cudaStream_t stream, TimingHook *timing, co
   const Rect tok_in = rect_bytes(&h->io_token[0], 1), tok_out = rect_bytes(&h->io_token[1], 1);
   auto host_in = [&]() {
     if (!P.host_io) return;
-    for (Loc l : first_use(P.sched)) {
+    for (Loc l : first_use(h, P.sched)) {
       const int q = (l - A11) % 4, i = q / 2, j = q % 2;
       const View &dv = l <= A22 ? P.L : (l <= B22 ? P.R : P.D);
       const char *hp = l <= A22 ? P.hA : (l <= B22 ? P.hB : P.hC);
@@ -746,6 +760,19 @@ double model_us(const Plan &P) {
   return flops / rate + bytes / 5.5e6 + launches * 2.5;
 }
 
+// The handle's own schedule: checked in the pebble game, lowered to rows.
+int set_schedule(swmm_t h, const swmm_search_spec *spec, const swmm_search_row *rows, int32_t nrows) {
+  if (!spec || !rows) return fail(h, SWMM_EINVAL, "spec or rows is NULL");
+  CustomSchedule cs;
+  std::string err;
+  if (!lower_schedule(*spec, rows, nrows, &cs, &err)) return fail(h, SWMM_EINVAL, "schedule rejected: " + err);
+  h->custom = std::move(cs);
+  h->custom_info = KindInfo{"custom", &h->custom.rows, h->custom.accumulate, true};
+  h->has_custom = true;
+  h->graphs.clear();  // captured calls hold the previous schedule
+  return SWMM_OK;
+}
+
 }  // namespace
 
 namespace swmm {
@@ -884,12 +911,17 @@ int swmm_workspace_elems(swmm_t h, int64_t m, int64_t k, int64_t n, const swmm_o
   h->last_error.clear();
   if (!opts) return fail(h, SWMM_EINVAL, "opts is NULL");
   const int s = opts->sched;
-  const bool acc_inplace = s == SWMM_T6_ACLR || s == SWMM_T7_ACCR || s == SWMM_T8_ACR;
+  bool acc_inplace = s == SWMM_T6_ACLR || s == SWMM_T7_ACCR || s == SWMM_T8_ACR;
   int entry = 0;
   if (s == SWMM_T2_HLJJTT || s == SWMM_T9_ACC || s == SWMM_TBLOCK) entry = 1;
   if (s == SWMM_T3_IP || s == SWMM_T4_OVL || s == SWMM_T4M_OVL || s == SWMM_T5_OVR || s == SWMM_IP0VMM ||
       acc_inplace)
     entry = 2;
+  if (s == SWMM_CUSTOM && h->has_custom) {
+    const bool ro = h->custom.preserve == 0xffu;
+    entry = ro ? (h->custom.accumulate ? 1 : 0) : 2;
+    acc_inplace = !ro && h->custom.accumulate;
+  }
   static const uint32_t one = 1;
   Req q{entry, m, k, n, nullptr, nullptr, nullptr, k, n, n, &one, acc_inplace || entry == 1 ? &one : nullptr};
   Plan P;
@@ -1130,5 +1162,20 @@ const char *swmm_strerror(int code) {
 }
 
 const char *swmm_last_error(swmm_t h) { return h ? h->last_error.c_str() : "invalid handle"; }
+
+int swmm_set_schedule(swmm_t h, const swmm_search_spec *spec, const swmm_search_row *rows, int32_t nrows) {
+  if (!h) return SWMM_EINVAL;
+  h->last_error.clear();
+  return set_schedule(h, spec, rows, nrows);
+}
+
+int swmm_schedule_workspace(const swmm_search_spec *spec, const swmm_search_row *rows, int32_t nrows, int64_t m,
+                            int64_t k, int64_t n, const swmm_opts *opts, int64_t *paper_elems, int64_t *plan_elems) {
+  swmm_ctx planner;  // no device
+  const int rc = set_schedule(&planner, spec, rows, nrows);
+  if (rc != SWMM_OK) return rc;
+  if (!opts || opts->sched != SWMM_CUSTOM) return SWMM_EINVAL;
+  return swmm_workspace_elems(&planner, m, k, n, opts, paper_elems, plan_elems);
+}
 
 }  // extern "C"

@@ -653,7 +653,7 @@ void Exec::peel(Kind k, Scalar alpha, bool acc, Scalar beta, View L, View R, Vie
 
 void Exec::table(Kind k, Scalar alpha, bool acc, Scalar beta, View L, View R, View D, int depth,
                  const Arena &ar) {
-  const KindInfo &K = kind_info(k);
+  const KindInfo &K = info(k);
   const Range nv(!dry, K.name, L.rows, L.cols, R.cols, depth);
   const int64_t hm = L.rows / 2, hk = L.cols / 2, hn = R.cols / 2;
   auto dims = [&](Shape s, int64_t &r, int64_t &c) {
@@ -837,7 +837,7 @@ void Exec::table(Kind k, Scalar alpha, bool acc, Scalar beta, View L, View R, Vi
         op_end();
       }
     } else {
-      const KindInfo &S = kind_info(row.kind);
+      const KindInfo &S = info(row.kind);
       const View a = at(row.s1, SH_A), b = at(row.s2, SH_B), d = at(row.dst, SH_C);
       const Scalar al = coef(row.c1), be = row.acc ? coef(row.cacc) : Scalar{};
       before_write(d);

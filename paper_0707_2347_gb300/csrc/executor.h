@@ -66,6 +66,9 @@ struct Exec {
   int num_sms = 152;
   int *err = nullptr;
   TimingHook *timing = nullptr;
+  // the handle's own schedule (K_CUSTOM), if any
+  const KindInfo *custom = nullptr;
+  const KindInfo &info(Kind k) const { return k == K_CUSTOM ? *custom : kind_info(k); }
 
   // workspace for temporaries (bump allocator, bytes)
   char *ws = nullptr;

@@ -32,6 +32,7 @@
 // cannot be computed again) or a block that must be preserved is lost.
 #include "swmm.h"
 #include "swmm_search.h"
+#include "schedules.h"
 
 #include <algorithm>
 #include <cstdint>
@@ -814,6 +815,74 @@ bool spec_ok(const swmm_search_spec *spec) {
 }
 
 }  // namespace
+
+namespace swmm {
+
+bool lower_schedule(const swmm_search_spec &spec, const swmm_search_row *rows, int nrows, CustomSchedule *out,
+                    std::string *err) {
+  if (!spec_ok(&spec) || nrows < 1 || nrows > SWMM_SEARCH_MAX_ROWS || !rows) {
+    *err = "bad schedule spec or row count";
+    return false;
+  }
+  const Graph &g = graph(spec.accumulate);
+  std::vector<swmm_search_row> r(rows, rows + nrows);
+  bool goal;
+  uint32_t w, t;
+  const int legal = replay(spec, g, r.data(), nrows, &goal, &w, &t);
+  if (legal < nrows) {
+    *err = "row " + std::to_string(legal + 1) + " is not a legal move";
+    return false;
+  }
+  if (!goal) {
+    *err = "the results or the preserved blocks do not end in place";
+    return false;
+  }
+  static const Coef cf[4] = {CF_ONE, CF_NEG, CF_BETA, CF_NBETA};
+  auto kind_of_code = [](int c) -> Kind {
+    switch (c) {
+      case SWMM_T1_DHSS: return K_T1;
+      case SWMM_T2_HLJJTT: return K_T2;
+      case SWMM_T3_IP: return K_IP;
+      case SWMM_T4_OVL: return K_OVL;
+      case SWMM_T4M_OVL: return K_OVLM;
+      case SWMM_T5_OVR: return K_OVR;
+      case SWMM_T6_ACLR: return K_ACLR;
+      case SWMM_T7_ACCR: return K_ACCR;
+      case SWMM_T8_ACR: return K_ACR;
+      case SWMM_T9_ACC: return K_ACC;
+    }
+    return K_CUSTOM;
+  };
+  out->rows.clear();
+  for (const swmm_search_row &x : r) {
+    Row y{};
+    y.dst = (Loc)x.dst;
+    y.s1 = (Loc)x.s1;
+    y.s2 = x.op == SWMM_ROW_COPY ? (Loc)x.s1 : (Loc)x.s2;
+    y.shape = (Shape)g.nodes[x.node].vec.sp;  // SP_A, SP_B, SP_C match SH_A, SH_B, SH_C
+    if (x.op == SWMM_ROW_ADD) {
+      y.op = OP_ADD;
+      y.c1 = CF_ONE;
+      y.c2 = cf[x.coef];
+    } else if (x.op == SWMM_ROW_COPY) {
+      y.op = OP_COPY;
+    } else {
+      y.op = OP_MUL;
+      y.shape = SH_C;
+      y.c1 = x.sign > 0 ? CF_ALPHA : CF_NALPHA;
+      y.kind = kind_of_code(x.kind);
+      y.acc = x.accumulate != 0;
+      y.cacc = y.acc ? cf[x.coef] : CF_ONE;
+    }
+    out->rows.push_back(y);
+  }
+  out->accumulate = spec.accumulate != 0;
+  out->preserve = spec.preserve;
+  out->temps = __builtin_popcount(t);
+  return true;
+}
+
+}  // namespace swmm
 
 extern "C" {
 

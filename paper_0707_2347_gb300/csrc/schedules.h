@@ -7,6 +7,7 @@
 #include <vector>
 
 #include "swmm_internal.h"
+#include "swmm_search.h"
 
 namespace swmm {
 
@@ -27,7 +28,8 @@ enum Kind : int8_t {
   K_ACCR,  // Table 7                           C <- aAB + bC, overwrites B
   K_ACR,   // Table 8                           C <- aAB + bC, overwrites B12, B21
   K_ACC,   // Table 9                           C <- aAB + bC, read-only
-  NKIND
+  NKIND,
+  K_CUSTOM  // a schedule given to the handle (swmm_set_schedule), not a table
 };
 
 // Coefficients appearing in the tables.
@@ -56,6 +58,20 @@ struct KindInfo {
   bool square;
 };
 
-const KindInfo &kind_info(Kind k);
+const KindInfo &kind_info(Kind k);  // k < NKIND
+
+// A one-level schedule in the rows of include/swmm_search.h, checked by
+// replaying it in the pebble game and lowered to executor rows (recursive
+// calls of the schedule itself become K_CUSTOM).  False, with the reason
+// in *err, when a row is not a legal move or the results do not end in
+// place.
+struct CustomSchedule {
+  std::vector<Row> rows;
+  bool accumulate = false;
+  uint32_t preserve = 0;  // bit b: block b (A11..B22) is kept
+  int temps = 0;          // temporaries the rows use
+};
+bool lower_schedule(const swmm_search_spec &spec, const swmm_search_row *rows, int nrows, CustomSchedule *out,
+                    std::string *err);
 
 }  // namespace swmm

@@ -70,6 +70,12 @@ def _lib():
         lib.swmm_search_node_name.argtypes = [ctypes.c_int32, ctypes.c_int32]
         lib.swmm_search_node_name.restype = ctypes.c_char_p
         lib.swmm_search_node_count.argtypes = [ctypes.c_int32]
+        lib.swmm_set_schedule.argtypes = [ctypes.c_void_p, ctypes.POINTER(_Spec), ctypes.POINTER(_Row),
+                                          ctypes.c_int32]
+        i64p = ctypes.POINTER(ctypes.c_int64)
+        lib.swmm_schedule_workspace.argtypes = [ctypes.POINTER(_Spec), ctypes.POINTER(_Row), ctypes.c_int32,
+                                                ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
+                                                ctypes.POINTER(swmm._Opts), i64p, i64p]
         lib._search_typed = True
     return lib
 
@@ -120,6 +126,40 @@ def schedule_search(*, accumulate=False, preserve=(), temps=0, kinds=(), max_wri
                    _rows_out(rows, res.nrows, accumulate) if res.found else [])
 
 
+def _crows(rows):
+    crows = (_Row * max(len(rows), 1))()
+    for i, r in enumerate(rows):
+        crows[i] = _Row(r.op, LOCS.index(r.dst), LOCS.index(r.s1), LOCS.index(r.s2) if r.s2 else -1,
+                        COEFS.index(r.coef), int(r.accumulate), r.sign, r.kind, -1)
+    return crows
+
+
+def set_schedule(handle, rows, *, accumulate=False, preserve=(), temps=0, kinds=(), max_copies=0,
+                 recompute=False):
+    """Give a swmm.Handle the one-level schedule `rows`; calls with
+    Opts(sched=swmm.CUSTOM) then run it at every level (SELF rows recurse
+    into it).  Raises SwmmError when the schedule is not a legal play."""
+    lib = _lib()
+    spec = _spec(accumulate, preserve, temps, kinds, -1, max_copies, recompute, MAX_ROWS, 0)
+    rc = lib.swmm_set_schedule(handle.h, ctypes.byref(spec), _crows(rows), len(rows))
+    if rc != swmm.OK:
+        raise swmm.SwmmError(rc, lib.swmm_last_error(handle.h).decode())
+
+
+def schedule_workspace(rows, m, k, n, opts, *, accumulate=False, preserve=(), temps=0, kinds=(), max_copies=0,
+                       recompute=False):
+    """(schedule's own temporaries, planner peak) in elements for a call of
+    `rows` on m x k x n with `opts` (sched must be swmm.CUSTOM); no device."""
+    lib = _lib()
+    spec = _spec(accumulate, preserve, temps, kinds, -1, max_copies, recompute, MAX_ROWS, 0)
+    paper, plan = ctypes.c_int64(), ctypes.c_int64()
+    rc = lib.swmm_schedule_workspace(ctypes.byref(spec), _crows(rows), len(rows), m, k, n, ctypes.byref(opts.c()),
+                                     ctypes.byref(paper), ctypes.byref(plan))
+    if rc != swmm.OK:
+        raise swmm.SwmmError(rc, "schedule workspace failed")
+    return paper.value, plan.value
+
+
 def schedule_check(rows, *, accumulate=False, preserve=(), temps=0, kinds=(), max_copies=0,
                    recompute=False) -> Outcome:
     """Replay `rows` (a list of Row) under the same rules; found is True when
@@ -127,10 +167,7 @@ def schedule_check(rows, *, accumulate=False, preserve=(), temps=0, kinds=(), ma
     lib = _lib()
     spec = _spec(accumulate, preserve, temps, kinds, -1, max_copies, recompute, MAX_ROWS, 0)
     n = len(rows)
-    crows = (_Row * max(n, 1))()
-    for i, r in enumerate(rows):
-        crows[i] = _Row(r.op, LOCS.index(r.dst), LOCS.index(r.s1), LOCS.index(r.s2) if r.s2 else -1,
-                        COEFS.index(r.coef), int(r.accumulate), r.sign, r.kind, -1)
+    crows = _crows(rows)
     res = _Result()
     rc = lib.swmm_schedule_check(ctypes.byref(spec), crows, n, ctypes.byref(res))
     if rc != swmm.OK:

@@ -20,11 +20,11 @@ OK, EINVAL, ENOMEM, EUNSUPPORTED, ECUDA, ETIMEOUT = range(6)
 MODP, FP32 = 0, 1
 # schedules (paper table numbers)
 CLASSICAL, T1_DHSS, T2_HLJJTT, T3_IP, T4_OVL, T5_OVR = 0, 1, 2, 3, 4, 5
-T6_ACLR, T7_ACCR, T8_ACR, T9_ACC, IPMM, T4M_OVL, IP0VMM, TBLOCK = 6, 7, 8, 9, 10, 11, 12, 13
+T6_ACLR, T7_ACCR, T8_ACR, T9_ACC, IPMM, T4M_OVL, IP0VMM, TBLOCK, CUSTOM = 6, 7, 8, 9, 10, 11, 12, 13, 14
 AUTO = -1
 SCHED_NAMES = {CLASSICAL: "classical", T1_DHSS: "T1", T2_HLJJTT: "T2", T3_IP: "IP", T4_OVL: "OvL",
                T5_OVR: "OvR", T6_ACLR: "AcLR", T7_ACCR: "AccR", T8_ACR: "AcR", T9_ACC: "Acc",
-               IPMM: "IPMM", T4M_OVL: "OvLM", IP0VMM: "IP0vMM", TBLOCK: "Sec7.2"}
+               IPMM: "IPMM", T4M_OVL: "OvLM", IP0VMM: "IP0vMM", TBLOCK: "Sec7.2", CUSTOM: "custom"}
 # flags
 FLAG_UNFUSED, FLAG_SIMT_LEAF, FLAG_TIMING, FLAG_GRAPH, FLAG_SERIAL = 1, 2, 4, 8, 16
 
@@ -64,7 +64,8 @@ EXPORTS = ["swmm_create", "swmm_destroy", "swmm_set_stream", "swmm_mul", "swmm_m
            "swmm_muladd_batched", "swmm_autotune", "swmm_workspace_elems", "swmm_leaf_timing", "swmm_get_stats",
            "swmm_sync", "swmm_strerror", "swmm_last_error", "swmm_matvec", "swmm_residual", "swmm_muladd_host",
            # include/swmm_search.h (host only, see search.py)
-           "swmm_schedule_search", "swmm_schedule_check", "swmm_search_node_name", "swmm_search_node_count"]
+           "swmm_schedule_search", "swmm_schedule_check", "swmm_search_node_name", "swmm_search_node_count",
+           "swmm_set_schedule", "swmm_schedule_workspace"]
 
 _lib = None
 

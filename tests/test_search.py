@@ -270,3 +270,45 @@ def test_search_spec_errors(Z):
         search.schedule_search(preserve=("C11",))
     names = search.node_names(True)
     assert names[:8] == list(A_ALL + B_ALL) and {"U1", "U5", "U6", "U7", "Z1", "Z3"} <= set(names)
+
+
+# ------------------------------------------------- planning a found schedule
+@pytest.mark.parametrize("case", ["IP", "OvL", "T1", "T2", "AcLR", "AccR"])
+def test_found_schedule_plans_its_own_temporaries(Z, case):
+    """The planner runs a found schedule at every level (SELF rows recurse
+    into it): its peak is the schedule's own temporaries summed over the
+    levels that keep them (the last level is fused), as Lemma 1 sums them."""
+    search, swmm = Z
+    acc, keep, temps, kinds, max_written, copies = CASES[case]
+    o = search.schedule_search(accumulate=acc, preserve=keep, temps=temps, kinds=kinds_of(Z, kinds),
+                               max_written=max_written, max_copies=copies)
+    spec = dict(accumulate=acc, preserve=keep, temps=temps, kinds=kinds_of(Z, kinds), max_copies=copies)
+    for n, depth in [(512, 1), (1024, 2), (8192, 3)]:
+        opts = swmm.Opts(sched=swmm.CUSTOM, depth=depth)
+        paper, plan = search.schedule_workspace(o.rows, n, n, n, opts, **spec)
+        want = sum(o.temps_used * (n >> (lv + 1)) ** 2 for lv in range(depth - 1))
+        assert paper == want
+        if "T1" not in kinds:
+            assert plan == want
+    # unfused: every level keeps its temporaries
+    paper, plan = search.schedule_workspace(o.rows, 256, 256, 256,
+                                            swmm.Opts(sched=swmm.CUSTOM, depth=2, flags=swmm.FLAG_UNFUSED), **spec)
+    assert paper == o.temps_used * (128 ** 2 + 64 ** 2)
+
+
+def test_set_schedule_rejects_illegal_rows(Z):
+    search, swmm = Z
+    rows = from_oracle(Z, OS.KINDS["IP"].table, False)
+    rows[3].coef = 1  # T3 = B22 + B12: no candidate value
+    with pytest.raises(swmm.SwmmError):
+        search.schedule_workspace(rows, 64, 64, 64, swmm.Opts(sched=swmm.CUSTOM, depth=2), temps=0, kinds=(3,))
+    rows = from_oracle(Z, OS.KINDS["IP"].table, False)[:-1]  # U5 never written
+    with pytest.raises(swmm.SwmmError):
+        search.schedule_workspace(rows, 64, 64, 64, swmm.Opts(sched=swmm.CUSTOM, depth=2), temps=0, kinds=(3,))
+    # the printed Table 3 itself plans with no temporaries
+    rows = from_oracle(Z, OS.KINDS["IP"].table, False)
+    assert search.schedule_workspace(rows, 64, 64, 64, swmm.Opts(sched=swmm.CUSTOM, depth=3), temps=0,
+                                     kinds=(3,)) == (0, 0)
+    # non-square operands are refused (the search model is square)
+    with pytest.raises(swmm.SwmmError):
+        search.schedule_workspace(rows, 64, 48, 64, swmm.Opts(sched=swmm.CUSTOM, depth=2), temps=0, kinds=(3,))
