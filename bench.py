@@ -35,7 +35,7 @@ import numpy as np  # noqa: E402
 import synth  # noqa: E402
 
 MODP, FP32 = 0, 1
-CLASSICAL, T1, T2, IP, T9, IPMM, IP0VMM, TBLOCK = 0, 1, 2, 3, 9, 10, 12, 13
+CLASSICAL, T1, T2, IP, T9, IPMM, IP0VMM, TBLOCK, CUSTOM = 0, 1, 2, 3, 9, 10, 12, 13, 14
 
 WORKLOADS = {
     # the accumulate schedule at 8192^2, three levels (default)
@@ -75,6 +75,16 @@ WORKLOADS = {
     "ip0vmm_16384x8192x4096_p251": dict(desc="C<-AB over Z/251, m=16384 k=8192 n=4096, Algorithm 1 (IP0vMM) depth 2",
                                         m=16384, k=8192, n=4096, mode=MODP, p=251, sched=IP0VMM, depth=2,
                                         entry="inplace"),
+    # Table 1 against the schedule the pebble-game search finds for the same
+    # contract (read-only C <- AB, two temporaries) when recursive calls may
+    # accumulate: 12 block additions per level instead of 15
+    "t1_16384_p65521_d3": dict(desc="C<-AB over Z/65521, 16384^2, Table 1 depth 3", m=16384, k=16384, n=16384,
+                               mode=MODP, p=65521, sched=T1, depth=3, entry="mul"),
+    "searched12_16384_p65521_d3": dict(desc="C<-AB over Z/65521, 16384^2, searched read-only schedule with two "
+                                            "temporaries and 12 block additions (Table 2 calls accumulate), depth 3",
+                                       m=16384, k=16384, n=16384, mode=MODP, p=65521, sched=CUSTOM, depth=3,
+                                       entry="mul", search=dict(preserve="AB", temps=2, kinds=("SELF", T2),
+                                                                max_adds=12)),
     # FP32 mode: error and speed per size and depth
     "fp32_sweep": dict(desc="C<-AB+C FP32 mode (3 fp16 split products), n in {4096, 8192, 16384}, "
                             "Table 9 depth 1-4 vs classical",
@@ -399,6 +409,19 @@ def main():
     if w["entry"] == "sweep":
         run_sweep(args, w, S, h, torch, dev, rank)
         return
+    searched = None
+    if w["sched"] == CUSTOM:
+        # the schedule the pebble-game search returns for this contract (host)
+        from paper_0707_2347_gb300 import search as Q
+        sp = w["search"]
+        spec = dict(preserve=("A11", "A12", "A21", "A22", "B11", "B12", "B21", "B22") if sp["preserve"] == "AB"
+                    else (), temps=sp["temps"], kinds=tuple(Q.SELF if x == "SELF" else x for x in sp["kinds"]))
+        o = Q.schedule_search(max_adds=sp["max_adds"], **spec)
+        if not o.found:
+            raise RuntimeError("schedule search found nothing for " + args.workload)
+        Q.set_schedule(h, o.rows, **spec)
+        searched = {"rows": len(o.rows), "adds": sum(r.op == Q.ADD for r in o.rows), "temps": o.temps_used,
+                    "schedule": [f"{r.value}->{r.dst}" for r in o.rows]}
     m, k, n = w["m"], w["k"], w["n"]
     A, B, C = make_inputs(w)
     dA, dB = torch.from_numpy(A).to(dev), torch.from_numpy(B).to(dev)
@@ -489,6 +512,8 @@ def main():
                      "timing_pass": "event pair per GEMM launch, graph captured in row order"},
     }
     line["clocks"] = clk.summary()
+    if searched:
+        line["config"]["searched_schedule"] = searched
 
     if not args.no_classical and w["sched"] != CLASSICAL:
         dC.copy_(dC0)

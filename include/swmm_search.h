@@ -89,9 +89,12 @@ typedef struct {
                            be written or overwritten by a call; -1: any */
   int32_t max_copies;   /* copy rows allowed (Section 4 rule 4), >= 0; a
                            copy goes into a free block */
-  int32_t recompute;    /* 1: a block addition may be computed again (Table
-                           9 forms T1 and T2 twice); 0: each value once */
+  int32_t recompute;    /* 1: an operand sum (S1..S4, T1..T4) may be formed
+                           again (Table 9 forms T1 and T2 twice); 0: each
+                           value once.  Values of C are formed once. */
   int32_t max_rows;     /* longest schedule searched, <= SWMM_SEARCH_MAX_ROWS */
+  int32_t max_adds;     /* at most this many block additions (each one pass
+                           over HBM at an upper level); -1: any */
   int64_t max_states;   /* give up after visiting this many states (<= 0:
                            2^26) */
 } swmm_search_spec;
@@ -114,8 +117,8 @@ typedef struct {
 typedef struct {
   int32_t found;      /* 1: rows hold a schedule meeting the spec */
   int32_t exhausted;  /* 1: every state was visited: with found == 0, no
-                         schedule of at most max_rows rows exists in this
-                         model */
+                         schedule of at most max_rows rows (and max_adds
+                         additions) exists in this model */
   int32_t nrows;      /* rows written */
   int32_t written;    /* input blocks the schedule writes or overwrites */
   int32_t temps_used; /* temporaries the schedule writes */

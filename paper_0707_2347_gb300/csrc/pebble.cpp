@@ -324,8 +324,8 @@ inline uint64_t mix(uint64_t x) {  // splitmix64 finaliser
   return x ^ (x >> 31);
 }
 
-// Open-addressing set of 128-bit state fingerprints with the shallowest
-// depth each was expanded at.
+// Open-addressing set of 128-bit state fingerprints with the rows and the
+// block additions of the cheapest path each was expanded at.
 class Visited {
  public:
   bool init(int64_t cap_states) {
@@ -335,9 +335,10 @@ class Visited {
     return tab_ != nullptr;
   }
   ~Visited() { delete[] tab_; }
-  // Slot of a fingerprint, or -1 when the state was already expanded at a
-  // depth <= `depth` (nothing to do); *full when the table has no room.
-  int64_t probe(uint64_t h1, uint64_t h2, int depth, bool *full) const {
+  // Slot of a fingerprint, or -1 when the state was already expanded with
+  // no more rows and no more additions (nothing to do); *full when the
+  // table has no room.
+  int64_t probe(uint64_t h1, uint64_t h2, int depth, int adds, bool *full) const {
     h1 |= 1;
     uint64_t i = h1 & (cap_ - 1);
     for (;;) {
@@ -349,23 +350,25 @@ class Visited {
         }
         return (int64_t)i;
       }
-      if (s.h1 == h1 && s.h2 == h2) return depth < s.depth ? (int64_t)i : -1;
+      if (s.h1 == h1 && s.h2 == h2) return (depth < s.depth || adds < s.adds) ? (int64_t)i : -1;
       i = (i + 1) & (cap_ - 1);
     }
   }
-  void insert(int64_t i, uint64_t h1, uint64_t h2, int depth) {
+  void insert(int64_t i, uint64_t h1, uint64_t h2, int depth, int adds) {
     Slot &s = tab_[i];
-    if (s.h1 == 0) ++size_;
+    const bool fresh = s.h1 == 0;
+    if (fresh) ++size_;
     s.h1 = h1 | 1;
     s.h2 = h2;
-    s.depth = (uint8_t)depth;
+    s.depth = (uint8_t)(fresh ? depth : std::min<int>(depth, s.depth));
+    s.adds = (uint8_t)(fresh ? adds : std::min<int>(adds, s.adds));
   }
   int64_t size() const { return (int64_t)size_; }
 
  private:
   struct Slot {
     uint64_t h1, h2;
-    uint8_t depth;
+    uint8_t depth, adds;
   };
   Slot *tab_ = nullptr;
   uint64_t cap_ = 0, size_ = 0;
@@ -398,7 +401,7 @@ class Search {
       if (g_.nodes[i].input) s.loc[g_.nodes[i].home] = (int8_t)i;
     s.done = g_.inputs;
     const uint64_t want = normalize(&s);
-    found_ = dfs(s, 0, want);
+    found_ = dfs(s, 0, 0, want);
     res->found = found_ ? 1 : 0;
     res->exhausted = (!found_ && !full_) ? 1 : 0;
     res->states = vis_.size();
@@ -426,7 +429,7 @@ class Search {
   }
   // a product is used once; without `recompute` a value is computed once
   bool can_compute(const State &s, const Deriv &d, int w) const {
-    if (d.type == D_ADD) return !(s.done >> w & 1) || sp_.recompute;
+    if (d.type == D_ADD) return !(s.done >> w & 1) || (sp_.recompute && g_.nodes[w].vec.sp != SP_C);
     return !(s.prod >> d.prod & 1);
   }
   // A value must be produced when it is a result or a preserved block not
@@ -558,11 +561,20 @@ class Search {
     return unused + __builtin_popcount(ops & ~pres) + std::max(0, pending - unused);
   }
 
-  bool step(State n, int depth, const swmm_search_row &row) {
+  // Lower bound on the block additions still to come: one per absent
+  // operand sum of a pending product.
+  int adds_bound(const State &s, uint64_t pres) const {
+    uint64_t ops = 0;
+    for (int p = 0; p < 7; ++p)
+      if (!(s.prod >> p & 1)) ops |= (1ull << g_.prod_a[p]) | (1ull << g_.prod_b[p]);
+    return __builtin_popcount(ops & ~pres & ~g_.inputs);
+  }
+
+  bool step(State n, int depth, int adds, const swmm_search_row &row) {
     if (sp_.max_written >= 0 && written_bound(n) > sp_.max_written) return false;
     const uint64_t want = normalize(&n);
     path_.push_back(row);
-    const bool ok = dfs(n, depth + 1, want);
+    const bool ok = dfs(n, depth + 1, adds + (row.op == SWMM_ROW_ADD ? 1 : 0), want);
     if (!ok) path_.pop_back();
     return ok;
   }
@@ -578,7 +590,7 @@ class Search {
     uint64_t keep = 0;
     for (uint64_t m = g_.results | preserved_; m; m &= m - 1) {
       const int i = __builtin_ctzll(m);
-      if (at_home(s, i) && (!sp_.recompute || (preserved_ >> i & 1))) keep |= 1ull << i;
+      if (at_home(s, i)) keep |= 1ull << i;  // results are C values: never formed twice
     }
     for (int p = 0; p < 7; ++p) {
       if (s.prod >> p & 1) continue;
@@ -602,7 +614,8 @@ class Search {
     return m;
   }
 
-  bool dfs(const State &s, int depth, uint64_t want) {
+  bool dfs(const State &s, int depth, int adds, uint64_t want) {
+    if (sp_.max_adds >= 0 && adds > sp_.max_adds) return false;
     if (goal(s)) {
       best_ = path_;
       return true;
@@ -610,9 +623,10 @@ class Search {
     if (full_) return false;
     const uint64_t pres = present(s);
     if (depth + rows_bound(s, pres) > sp_.max_rows) return false;
+    if (sp_.max_adds >= 0 && adds + adds_bound(s, pres) > sp_.max_adds) return false;
     uint64_t h1, h2;
     fingerprint(s, pres, want, &h1, &h2);
-    const int64_t slot = vis_.probe(h1, h2, depth, &full_);
+    const int64_t slot = vis_.probe(h1, h2, depth, adds, &full_);
     if (slot < 0) return false;
     // dead states go to a lossy cache (an evicted one is only re-checked)
     uint64_t &dead = dead_[h1 & (kDeadSlots - 1)];
@@ -621,7 +635,7 @@ class Search {
       dead = h2 | 1;
       return false;
     }
-    vis_.insert(slot, h1, h2, depth);
+    vis_.insert(slot, h1, h2, depth, adds);
     const uint32_t dmask = dests(s);
 
     for (uint64_t m = want & ~g_.inputs; m; m &= m - 1) {
@@ -641,7 +655,7 @@ class Search {
             n.done |= 1ull << w;
             wrote(n, dst);
             const swmm_search_row r{SWMM_ROW_ADD, dst, lu, lv, d.coef, 0, 1, 0, w};
-            if (step(n, depth, r)) return true;
+            if (step(n, depth, adds, r)) return true;
             if (full_) return false;
           }
           continue;
@@ -667,7 +681,7 @@ class Search {
                 if (c.clob & 1) n.loc[la] = kEmpty, wrote(n, la);
                 if (c.clob & 2) n.loc[lb] = kEmpty, wrote(n, lb);
                 const swmm_search_row r{SWMM_ROW_MUL, dst, la, lb, d.coef, d.type == D_ACC ? 1 : 0, d.sign, c.kind, w};
-                if (step(n, depth, r)) return true;
+                if (step(n, depth, adds, r)) return true;
                 if (full_) return false;
               }
             }
@@ -688,7 +702,7 @@ class Search {
           n.copies++;
           wrote(n, dst);
           const swmm_search_row r{SWMM_ROW_COPY, dst, from, -1, 0, 0, 1, 0, x};
-          if (step(n, depth, r)) return true;
+          if (step(n, depth, adds, r)) return true;
           if (full_) return false;
         }
       }
@@ -753,7 +767,7 @@ int replay(const swmm_search_spec &sp, const Graph &g, swmm_search_row *rows, in
       Vec cv;
       if (u.sp != v.sp || !scaled(v, r.coef, &cv)) return i;
       const int w = node_of(add(u, cv));
-      if (w < 0 || g.nodes[w].input || ((done >> w & 1) && !sp.recompute)) return i;
+      if (w < 0 || g.nodes[w].input || ((done >> w & 1) && !(sp.recompute && g.nodes[w].vec.sp != SP_C))) return i;
       loc[r.dst] = (int8_t)w;
       done |= 1ull << w;
       r.node = w;
@@ -806,7 +820,7 @@ int replay(const swmm_search_spec &sp, const Graph &g, swmm_search_row *rows, in
 bool spec_ok(const swmm_search_spec *spec) {
   if (!spec || (spec->accumulate != 0 && spec->accumulate != 1)) return false;
   if (spec->temps < 0 || spec->temps > 3 || spec->max_copies < 0 || spec->max_rows < 1 ||
-      spec->max_rows > SWMM_SEARCH_MAX_ROWS || (spec->preserve & ~0xffu))
+      spec->max_rows > SWMM_SEARCH_MAX_ROWS || (spec->preserve & ~0xffu) || spec->max_adds > 255)
     return false;
   const uint32_t known = (1u << SWMM_T1_DHSS) | (1u << SWMM_T2_HLJJTT) | (1u << SWMM_T3_IP) | (1u << SWMM_T4_OVL) |
                          (1u << SWMM_T5_OVR) | (1u << SWMM_T6_ACLR) | (1u << SWMM_T7_ACCR) | (1u << SWMM_T8_ACR) |

@@ -24,7 +24,8 @@ MAX_ROWS = 64
 class _Spec(ctypes.Structure):
     _fields_ = [("accumulate", ctypes.c_int32), ("preserve", ctypes.c_uint32), ("temps", ctypes.c_int32),
                 ("kinds", ctypes.c_uint32), ("max_written", ctypes.c_int32), ("max_copies", ctypes.c_int32),
-                ("recompute", ctypes.c_int32), ("max_rows", ctypes.c_int32), ("max_states", ctypes.c_int64)]
+                ("recompute", ctypes.c_int32), ("max_rows", ctypes.c_int32), ("max_adds", ctypes.c_int32),
+                ("max_states", ctypes.c_int64)]
 
 
 class _Row(ctypes.Structure):
@@ -80,7 +81,7 @@ def _lib():
     return lib
 
 
-def _spec(accumulate, preserve, temps, kinds, max_written, max_copies, recompute, max_rows, max_states):
+def _spec(accumulate, preserve, temps, kinds, max_written, max_copies, recompute, max_rows, max_states, max_adds=-1):
     pm = 0
     for b in preserve:
         i = LOCS.index(b)
@@ -91,7 +92,7 @@ def _spec(accumulate, preserve, temps, kinds, max_written, max_copies, recompute
     for k in kinds:
         km |= 1 << int(k)
     return _Spec(int(bool(accumulate)), pm, temps, km, max_written, max_copies, int(bool(recompute)), max_rows,
-                 max_states)
+                 max_adds, max_states)
 
 
 def node_names(accumulate: bool) -> list:
@@ -111,12 +112,14 @@ def _rows_out(crows, n, accumulate):
 
 
 def schedule_search(*, accumulate=False, preserve=(), temps=0, kinds=(), max_written=-1, max_copies=0,
-                    recompute=False, max_rows=40, max_states=0) -> Outcome:
+                    recompute=False, max_rows=40, max_states=0, max_adds=-1) -> Outcome:
     """Search for one level's schedule: C <- alpha AB (+ beta C when
     `accumulate`), keeping the blocks named in `preserve`, with `temps`
-    temporaries, recursive products of the given `kinds`."""
+    temporaries, recursive products of the given `kinds`, at most
+    `max_adds` block additions."""
     lib = _lib()
-    spec = _spec(accumulate, preserve, temps, kinds, max_written, max_copies, recompute, max_rows, max_states)
+    spec = _spec(accumulate, preserve, temps, kinds, max_written, max_copies, recompute, max_rows, max_states,
+                 max_adds)
     rows = (_Row * MAX_ROWS)()
     res = _Result()
     rc = lib.swmm_schedule_search(ctypes.byref(spec), rows, MAX_ROWS, ctypes.byref(res))

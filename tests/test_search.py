@@ -98,8 +98,8 @@ CASES = {
 
 def kinds_of(Z, names):
     search, swmm = Z
-    code = {"T1": swmm.T1_DHSS, "IP": swmm.T3_IP, "OvR": swmm.T5_OVR, "AcLR": swmm.T6_ACLR,
-            "AccR": swmm.T7_ACCR, "SELF": search.SELF}
+    code = {"T1": swmm.T1_DHSS, "T2": swmm.T2_HLJJTT, "IP": swmm.T3_IP, "OvR": swmm.T5_OVR,
+            "AcLR": swmm.T6_ACLR, "AccR": swmm.T7_ACCR, "SELF": search.SELF}
     return tuple(code[n] for n in names)
 
 
@@ -156,6 +156,25 @@ def test_read_only_product_needs_two_temporaries(Z):
     search, _ = Z
     o = search.schedule_search(preserve=A_ALL + B_ALL, temps=1, kinds=(search.SELF,))
     assert not o.found and o.exhausted
+
+
+def test_fewest_block_additions(Z, monkeypatch):
+    """Section 2's 15 additions are the least for a read-only C <- AB with
+    two temporaries when the recursive calls do not accumulate; with calls
+    that accumulate into their destination (Table 2's kind), 12 suffice and
+    11 do not.  The 12-addition schedule runs in the oracle."""
+    search, swmm = Z
+    keep = A_ALL + B_ALL
+    o = search.schedule_search(preserve=keep, temps=2, kinds=(search.SELF,), max_adds=15)
+    assert o.found and sum(r.op == search.ADD for r in o.rows) == 15
+    o = search.schedule_search(preserve=keep, temps=2, kinds=(search.SELF,), max_adds=14)
+    assert not o.found and o.exhausted
+    kinds = (search.SELF, swmm.T2_HLJJTT)
+    o = search.schedule_search(preserve=keep, temps=2, kinds=kinds, max_adds=11)
+    assert not o.found and o.exhausted
+    o = search.schedule_search(preserve=keep, temps=2, kinds=kinds, max_adds=12)
+    assert o.found and sum(r.op == search.ADD for r in o.rows) == 12 and o.temps_used == 2
+    run_found(Z, monkeypatch, o.rows, False, keep)
 
 
 @pytest.mark.parametrize("case", ["AcLR", "AccR"])
