@@ -31,9 +31,10 @@
  *
  * The search is a depth-first enumeration of the game's states (block
  * contents, values computed, products used, input blocks overwritten) with
- * a visited set and admissible bounds (rows still needed, blocks that will
- * be overwritten), so a negative answer with `exhausted` set is a proof that
- * no schedule of at most max_rows rows exists in this model.
+ * a visited set and admissible bounds (rows and block additions still
+ * needed, blocks that will be overwritten), so a negative answer with
+ * `exhausted` set is a proof that no schedule within the spec's limits
+ * exists in this model.
  *
  * No GPU is used; the library may be loaded on a host without one.
  */

@@ -29,7 +29,9 @@
 // 128-bit fingerprint of the state (temporaries are interchangeable, so
 // their contents are sorted first).  A state is pruned as soon as some
 // result can no longer be obtained (a value it needs was overwritten and
-// cannot be computed again) or a block that must be preserved is lost.
+// cannot be computed again), a block that must be preserved is lost, or an
+// admissible bound (rows, block additions, input blocks overwritten) shows
+// that the spec's limits cannot be met from it.
 #include "swmm.h"
 #include "swmm_search.h"
 #include "schedules.h"
