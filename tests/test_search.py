@@ -14,6 +14,8 @@ Pins:
     and none overwrites fewer than four input blocks; and the memory of
     Tables 1, 4, 5, 6 and 7 is the least the game allows.
 """
+import ctypes
+
 import numpy as np
 import pytest
 
@@ -331,3 +333,26 @@ def test_set_schedule_rejects_illegal_rows(Z):
     # non-square operands are refused (the search model is square)
     with pytest.raises(swmm.SwmmError):
         search.schedule_workspace(rows, 64, 48, 64, swmm.Opts(sched=swmm.CUSTOM, depth=2), temps=0, kinds=(3,))
+
+
+def test_mixed_schedule_table9_over_table2(Z):
+    """Mixed schedules per level: Table 9's rows with Table 2 in place of its
+    recursive Acc calls are a legal play, run through the handle's own
+    schedule, and keep one more quarter-size temporary at the second level
+    than Table 9 (Table 2 holds three, Section 3.2)."""
+    search, swmm = Z
+    keep, temps, kinds, copies, recompute = TABLES["Acc"]
+    rows = from_oracle(Z, OS.KINDS["Acc"].table, True)
+    for r in rows:
+        if r.op == search.MUL and r.kind == swmm.T9_ACC:
+            r.kind = swmm.T2_HLJJTT
+    spec = dict(accumulate=True, preserve=keep, temps=temps, kinds=(1, 2, 6, 7), recompute=recompute)
+    assert search.schedule_check(rows, **spec).found
+    n = 8192
+    _, plan = search.schedule_workspace(rows, n, n, n, swmm.Opts(sched=swmm.CUSTOM, depth=3), **spec)
+    paper9, plan9 = ctypes.c_int64(), ctypes.c_int64()
+    opts9 = swmm.Opts(sched=swmm.T9_ACC, depth=3).c()
+    assert swmm.load().swmm_workspace_elems(None, n, n, n, ctypes.byref(opts9), ctypes.byref(paper9),
+                                            ctypes.byref(plan9)) == swmm.OK
+    assert plan9.value == 2 * (n // 2) ** 2 + 2 * (n // 4) ** 2
+    assert plan == plan9.value + (n // 4) ** 2
