@@ -48,7 +48,7 @@ namespace {
 // ------------------------------------------------------------------ values
 enum Space : int8_t { SP_A = 0, SP_B = 1, SP_C = 2 };
 constexpr int kDim = 11;  // C space: P1..P7, C11, C12, C21, C22
-constexpr int kMaxNodes = 64;
+constexpr size_t kMaxNodes = 64;
 
 struct Vec {
   Space sp = SP_A;
@@ -206,6 +206,10 @@ void push(Graph &g, const char *name, const char *expr) {
   parse(expr, &n.vec);
   g.nodes.push_back(n);
 }
+
+// value sets are bit masks of one 64-bit word; location contents are int8
+static_assert(sizeof(kAB) / sizeof(Def) + sizeof(kExtraABC) / sizeof(Def) + 4 <= kMaxNodes,
+              "candidate values must fit a 64-bit mask");
 
 Graph build_graph(int accumulate) {
   Graph g;
