@@ -167,6 +167,16 @@ int swmm_schedule_workspace(const swmm_search_spec *spec, const swmm_search_row 
                             int64_t k, int64_t n, const swmm_opts *opts, int64_t *paper_elems,
                             int64_t *plan_elems);
 
+/* The rows of the paper's table `sched` (SWMM_T1_DHSS ... SWMM_T9_ACC,
+ * SWMM_T4M_OVL) as the library runs them, in the form swmm_schedule_check
+ * and swmm_set_schedule take (node = -1; a recursive call of the table
+ * itself has the table's own code as kind), so that a table can be
+ * replayed, or changed (another kind for some rows) and run as the
+ * handle's schedule.  *nrows receives the table's row count.  Returns
+ * SWMM_OK, or SWMM_EINVAL for an unknown code or when max_rows is smaller
+ * than the table. */
+int swmm_table_rows(int32_t sched, swmm_search_row *rows, int32_t max_rows, int32_t *nrows);
+
 /* Name of candidate value `node` of the graph for `accumulate` (0 or 1):
  * "A11" ... "B22" and "C11" ... "C22" for the inputs, "S1" ... "T4", "P1" ...
  * "P7", "U1" ... "U7" for the Section 2 values (U1, U5, U6, U7 are the

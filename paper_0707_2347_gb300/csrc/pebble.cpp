@@ -837,6 +837,19 @@ bool spec_ok(const swmm_search_spec *spec) {
 }  // namespace
 
 namespace swmm {
+namespace {
+
+// schedule codes of swmm.h <-> kinds of the executor
+constexpr int kCodeOfKind[NKIND] = {SWMM_T1_DHSS, SWMM_T2_HLJJTT, SWMM_T3_IP,   SWMM_T4_OVL,  SWMM_T4M_OVL,
+                                    SWMM_T5_OVR,  SWMM_T6_ACLR,   SWMM_T7_ACCR, SWMM_T8_ACR, SWMM_T9_ACC};
+static_assert(K_T1 == 0 && K_OVLM == 4 && K_ACC == 9, "kind order");
+Kind kind_of_code(int c) {
+  for (int k = 0; k < NKIND; ++k)
+    if (kCodeOfKind[k] == c) return (Kind)k;
+  return K_CUSTOM;
+}
+
+}  // namespace
 
 bool lower_schedule(const swmm_search_spec &spec, const swmm_search_row *rows, int nrows, CustomSchedule *out,
                     std::string *err) {
@@ -858,21 +871,6 @@ bool lower_schedule(const swmm_search_spec &spec, const swmm_search_row *rows, i
     return false;
   }
   static const Coef cf[4] = {CF_ONE, CF_NEG, CF_BETA, CF_NBETA};
-  auto kind_of_code = [](int c) -> Kind {
-    switch (c) {
-      case SWMM_T1_DHSS: return K_T1;
-      case SWMM_T2_HLJJTT: return K_T2;
-      case SWMM_T3_IP: return K_IP;
-      case SWMM_T4_OVL: return K_OVL;
-      case SWMM_T4M_OVL: return K_OVLM;
-      case SWMM_T5_OVR: return K_OVR;
-      case SWMM_T6_ACLR: return K_ACLR;
-      case SWMM_T7_ACCR: return K_ACCR;
-      case SWMM_T8_ACR: return K_ACR;
-      case SWMM_T9_ACC: return K_ACC;
-    }
-    return K_CUSTOM;
-  };
   out->rows.clear();
   for (const swmm_search_row &x : r) {
     Row y{};
@@ -936,6 +934,55 @@ int swmm_schedule_check(const swmm_search_spec *spec, swmm_search_row *rows, int
   res->found = (res->nrows == nrows && goal) ? 1 : 0;
   res->written = __builtin_popcount(w);
   res->temps_used = __builtin_popcount(t);
+  return SWMM_OK;
+}
+
+int swmm_table_rows(int32_t sched, swmm_search_row *rows, int32_t max_rows, int32_t *nrows) {
+  using namespace swmm;
+  const Kind k = kind_of_code(sched);
+  if (k == K_CUSTOM || !nrows || max_rows < 0 || (!rows && max_rows > 0)) return SWMM_EINVAL;
+  const std::vector<Row> &t = *kind_info(k).table;
+  *nrows = (int32_t)t.size();
+  if ((int)t.size() > max_rows) return SWMM_EINVAL;
+  auto coef_of = [](Coef c) {
+    switch (c) {
+      case CF_NEG: return SWMM_COEF_NEG;
+      case CF_BETA: return SWMM_COEF_BETA;
+      case CF_NBETA: return SWMM_COEF_NBETA;
+      default: return SWMM_COEF_ONE;
+    }
+  };
+  for (size_t i = 0; i < t.size(); ++i) {
+    const Row &y = t[i];
+    swmm_search_row &x = rows[i];
+    x = swmm_search_row{};
+    x.dst = y.dst;
+    x.s1 = y.s1;
+    x.s2 = y.s2;
+    x.sign = 1;
+    x.node = -1;
+    if (y.op == OP_ADD) {
+      x.op = SWMM_ROW_ADD;
+      // rows are u + c v; a leading -1 puts the other operand first
+      if (y.c1 == CF_ONE) {
+        x.coef = coef_of(y.c2);
+      } else {
+        x.s1 = y.s2;
+        x.s2 = y.s1;
+        x.coef = coef_of(y.c1);
+        if (y.c2 != CF_ONE) return SWMM_EUNSUPPORTED;
+      }
+    } else if (y.op == OP_COPY) {
+      x.op = SWMM_ROW_COPY;
+      x.s2 = -1;
+    } else {
+      x.op = SWMM_ROW_MUL;
+      x.sign = y.c1 == CF_NALPHA ? -1 : 1;
+      x.kind = kCodeOfKind[y.kind];
+      x.accumulate = y.acc ? 1 : 0;
+      x.coef = y.acc ? coef_of(y.cacc) : SWMM_COEF_ONE;
+    }
+  }
   return SWMM_OK;
 }
 

@@ -77,6 +77,8 @@ def _lib():
         lib.swmm_schedule_workspace.argtypes = [ctypes.POINTER(_Spec), ctypes.POINTER(_Row), ctypes.c_int32,
                                                 ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
                                                 ctypes.POINTER(swmm._Opts), i64p, i64p]
+        lib.swmm_table_rows.argtypes = [ctypes.c_int32, ctypes.POINTER(_Row), ctypes.c_int32,
+                                        ctypes.POINTER(ctypes.c_int32)]
         lib._search_typed = True
     return lib
 
@@ -161,6 +163,21 @@ def schedule_workspace(rows, m, k, n, opts, *, accumulate=False, preserve=(), te
     if rc != swmm.OK:
         raise swmm.SwmmError(rc, "schedule workspace failed")
     return paper.value, plan.value
+
+
+def table_rows(sched: int) -> list:
+    """The rows of the paper's table `sched` (a schedule code of swmm.py) as
+    the library runs them; value names are left empty (schedule_check
+    fills them)."""
+    lib = _lib()
+    crows = (_Row * MAX_ROWS)()
+    n = ctypes.c_int32()
+    rc = lib.swmm_table_rows(sched, crows, MAX_ROWS, ctypes.byref(n))
+    if rc != swmm.OK:
+        raise swmm.SwmmError(rc, f"no table for schedule code {sched}")
+    return [Row(op=r.op, dst=LOCS[r.dst], s1=LOCS[r.s1], s2=LOCS[r.s2] if r.op != COPY else None,
+                coef=COEFS[r.coef], accumulate=bool(r.accumulate), sign=r.sign, kind=r.kind)
+            for r in crows[:n.value]]
 
 
 def schedule_check(rows, *, accumulate=False, preserve=(), temps=0, kinds=(), max_copies=0,

@@ -65,7 +65,7 @@ EXPORTS = ["swmm_create", "swmm_destroy", "swmm_set_stream", "swmm_mul", "swmm_m
            "swmm_sync", "swmm_strerror", "swmm_last_error", "swmm_matvec", "swmm_residual", "swmm_muladd_host",
            # include/swmm_search.h (host only, see search.py)
            "swmm_schedule_search", "swmm_schedule_check", "swmm_search_node_name", "swmm_search_node_count",
-           "swmm_set_schedule", "swmm_schedule_workspace"]
+           "swmm_set_schedule", "swmm_schedule_workspace", "swmm_table_rows"]
 
 _lib = None
 

@@ -342,7 +342,7 @@ def test_mixed_schedule_table9_over_table2(Z):
     than Table 9 (Table 2 holds three, Section 3.2)."""
     search, swmm = Z
     keep, temps, kinds, copies, recompute = TABLES["Acc"]
-    rows = from_oracle(Z, OS.KINDS["Acc"].table, True)
+    rows = search.table_rows(swmm.T9_ACC)
     for r in rows:
         if r.op == search.MUL and r.kind == swmm.T9_ACC:
             r.kind = swmm.T2_HLJJTT
@@ -356,3 +356,24 @@ def test_mixed_schedule_table9_over_table2(Z):
                                             ctypes.byref(plan9)) == swmm.OK
     assert plan9.value == 2 * (n // 2) ** 2 + 2 * (n // 4) ** 2
     assert plan == plan9.value + (n // 4) ** 2
+
+
+CODE = {"T1": 1, "T2": 2, "IP": 3, "OvL": 4, "OvLM": 11, "OvR": 5, "AcLR": 6, "AccR": 7, "AcR": 8, "Acc": 9}
+
+
+@pytest.mark.parametrize("kind", list(TABLES))
+def test_library_tables_match_the_oracle_transcription(Z, kind):
+    """The tables the library runs (its own transcription of Tables 1-9)
+    replayed in the game write, row by row, the same value into the same
+    block with the same call kind as the oracle's independent transcription."""
+    search, _ = Z
+    keep, temps, kinds, copies, recompute = TABLES[kind]
+    K = OS.KINDS[kind]
+    spec = dict(accumulate=K.accumulate, preserve=keep, temps=temps, kinds=kinds, max_copies=copies,
+                recompute=recompute)
+    lib = search.schedule_check(search.table_rows(CODE[kind]), **spec)
+    ora = search.schedule_check(from_oracle(Z, K.table, K.accumulate), **spec)
+    assert lib.found and ora.found
+    assert len(lib.rows) == len(ora.rows)
+    for i, (a, b) in enumerate(zip(lib.rows, ora.rows)):
+        assert (a.op, a.dst, a.value, a.kind, a.accumulate) == (b.op, b.dst, b.value, b.kind, b.accumulate), (kind, i)
