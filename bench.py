@@ -85,6 +85,12 @@ WORKLOADS = {
                                        m=16384, k=16384, n=16384, mode=MODP, p=65521, sched=CUSTOM, depth=3,
                                        entry="mul", search=dict(preserve="AB", temps=2, kinds=("SELF", T2),
                                                                 max_adds=12)),
+    # a mixed schedule: Table 9 at the top level, Table 2 (14 block additions
+    # instead of 17, one more temporary) for its accumulating calls below
+    "t9_over_t2_8192_p65521": dict(desc="C<-AB+C over Z/65521, 8192^2, Table 9 rows at every Table 9 level with "
+                                        "Table 2 for their accumulating calls, depth 3",
+                                   m=8192, k=8192, n=8192, mode=MODP, p=65521, sched=CUSTOM, depth=3,
+                                   entry="muladd", table=T9, replace={T9: T2, 6: T2, 7: T2}),
     # FP32 mode: error and speed per size and depth
     "fp32_sweep": dict(desc="C<-AB+C FP32 mode (3 fp16 split products), n in {4096, 8192, 16384}, "
                             "Table 9 depth 1-4 vs classical",
@@ -410,7 +416,18 @@ def main():
         run_sweep(args, w, S, h, torch, dev, rank)
         return
     searched = None
-    if w["sched"] == CUSTOM:
+    if w["sched"] == CUSTOM and "table" in w:
+        # a paper table as the library runs it, with other kinds for some calls
+        from paper_0707_2347_gb300 import search as Q
+        rows = Q.table_rows(w["table"])
+        for r in rows:
+            if r.op == Q.MUL:
+                r.kind = w["replace"].get(r.kind, r.kind)
+        kinds = sorted({r.kind for r in rows if r.op == Q.MUL})
+        Q.set_schedule(h, rows, accumulate=True, preserve=("A11", "A12", "A21", "A22", "B11", "B12", "B21", "B22"),
+                       temps=2, kinds=kinds, recompute=True)
+        searched = {"table": S.SCHED_NAMES[w["table"]], "kinds": [S.SCHED_NAMES[k] for k in kinds]}
+    elif w["sched"] == CUSTOM:
         # the schedule the pebble-game search returns for this contract (host)
         from paper_0707_2347_gb300 import search as Q
         sp = w["search"]
@@ -513,7 +530,7 @@ def main():
     }
     line["clocks"] = clk.summary()
     if searched:
-        line["config"]["searched_schedule"] = searched
+        line["config"]["custom_schedule"] = searched
 
     if not args.no_classical and w["sched"] != CLASSICAL:
         dC.copy_(dC0)
