@@ -148,6 +148,7 @@ struct Node {
   bool input = false, result = false;
   std::vector<Deriv> der;
   uint64_t need_any = 0;  // values some derivation of it reads
+  unsigned finishers = 0; // products an accumulation into it can use (bit p)
 };
 
 struct Graph {
@@ -278,6 +279,7 @@ Graph build_graph(int accumulate) {
       }
     }
     for (Deriv &d : W.der) {
+      if (d.type == D_ACC) W.finishers |= 1u << d.prod;
       if (d.type == D_ADD) d.rd = (1ull << d.u) | (1ull << d.v);
       else d.rd = (1ull << g.prod_a[d.prod]) | (1ull << g.prod_b[d.prod]) | (d.type == D_ACC ? 1ull << d.v : 0);
       W.need_any |= d.rd;
@@ -557,24 +559,51 @@ class Search {
   // absent operand sum of a pending product, one per result not in place
   // beyond those a product row can leave in place.
   int rows_bound(const State &s, uint64_t pres) const {
-    int unused = 7 - __builtin_popcount(s.prod);
-    uint64_t ops = 0;
-    for (int p = 0; p < 7; ++p)
-      if (!(s.prod >> p & 1)) ops |= (1ull << g_.prod_a[p]) | (1ull << g_.prod_b[p]);
-    int pending = 0;
-    for (uint64_t m = g_.results; m; m &= m - 1)
-      if (!at_home(s, __builtin_ctzll(m))) ++pending;
-    return unused + __builtin_popcount(ops & ~pres) + std::max(0, pending - unused);
+    const int unused = 7 - __builtin_popcount(s.prod);
+    return unused + absent_operands(s, pres) + unfinished(s);
   }
-
-  // Lower bound on the block additions still to come: one per absent
-  // operand sum of a pending product.
-  int adds_bound(const State &s, uint64_t pres) const {
+  // absent operand sums of pending products (each needs an addition)
+  int absent_operands(const State &s, uint64_t pres) const {
     uint64_t ops = 0;
     for (int p = 0; p < 7; ++p)
       if (!(s.prod >> p & 1)) ops |= (1ull << g_.prod_a[p]) | (1ull << g_.prod_b[p]);
     return __builtin_popcount(ops & ~pres & ~g_.inputs);
   }
+  // Results not in place that no pending product can finish: a result's
+  // last row is an addition unless it accumulates a product into the rest
+  // of the result, and each product finishes at most one result (a
+  // bipartite matching of pending results to pending products).
+  int unfinished(const State &s) const {
+    int res[4], n = 0;
+    for (uint64_t m = g_.results; m; m &= m - 1) {
+      const int r = __builtin_ctzll(m);
+      if (!at_home(s, r)) res[n++] = r;
+    }
+    int owner[7] = {-1, -1, -1, -1, -1, -1, -1};
+    int matched = 0;
+    for (int i = 0; i < n; ++i) {
+      bool seen[7] = {};
+      if (augment(s, res, i, owner, seen)) ++matched;
+    }
+    return n - matched;
+  }
+  bool augment(const State &s, const int *res, int i, int *owner, bool *seen) const {
+    const unsigned fin = g_.nodes[res[i]].finishers & ~s.prod;
+    for (int p = 0; p < 7; ++p) {
+      if (!(fin >> p & 1) || seen[p]) continue;
+      seen[p] = true;
+      if (owner[p] < 0 || augment(s, res, owner[p], owner, seen)) {
+        owner[p] = i;
+        return true;
+      }
+    }
+    return false;
+  }
+
+  // Lower bound on the block additions still to come: one per absent
+  // operand sum of a pending product, one per result no pending product
+  // can finish.
+  int adds_bound(const State &s, uint64_t pres) const { return absent_operands(s, pres) + unfinished(s); }
 
   bool step(State n, int depth, int adds, const swmm_search_row &row) {
     if (sp_.max_written >= 0 && written_bound(n) > sp_.max_written) return false;

@@ -63,8 +63,8 @@ def run_found(Z, monkeypatch, rows, accumulate, preserve):
     keep = frozenset(blocks[b] for b in preserve)
     kind = OS.Kind(table, accumulate, frozenset(blocks.values()) - keep, keep, True)
     monkeypatch.setitem(OS.KINDS, "Found", kind)
-    for R, n, depth in [(ring.ModP(65521), 8, 1), (ring.ModP(251), 8, 2), (ring.ModP(65521), 16, 3),
-                        (ring.Real(), 16, 2)]:
+    for R, n, depth in [(ring.ModP(65521), 8, 1), (ring.ModP(251), 8, 2), (ring.ModP(65521), 8, 3),
+                        (ring.Real(), 8, 2)]:
         rng = np.random.default_rng(n + depth)
         if isinstance(R, ring.ModP):
             A, B, C = (rng.integers(0, R.p, (n, n)) for _ in range(3))
