@@ -272,6 +272,7 @@ Graph build_graph(int accumulate) {
       for (int v = 0; v < N; ++v) {
         if (v == w || v == u || g.nodes[v].vec.sp != W.vec.sp) continue;
         for (int c = 0; c < ncoef; ++c) {
+          if (c == SWMM_COEF_ONE && v < u) continue;  // u + v once
           Vec cv;
           if (!scaled(g.nodes[v].vec, c, &cv)) continue;
           if (add(g.nodes[u].vec, cv) == W.vec) W.der.push_back({D_ADD, (int8_t)u, (int8_t)v, (int8_t)c, -1, 1, 0});
