@@ -162,10 +162,13 @@ int swmm_set_schedule(swmm_t h, const swmm_search_spec *spec, const swmm_search_
 /* Plan a call of schedule `rows` without a handle or a device: what
  * swmm_workspace_elems reports for it (paper_elems: the schedule's own
  * temporaries over the levels that keep them; plan_elems: the planner's
- * peak).  opts->sched must be SWMM_CUSTOM. */
+ * peak), and the time the autotuner's model gives the plan (model_us, from
+ * the plan's leaf flops, block-addition and staging bytes and launches; a
+ * ranking aid, not a measurement).  opts->sched must be SWMM_CUSTOM.  Any
+ * output pointer may be NULL. */
 int swmm_schedule_workspace(const swmm_search_spec *spec, const swmm_search_row *rows, int32_t nrows, int64_t m,
                             int64_t k, int64_t n, const swmm_opts *opts, int64_t *paper_elems,
-                            int64_t *plan_elems);
+                            int64_t *plan_elems, double *model_us);
 
 /* The rows of the paper's table `sched` (SWMM_T1_DHSS ... SWMM_T9_ACC,
  * SWMM_T4M_OVL) as the library runs them, in the form swmm_schedule_check

@@ -760,6 +760,27 @@ double model_us(const Plan &P) {
   return flops / rate + bytes / 5.5e6 + launches * 2.5;
 }
 
+// The dry run of a call with no operands: the entry point the schedule's
+// contract implies, unit scalars.
+int plan_only(swmm_t h, int64_t m, int64_t k, int64_t n, const swmm_opts *opts, Plan &P) {
+  if (!opts) return fail(h, SWMM_EINVAL, "opts is NULL");
+  const int s = opts->sched;
+  bool acc_inplace = s == SWMM_T6_ACLR || s == SWMM_T7_ACCR || s == SWMM_T8_ACR;
+  int entry = 0;
+  if (s == SWMM_T2_HLJJTT || s == SWMM_T9_ACC || s == SWMM_TBLOCK) entry = 1;
+  if (s == SWMM_T3_IP || s == SWMM_T4_OVL || s == SWMM_T4M_OVL || s == SWMM_T5_OVR || s == SWMM_IP0VMM ||
+      acc_inplace)
+    entry = 2;
+  if (s == SWMM_CUSTOM && h->has_custom) {
+    const bool ro = h->custom.preserve == 0xffu;
+    entry = ro ? (h->custom.accumulate ? 1 : 0) : 2;
+    acc_inplace = !ro && h->custom.accumulate;
+  }
+  static const uint32_t one = 1;
+  Req q{entry, m, k, n, nullptr, nullptr, nullptr, k, n, n, &one, acc_inplace || entry == 1 ? &one : nullptr};
+  return make_plan(h, q, opts, false, P);
+}
+
 // The handle's own schedule: checked in the pebble game, lowered to rows.
 int set_schedule(swmm_t h, const swmm_search_spec *spec, const swmm_search_row *rows, int32_t nrows) {
   if (!spec || !rows) return fail(h, SWMM_EINVAL, "spec or rows is NULL");
@@ -909,23 +930,8 @@ int swmm_workspace_elems(swmm_t h, int64_t m, int64_t k, int64_t n, const swmm_o
   swmm_ctx planner;  // planning needs no device: a NULL handle is accepted
   if (!h) h = &planner;
   h->last_error.clear();
-  if (!opts) return fail(h, SWMM_EINVAL, "opts is NULL");
-  const int s = opts->sched;
-  bool acc_inplace = s == SWMM_T6_ACLR || s == SWMM_T7_ACCR || s == SWMM_T8_ACR;
-  int entry = 0;
-  if (s == SWMM_T2_HLJJTT || s == SWMM_T9_ACC || s == SWMM_TBLOCK) entry = 1;
-  if (s == SWMM_T3_IP || s == SWMM_T4_OVL || s == SWMM_T4M_OVL || s == SWMM_T5_OVR || s == SWMM_IP0VMM ||
-      acc_inplace)
-    entry = 2;
-  if (s == SWMM_CUSTOM && h->has_custom) {
-    const bool ro = h->custom.preserve == 0xffu;
-    entry = ro ? (h->custom.accumulate ? 1 : 0) : 2;
-    acc_inplace = !ro && h->custom.accumulate;
-  }
-  static const uint32_t one = 1;
-  Req q{entry, m, k, n, nullptr, nullptr, nullptr, k, n, n, &one, acc_inplace || entry == 1 ? &one : nullptr};
   Plan P;
-  int rc = make_plan(h, q, opts, false, P);
+  const int rc = plan_only(h, m, k, n, opts, P);
   if (rc != SWMM_OK) return rc;
   if (paper_out) *paper_out = P.paper;
   if (plan_out) *plan_out = P.x.tmp_peak_elems;
@@ -1170,12 +1176,19 @@ int swmm_set_schedule(swmm_t h, const swmm_search_spec *spec, const swmm_search_
 }
 
 int swmm_schedule_workspace(const swmm_search_spec *spec, const swmm_search_row *rows, int32_t nrows, int64_t m,
-                            int64_t k, int64_t n, const swmm_opts *opts, int64_t *paper_elems, int64_t *plan_elems) {
+                            int64_t k, int64_t n, const swmm_opts *opts, int64_t *paper_elems, int64_t *plan_elems,
+                            double *model_us_out) {
   swmm_ctx planner;  // no device
-  const int rc = set_schedule(&planner, spec, rows, nrows);
+  int rc = set_schedule(&planner, spec, rows, nrows);
   if (rc != SWMM_OK) return rc;
   if (!opts || opts->sched != SWMM_CUSTOM) return SWMM_EINVAL;
-  return swmm_workspace_elems(&planner, m, k, n, opts, paper_elems, plan_elems);
+  Plan P;
+  rc = plan_only(&planner, m, k, n, opts, P);
+  if (rc != SWMM_OK) return rc;
+  if (paper_elems) *paper_elems = P.paper;
+  if (plan_elems) *plan_elems = P.x.tmp_peak_elems;
+  if (model_us_out) *model_us_out = model_us(P);
+  return SWMM_OK;
 }
 
 }  // extern "C"

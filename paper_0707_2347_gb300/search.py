@@ -76,7 +76,8 @@ def _lib():
         i64p = ctypes.POINTER(ctypes.c_int64)
         lib.swmm_schedule_workspace.argtypes = [ctypes.POINTER(_Spec), ctypes.POINTER(_Row), ctypes.c_int32,
                                                 ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
-                                                ctypes.POINTER(swmm._Opts), i64p, i64p]
+                                                ctypes.POINTER(swmm._Opts), i64p, i64p,
+                                                ctypes.POINTER(ctypes.c_double)]
         lib.swmm_table_rows.argtypes = [ctypes.c_int32, ctypes.POINTER(_Row), ctypes.c_int32,
                                         ctypes.POINTER(ctypes.c_int32)]
         lib._search_typed = True
@@ -151,18 +152,46 @@ def set_schedule(handle, rows, *, accumulate=False, preserve=(), temps=0, kinds=
         raise swmm.SwmmError(rc, lib.swmm_last_error(handle.h).decode())
 
 
+def _plan(rows, m, k, n, opts, spec):
+    lib = _lib()
+    paper, plan, us = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_double()
+    rc = lib.swmm_schedule_workspace(ctypes.byref(spec), _crows(rows), len(rows), m, k, n, ctypes.byref(opts.c()),
+                                     ctypes.byref(paper), ctypes.byref(plan), ctypes.byref(us))
+    if rc != swmm.OK:
+        raise swmm.SwmmError(rc, "schedule planning failed")
+    return paper.value, plan.value, us.value
+
+
 def schedule_workspace(rows, m, k, n, opts, *, accumulate=False, preserve=(), temps=0, kinds=(), max_copies=0,
                        recompute=False):
     """(schedule's own temporaries, planner peak) in elements for a call of
     `rows` on m x k x n with `opts` (sched must be swmm.CUSTOM); no device."""
-    lib = _lib()
     spec = _spec(accumulate, preserve, temps, kinds, -1, max_copies, recompute, MAX_ROWS, 0)
-    paper, plan = ctypes.c_int64(), ctypes.c_int64()
-    rc = lib.swmm_schedule_workspace(ctypes.byref(spec), _crows(rows), len(rows), m, k, n, ctypes.byref(opts.c()),
-                                     ctypes.byref(paper), ctypes.byref(plan))
-    if rc != swmm.OK:
-        raise swmm.SwmmError(rc, "schedule workspace failed")
-    return paper.value, plan.value
+    return _plan(rows, m, k, n, opts, spec)[:2]
+
+
+def schedule_model_us(rows, m, k, n, opts, *, accumulate=False, preserve=(), temps=0, kinds=(), max_copies=0,
+                      recompute=False):
+    """The autotuner's modelled time (microseconds) for a call of `rows`."""
+    spec = _spec(accumulate, preserve, temps, kinds, -1, max_copies, recompute, MAX_ROWS, 0)
+    return _plan(rows, m, k, n, opts, spec)[2]
+
+
+def frontier(candidates, m, k, n, opts):
+    """Memory-speed frontier of one-level schedules for an m x k x n call.
+
+    candidates: {name: (rows, spec dict as set_schedule takes it)}.  Returns
+    [(name, planned temporaries, modelled us)] of the candidates no other
+    one beats on both, fewest temporaries first."""
+    pts = []
+    for name, (rows, spec) in candidates.items():
+        _, plan, us = _plan(rows, m, k, n, opts, _spec(spec.get("accumulate", False), spec.get("preserve", ()),
+                                                          spec.get("temps", 0), spec.get("kinds", ()), -1,
+                                                          spec.get("max_copies", 0), spec.get("recompute", False),
+                                                          MAX_ROWS, 0))
+        pts.append((name, plan, us))
+    keep = [a for a in pts if not any(b[1] <= a[1] and b[2] < a[2] or b[1] < a[1] and b[2] <= a[2] for b in pts)]
+    return sorted(keep, key=lambda t: (t[1], t[2]))
 
 
 def table_rows(sched: int) -> list:

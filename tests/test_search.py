@@ -377,3 +377,31 @@ def test_library_tables_match_the_oracle_transcription(Z, kind):
     assert len(lib.rows) == len(ora.rows)
     for i, (a, b) in enumerate(zip(lib.rows, ora.rows)):
         assert (a.op, a.dst, a.value, a.kind, a.accumulate) == (b.op, b.dst, b.value, b.kind, b.accumulate), (kind, i)
+
+
+def test_model_ranks_measured_pairs_and_frontier(Z):
+    """The autotuner's cost model, applied to one-level schedules, ranks the
+    two pairs measured on a GB300 the way the measurement did (Table 9 over
+    Table 2 ahead of Table 9 at 8192^2 depth 3: 4.580 vs 4.644 ms; the
+    searched 12-addition schedule ahead of Table 1 at 16384^2 depth 3:
+    23.80 vs 24.70 ms), and the memory-speed frontier keeps both ends."""
+    search, swmm = Z
+    keep = A_ALL + B_ALL
+    o = swmm.Opts(mode=swmm.MODP, p=65521, sched=swmm.CUSTOM, depth=3)
+    t9 = search.table_rows(swmm.T9_ACC)
+    mix = search.table_rows(swmm.T9_ACC)
+    for r in mix:
+        if r.op == search.MUL and r.kind in (swmm.T9_ACC, swmm.T6_ACLR, swmm.T7_ACCR):
+            r.kind = swmm.T2_HLJJTT
+    sp9 = dict(accumulate=True, preserve=keep, temps=2, kinds=(1, 6, 7, 9), recompute=True)
+    spm = dict(accumulate=True, preserve=keep, temps=2, kinds=(1, 2), recompute=True)
+    n = 8192
+    assert search.schedule_model_us(mix, n, n, n, o, **spm) < search.schedule_model_us(t9, n, n, n, o, **sp9)
+    front = search.frontier({"T9": (t9, sp9), "T9/T2": (mix, spm)}, n, n, n, o)
+    assert [f[0] for f in front] == ["T9", "T9/T2"] and front[0][1] < front[1][1]
+    t1 = search.table_rows(swmm.T1_DHSS)
+    s12 = search.schedule_search(preserve=keep, temps=2, kinds=(search.SELF, swmm.T2_HLJJTT), max_adds=12).rows
+    n = 16384
+    m1 = search.schedule_model_us(t1, n, n, n, o, preserve=keep, temps=2, kinds=(1,))
+    m12 = search.schedule_model_us(s12, n, n, n, o, preserve=keep, temps=2, kinds=(search.SELF, 2))
+    assert m12 < m1
