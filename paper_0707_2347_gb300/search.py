@@ -225,3 +225,79 @@ def schedule_check(rows, *, accumulate=False, preserve=(), temps=0, kinds=(), ma
     out = _rows_out(crows, legal, accumulate)
     return Outcome(bool(res.found), False, 0, res.written, res.temps_used, out,
                    -1 if legal == n else legal)
+
+
+# contract of each printed table: (accumulates, blocks it keeps, temporaries)
+_A, _B = ("A11", "A12", "A21", "A22"), ("B11", "B12", "B21", "B22")
+TABLE_CONTRACT = {
+    swmm.T1_DHSS: (False, _A + _B, 2), swmm.T2_HLJJTT: (True, _A + _B, 3), swmm.T3_IP: (False, (), 0),
+    swmm.T4_OVL: (False, _B, 1), swmm.T4M_OVL: (False, _B + ("A12", "A22"), 1), swmm.T5_OVR: (False, _A, 1),
+    swmm.T6_ACLR: (True, (), 2), swmm.T7_ACCR: (True, _A, 2), swmm.T8_ACR: (True, _A + ("B11", "B22"), 2),
+    swmm.T9_ACC: (True, _A + _B, 2),
+}
+
+
+def tune(m, k, n, opts, *, accumulate=False, preserve=(), max_elems=None, search_states=1 << 18):
+    """Pick a one-level schedule for an m x k x n call under a contract
+    (accumulate or not, blocks of A and B to keep) and a memory cap.
+
+    Candidates: every printed table whose contract covers the request; the
+    same table with Table 2 for its accumulating calls and with Table 1 for
+    its plain calls; and, for C <- AB, the schedule the pebble-game search
+    returns with the fewest block additions for each number of temporaries
+    the tables use (each search bounded by `search_states`).  Each is planned
+    (temporaries) and costed by the autotuner's model.  Returns (name, rows,
+    spec, planned elements, modelled us) of the fastest candidate within
+    `max_elems`, and the memory-speed frontier of all of them."""
+    keep = set(preserve)
+    cands = {}
+    for code, (acc, tkeep, temps) in TABLE_CONTRACT.items():
+        if acc != bool(accumulate) or not keep <= set(tkeep):
+            continue
+        base = table_rows(code)
+        kinds0 = {r.kind for r in base if r.op == MUL}
+        variants = {swmm.SCHED_NAMES[code]: base}
+        for repl, tag in (({swmm.T9_ACC: swmm.T2_HLJJTT, swmm.T6_ACLR: swmm.T2_HLJJTT,
+                            swmm.T7_ACCR: swmm.T2_HLJJTT, swmm.T8_ACR: swmm.T2_HLJJTT}, "/T2"),
+                          ({swmm.T3_IP: swmm.T1_DHSS, swmm.T4_OVL: swmm.T1_DHSS, swmm.T5_OVR: swmm.T1_DHSS,
+                            swmm.T4M_OVL: swmm.T1_DHSS}, "/T1")):
+            if not kinds0 & set(repl):
+                continue
+            rows = [Row(**r.__dict__) for r in base]
+            for r in rows:
+                if r.op == MUL:
+                    r.kind = repl.get(r.kind, r.kind)
+            variants[swmm.SCHED_NAMES[code] + tag] = rows
+        for name, rows in variants.items():
+            spec = dict(accumulate=acc, preserve=tuple(tkeep), temps=temps,
+                        kinds=tuple(sorted({r.kind for r in rows if r.op == MUL})),
+                        max_copies=sum(r.op == COPY for r in rows), recompute=code == swmm.T9_ACC)
+            if schedule_check(rows, **spec).found:
+                cands[name] = (rows, spec)
+    # searched schedules for C <- AB (the accumulating game is too large to
+    # search within a tuning call): fewest additions per table memory
+    for temps in sorted({sp["temps"] for _, sp in cands.values()}) if not accumulate else ():
+        kinds = (SELF, swmm.T2_HLJJTT) if len(keep) == 8 else (SELF, swmm.T3_IP)
+        best = None
+        for adds in range(15, 10, -1):
+            o = schedule_search(preserve=tuple(keep), temps=temps, kinds=kinds, max_adds=adds, max_rows=30,
+                                max_states=search_states)
+            if not o.found:
+                break
+            best = o
+        if best is not None:
+            cands[f"searched t{temps}"] = (best.rows, dict(accumulate=False, preserve=tuple(keep), temps=temps,
+                                                           kinds=kinds))
+    scored = []
+    for name, (rows, spec) in cands.items():
+        _, plan, us = _plan(rows, m, k, n, opts, _spec(spec["accumulate"], spec["preserve"], spec["temps"],
+                                                        spec["kinds"], -1, spec.get("max_copies", 0),
+                                                        spec.get("recompute", False), MAX_ROWS, 0))
+        scored.append((name, plan, us))
+    ok = [t for t in scored if max_elems is None or t[1] <= max_elems]
+    if not ok:
+        raise ValueError("no candidate schedule fits the memory cap")
+    name, plan, us = min(ok, key=lambda t: (t[2], t[1]))
+    front = [a for a in scored if not any(b[1] <= a[1] and b[2] < a[2] or b[1] < a[1] and b[2] <= a[2]
+                                          for b in scored)]
+    return (name, cands[name][0], cands[name][1], plan, us), sorted(front, key=lambda t: (t[1], t[2]))
