@@ -95,7 +95,8 @@ typedef struct {
                            value once.  Values of C are formed once. */
   int32_t max_rows;     /* longest schedule searched, <= SWMM_SEARCH_MAX_ROWS */
   int32_t max_adds;     /* at most this many block additions (each one pass
-                           over HBM at an upper level); -1: any */
+                           over HBM at an upper level), <= 255; -1: any
+                           (0 allows none) */
   int64_t max_states;   /* give up after visiting this many states (<= 0:
                            2^26) */
 } swmm_search_spec;
