@@ -85,6 +85,12 @@ WORKLOADS = {
                                        m=16384, k=16384, n=16384, mode=MODP, p=65521, sched=CUSTOM, depth=3,
                                        entry="mul", search=dict(preserve="AB", temps=2, kinds=("SELF", T2),
                                                                 max_adds=12)),
+    # Table 9's contract with 16 block additions instead of 17: a schedule the
+    # pebble-game search found, shipped in schedules_found.py
+    "searched16_8192_p65521_d3": dict(desc="C<-AB+C over Z/65521, 8192^2, searched read-only schedule with two "
+                                           "temporaries and 16 block additions (Table 9: 17), depth 3",
+                                      m=8192, k=8192, n=8192, mode=MODP, p=65521, sched=CUSTOM, depth=3,
+                                      entry="muladd", found="acc16"),
     # a mixed schedule: Table 9 at the top level, Table 2 (14 block additions
     # instead of 17, one more temporary) for its accumulating calls below
     "t9_over_t2_8192_p65521": dict(desc="C<-AB+C over Z/65521, 8192^2, Table 9 rows at every Table 9 level with "
@@ -427,6 +433,12 @@ def main():
         Q.set_schedule(h, rows, accumulate=True, preserve=("A11", "A12", "A21", "A22", "B11", "B12", "B21", "B22"),
                        temps=2, kinds=kinds, recompute=True)
         searched = {"table": S.SCHED_NAMES[w["table"]], "kinds": [S.SCHED_NAMES[k] for k in kinds]}
+    elif w["sched"] == CUSTOM and "found" in w:
+        from paper_0707_2347_gb300 import schedules_found as F
+        from paper_0707_2347_gb300 import search as Q
+        rows = F.rows(w["found"])
+        Q.set_schedule(h, rows, **F.spec(w["found"]))
+        searched = {"found": w["found"], "rows": len(rows), "adds": sum(r.op == Q.ADD for r in rows)}
     elif w["sched"] == CUSTOM:
         # the schedule the pebble-game search returns for this contract (host)
         from paper_0707_2347_gb300 import search as Q

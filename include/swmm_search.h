@@ -99,6 +99,8 @@ typedef struct {
                            (0 allows none) */
   int64_t max_states;   /* give up after visiting this many states (<= 0:
                            2^26) */
+  uint64_t exclude;     /* bit v: candidate value v (swmm_search_node_name)
+                           is never formed, to search a smaller graph */
 } swmm_search_spec;
 
 #define SWMM_SEARCH_MAX_ROWS 64

@@ -438,6 +438,7 @@ class Search {
   }
   // a product is used once; without `recompute` a value is computed once
   bool can_compute(const State &s, const Deriv &d, int w) const {
+    if (sp_.exclude >> w & 1) return false;
     if (d.type == D_ADD) return !(s.done >> w & 1) || (sp_.recompute && g_.nodes[w].vec.sp != SP_C);
     return !(s.prod >> d.prod & 1);
   }

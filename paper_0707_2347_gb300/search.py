@@ -25,7 +25,7 @@ class _Spec(ctypes.Structure):
     _fields_ = [("accumulate", ctypes.c_int32), ("preserve", ctypes.c_uint32), ("temps", ctypes.c_int32),
                 ("kinds", ctypes.c_uint32), ("max_written", ctypes.c_int32), ("max_copies", ctypes.c_int32),
                 ("recompute", ctypes.c_int32), ("max_rows", ctypes.c_int32), ("max_adds", ctypes.c_int32),
-                ("max_states", ctypes.c_int64)]
+                ("max_states", ctypes.c_int64), ("exclude", ctypes.c_uint64)]
 
 
 class _Row(ctypes.Structure):
@@ -84,7 +84,8 @@ def _lib():
     return lib
 
 
-def _spec(accumulate, preserve, temps, kinds, max_written, max_copies, recompute, max_rows, max_states, max_adds=-1):
+def _spec(accumulate, preserve, temps, kinds, max_written, max_copies, recompute, max_rows, max_states, max_adds=-1,
+          exclude=()):
     pm = 0
     for b in preserve:
         i = LOCS.index(b)
@@ -94,8 +95,12 @@ def _spec(accumulate, preserve, temps, kinds, max_written, max_copies, recompute
     km = 0
     for k in kinds:
         km |= 1 << int(k)
+    names = node_names(accumulate) if exclude else []
+    em = 0
+    for v in exclude:
+        em |= 1 << names.index(v)
     return _Spec(int(bool(accumulate)), pm, temps, km, max_written, max_copies, int(bool(recompute)), max_rows,
-                 max_adds, max_states)
+                 max_adds, max_states, em)
 
 
 def node_names(accumulate: bool) -> list:
@@ -115,14 +120,15 @@ def _rows_out(crows, n, accumulate):
 
 
 def schedule_search(*, accumulate=False, preserve=(), temps=0, kinds=(), max_written=-1, max_copies=0,
-                    recompute=False, max_rows=40, max_states=0, max_adds=-1) -> Outcome:
+                    recompute=False, max_rows=40, max_states=0, max_adds=-1, exclude=()) -> Outcome:
     """Search for one level's schedule: C <- alpha AB (+ beta C when
     `accumulate`), keeping the blocks named in `preserve`, with `temps`
     temporaries, recursive products of the given `kinds`, at most
-    `max_adds` block additions."""
+    `max_adds` block additions, never forming the values named in
+    `exclude` (see node_names)."""
     lib = _lib()
     spec = _spec(accumulate, preserve, temps, kinds, max_written, max_copies, recompute, max_rows, max_states,
-                 max_adds)
+                 max_adds, exclude)
     rows = (_Row * MAX_ROWS)()
     res = _Result()
     rc = lib.swmm_schedule_search(ctypes.byref(spec), rows, MAX_ROWS, ctypes.byref(res))

@@ -111,3 +111,19 @@ def test_custom_entry_point_must_match_contract(handle):
         handle.mul(dev(A), dev(B), dev(C), o)  # it overwrites A: only swmm_mul_inplace
     with pytest.raises(S.SwmmError):  # not square
         handle.mul_inplace(dev(A[:, :128]), dev(B[:128, :128]), dev(C[:, :128]), o)
+
+
+@pytest.mark.parametrize("n,depth,flags", [(512, 2, 0), (512, 2, S.FLAG_UNFUSED), (1024, 3, S.FLAG_GRAPH)])
+def test_shipped_table9_class_schedule_on_gpu(handle, n, depth, flags):
+    """The shipped 16-addition schedule for Table 9's contract, bit-exact."""
+    from paper_0707_2347_gb300 import schedules_found as F
+    Q.set_schedule(handle, F.rows("acc16"), **F.spec("acc16"))
+    p, alpha, beta = 65521, 3, 5
+    A, B, C = modp_inputs(n, n, n, p, tag=34)
+    dA, dB, dC = dev(A), dev(B), dev(C)
+    handle.muladd(alpha, dA, dB, beta, dC, S.Opts(mode=S.MODP, p=p, sched=S.CUSTOM, depth=depth, flags=flags))
+    handle.sync()
+    out = host(dC)
+    idx = np.arange(n) if n <= 512 else np.array([0, 1, n // 2 - 1, n // 2, n - 2, n - 1])
+    assert np.array_equal(out[idx], classical.rows_muladd_modp(idx, alpha, A, B, beta, C, p))
+    assert np.array_equal(host(dA), A) and np.array_equal(host(dB), B)
