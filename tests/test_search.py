@@ -445,3 +445,20 @@ def test_shipped_table9_class_schedule(Z, monkeypatch):
     search_kw = dict(F.FOUND["acc16"]["search"], max_adds=15)
     o = search.schedule_search(**spec, **search_kw)
     assert not o.found and o.exhausted
+
+
+def test_table2_additions_least_over_its_values(Z):
+    """Table 2 (read-only C <- alpha AB + beta C, three temporaries, read-only
+    calls) spends 14 block additions; over its own intermediate values 13
+    are out of reach, and the search finds a 14-addition schedule."""
+    search, swmm = Z
+    names = search.node_names(True)
+    own = {"P5+bC22", "P5+bC12", "P1+bC11", "P3+P5+bC12", "P4-bC21"}
+    ex = tuple(n for n in names if ("b" in n or n in ("Z1", "Z2", "Z3")) and n not in own and not n.startswith("U"))
+    kw = dict(accumulate=True, preserve=A_ALL + B_ALL, temps=3, kinds=(swmm.T1_DHSS, search.SELF), max_rows=26,
+              exclude=ex)
+    assert sum(r.op == search.ADD for r in search.table_rows(swmm.T2_HLJJTT)) == 14
+    o = search.schedule_search(max_adds=13, **kw)
+    assert not o.found and o.exhausted
+    o = search.schedule_search(max_adds=14, **kw)
+    assert o.found and sum(r.op == search.ADD for r in o.rows) == 14
