@@ -462,3 +462,17 @@ def test_table2_additions_least_over_its_values(Z):
     assert not o.found and o.exhausted
     o = search.schedule_search(max_adds=14, **kw)
     assert o.found and sum(r.op == search.ADD for r in o.rows) == 14
+
+
+def test_in_place_additions_with_accumulating_calls(Z, monkeypatch):
+    """C <- AB overwriting A and B with no temporary at this level: letting
+    products accumulate through Table 6 (AcLR) calls brings Table 3's 15
+    block additions down to 11, and 10 are out of reach.  (The AcLR calls
+    then hold Table 6's temporaries one level down.)"""
+    search, swmm = Z
+    kinds = (swmm.T3_IP, swmm.T6_ACLR)
+    o = search.schedule_search(temps=0, kinds=kinds, max_adds=10, max_rows=30)
+    assert not o.found and o.exhausted
+    o = search.schedule_search(temps=0, kinds=kinds, max_adds=11, max_rows=30)
+    assert o.found and sum(r.op == search.ADD for r in o.rows) == 11
+    run_found(Z, monkeypatch, o.rows, False, ())
