@@ -456,7 +456,11 @@ class Search {
       const int w = __builtin_ctzll(todo);
       todo &= todo - 1;
       seen |= 1ull << w;
-      if (g_.nodes[w].input || !to_produce(s, pres, w)) continue;
+      // a present value is expanded too when it may be formed again later
+      // (an operand sum under `recompute`): what it is formed from stays
+      if (g_.nodes[w].input ||
+          (!to_produce(s, pres, w) && !(sp_.recompute && g_.nodes[w].vec.sp != SP_C)))
+        continue;
       for (const Deriv &d : g_.nodes[w].der) {
         if (!can_compute(s, d, w)) continue;
         const uint64_t r = d.rd;

@@ -429,8 +429,10 @@ def test_tune_picks_within_memory_cap(Z):
 def test_shipped_table9_class_schedule(Z, monkeypatch):
     """The shipped schedule for Table 9's contract (read-only C <- alpha AB +
     beta C, two temporaries) is a legal play with 16 additions against
-    Table 9's 17, runs in the oracle, is what the stored search finds again,
-    and 15 additions are out of reach over Table 9's intermediate values."""
+    Table 9's 17, runs in the oracle, and 15 additions are out of reach over
+    Table 9's intermediate values (the search spec that found it; finding it
+    again takes as long as this proof, so schedules_found.regenerate is not
+    run here)."""
     search, swmm = Z
     from paper_0707_2347_gb300 import schedules_found as F
     rows, spec = F.rows("acc16"), F.spec("acc16")
@@ -439,9 +441,6 @@ def test_shipped_table9_class_schedule(Z, monkeypatch):
     assert sum(r.op == search.ADD for r in rows) == 16
     assert sum(r.op == search.ADD for r in search.table_rows(swmm.T9_ACC)) == 17
     run_found(Z, monkeypatch, chk.rows, True, spec["preserve"])  # rows with their value names
-    again = F.regenerate("acc16")
-    assert [(r.op, r.dst, r.s1, r.s2, r.coef, r.kind) for r in again] == \
-        [(r.op, r.dst, r.s1, r.s2, r.coef, r.kind) for r in rows]
     search_kw = dict(F.FOUND["acc16"]["search"], max_adds=15)
     o = search.schedule_search(**spec, **search_kw)
     assert not o.found and o.exhausted
