@@ -15,6 +15,11 @@ checked against the search that produced it.
   ab12   C <- alpha AB, A and B read-only, two temporaries (Table 1's
          contract), 12 block additions against Table 1's 15: three products
          are Table 2 calls that accumulate into their destination.
+  aclr14 C <- alpha AB + beta C overwriting A and B, two temporaries (Table
+         6's contract), 14 block additions against Table 6's 17.
+  accr14 C <- alpha AB + beta C overwriting B, two temporaries (Table 7's
+         contract), 14 block additions against Table 7's 17.
+The last three are found at run time (a few seconds at most).
 """
 from __future__ import annotations
 
@@ -61,7 +66,17 @@ FOUND = {
     "ab12": dict(
         spec=dict(accumulate=False, preserve=_AB, temps=2, kinds=(Q.SELF, swmm.T2_HLJJTT)),
         search=dict(max_adds=12),
-        rows=None,  # found at run time: the search takes well under a second
+        rows=None,
+    ),
+    "aclr14": dict(
+        spec=dict(accumulate=True, preserve=(), temps=2, kinds=(swmm.T3_IP, Q.SELF)),
+        search=dict(max_adds=14, max_rows=30),
+        rows=None,
+    ),
+    "accr14": dict(
+        spec=dict(accumulate=True, preserve=_AB[:4], temps=2, kinds=(swmm.T3_IP, swmm.T5_OVR, Q.SELF)),
+        search=dict(max_adds=14, max_rows=30),
+        rows=None,
     ),
 }
 

@@ -475,3 +475,19 @@ def test_in_place_additions_with_accumulating_calls(Z, monkeypatch):
     o = search.schedule_search(temps=0, kinds=kinds, max_adds=11, max_rows=30)
     assert o.found and sum(r.op == search.ADD for r in o.rows) == 11
     run_found(Z, monkeypatch, o.rows, False, ())
+
+
+@pytest.mark.parametrize("name,table", [("ab12", 1), ("aclr14", 6), ("accr14", 7)])
+def test_shipped_schedules_with_fewer_additions(Z, monkeypatch, name, table):
+    """The shipped searched schedules keep their table's contract and memory
+    with fewer block additions (Table 1: 15 -> 12; Tables 6 and 7: 17 -> 14),
+    and run in the oracle."""
+    search, _ = Z
+    from paper_0707_2347_gb300 import schedules_found as F
+    spec = F.spec(name)
+    chk = search.schedule_check(F.rows(name), **spec)
+    assert chk.found and chk.temps_used == spec["temps"]
+    adds = sum(r.op == search.ADD for r in chk.rows)
+    assert adds == F.FOUND[name]["search"]["max_adds"]
+    assert adds + 3 == sum(r.op == search.ADD for r in search.table_rows(table))
+    run_found(Z, monkeypatch, chk.rows, spec["accumulate"], spec["preserve"])
