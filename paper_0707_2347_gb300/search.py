@@ -249,7 +249,9 @@ def tune(m, k, n, opts, *, accumulate=False, preserve=(), max_elems=None, search
 
     Candidates: every printed table whose contract covers the request; the
     same table with Table 2 for its accumulating calls and with Table 1 for
-    its plain calls; and, for C <- AB, the schedule the pebble-game search
+    its plain calls; the searched schedules the library ships
+    (schedules_found.py) whose contract covers it; and, for C <- AB, the
+    schedule the pebble-game search
     returns with the fewest block additions for each number of temporaries
     the tables use (each search bounded by `search_states`).  Each is planned
     (temporaries) and costed by the autotuner's model.  Returns (name, rows,
@@ -280,6 +282,12 @@ def tune(m, k, n, opts, *, accumulate=False, preserve=(), max_elems=None, search
                         max_copies=sum(r.op == COPY for r in rows), recompute=code == swmm.T9_ACC)
             if schedule_check(rows, **spec).found:
                 cands[name] = (rows, spec)
+    # the searched schedules the library ships (schedules_found.py)
+    from . import schedules_found as found
+    for fname, f in found.FOUND.items():
+        fs = f["spec"]
+        if fs["accumulate"] == bool(accumulate) and keep <= set(fs["preserve"]):
+            cands["found:" + fname] = (found.rows(fname), dict(fs))
     # searched schedules for C <- AB (the accumulating game is too large to
     # search within a tuning call): fewest additions per table memory
     for temps in sorted({sp["temps"] for _, sp in cands.values()}) if not accumulate else ():
