@@ -83,8 +83,7 @@ WORKLOADS = {
     "searched12_16384_p65521_d3": dict(desc="C<-AB over Z/65521, 16384^2, searched read-only schedule with two "
                                             "temporaries and 12 block additions (Table 2 calls accumulate), depth 3",
                                        m=16384, k=16384, n=16384, mode=MODP, p=65521, sched=CUSTOM, depth=3,
-                                       entry="mul", search=dict(preserve="AB", temps=2, kinds=("SELF", T2),
-                                                                max_adds=12)),
+                                       entry="mul", found="ab12"),
     # Table 9's contract with 16 block additions instead of 17: a schedule the
     # pebble-game search found, shipped in schedules_found.py
     "searched16_8192_p65521_d3": dict(desc="C<-AB+C over Z/65521, 8192^2, searched read-only schedule with two "
@@ -439,18 +438,6 @@ def main():
         rows = F.rows(w["found"])
         Q.set_schedule(h, rows, **F.spec(w["found"]))
         searched = {"found": w["found"], "rows": len(rows), "adds": sum(r.op == Q.ADD for r in rows)}
-    elif w["sched"] == CUSTOM:
-        # the schedule the pebble-game search returns for this contract (host)
-        from paper_0707_2347_gb300 import search as Q
-        sp = w["search"]
-        spec = dict(preserve=("A11", "A12", "A21", "A22", "B11", "B12", "B21", "B22") if sp["preserve"] == "AB"
-                    else (), temps=sp["temps"], kinds=tuple(Q.SELF if x == "SELF" else x for x in sp["kinds"]))
-        o = Q.schedule_search(max_adds=sp["max_adds"], **spec)
-        if not o.found:
-            raise RuntimeError("schedule search found nothing for " + args.workload)
-        Q.set_schedule(h, o.rows, **spec)
-        searched = {"rows": len(o.rows), "adds": sum(r.op == Q.ADD for r in o.rows), "temps": o.temps_used,
-                    "schedule": [f"{r.value}->{r.dst}" for r in o.rows]}
     m, k, n = w["m"], w["k"], w["n"]
     A, B, C = make_inputs(w)
     dA, dB = torch.from_numpy(A).to(dev), torch.from_numpy(B).to(dev)
