@@ -11,8 +11,9 @@
  * overwrites fewer than four input blocks, and none overwrites only one of
  * A and B without a temporary.
  *
- * This entry point plays that game for one level of the recursion, square
- * blocks, with the locations the tables use: the quadrants A11 ... C22 of
+ * This entry point plays that game for one level of the recursion (square
+ * blocks unless the spec gives the operands' relative sizes), with the
+ * locations the tables use: the quadrants A11 ... C22 of
  * the caller's matrices and up to three temporaries X, Y, Z.  Values are
  * vectors over the operand blocks, the seven products P1 ... P7 and the
  * blocks of the input C; a row may compute any candidate value that is one
@@ -101,6 +102,11 @@ typedef struct {
                            2^26) */
   uint64_t exclude;     /* bit v: candidate value v (swmm_search_node_name)
                            is never formed, to search a smaller graph */
+  int32_t m, k, n;      /* relative sizes of the operands (A m x k, B k x n,
+                           C m x n; Section 5.3): a value goes only into a
+                           block it fits (temporaries hold any), the square
+                           tables (4-7, 9) are not called unless m = k = n,
+                           Table 3 only when k = n <= m.  0, 0, 0: square */
 } swmm_search_spec;
 
 #define SWMM_SEARCH_MAX_ROWS 64

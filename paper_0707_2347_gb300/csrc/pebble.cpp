@@ -309,6 +309,36 @@ const Contract kContracts[] = {
     {SWMM_T4M_OVL, false, 1},
 };
 
+// Block shapes (Section 5.3).  With relative operand sizes m x k (A), k x n
+// (B) and m x n (C), the blocks of A, B and C are halved alike, a value of
+// A, B or C has its matrix's block shape, and a value fits a block when
+// neither dimension is larger.  Temporaries hold any value.  Tables 4-7 and
+// 9 need m = k = n; Table 3 needs k = n <= m.
+struct Dims {
+  int m = 1, k = 1, n = 1;
+  bool square() const { return m == k && k == n; }
+};
+Dims dims_of(const swmm_search_spec &s) {
+  Dims d;
+  if (s.m > 0 && s.k > 0 && s.n > 0) d.m = s.m, d.k = s.k, d.n = s.n;
+  return d;
+}
+bool fits(const Dims &d, int space, int loc) {
+  if (loc >= SWMM_LOC_X) return true;
+  const int vr = space == SP_B ? d.k : d.m, vc = space == SP_A ? d.k : d.n;
+  const int lr = loc >= SWMM_LOC_B11 && loc < SWMM_LOC_C11 ? d.k : d.m;
+  const int lc = loc < SWMM_LOC_B11 ? d.k : d.n;
+  return vr <= lr && vc <= lc;
+}
+bool kind_allowed(const Dims &d, int kind) {
+  if (d.square() || kind == SWMM_SEARCH_SELF) return true;
+  switch (kind) {
+    case SWMM_T1_DHSS: case SWMM_T2_HLJJTT: case SWMM_T8_ACR: return true;
+    case SWMM_T3_IP: return d.k == d.n && d.n <= d.m;
+    default: return false;  // the square-only tables
+  }
+}
+
 // The schedule searched for overwrites an operand of its own recursive calls
 // where its spec lets it overwrite a block of that matrix.
 int self_clobber(const swmm_search_spec &s) {
@@ -390,8 +420,9 @@ class Search {
     N_ = (int)g.nodes.size();
     for (int b = 0; b < 8; ++b)
       if (s.preserve >> b & 1) preserved_ |= 1ull << home_of(b);
+    dims_ = dims_of(s);
     for (const Contract &c : kContracts)
-      if (s.kinds >> c.kind & 1) con_.push_back(c);
+      if ((s.kinds >> c.kind & 1) && kind_allowed(dims_, c.kind)) con_.push_back(c);
     if (s.kinds >> SWMM_SEARCH_SELF & 1) con_.push_back({SWMM_SEARCH_SELF, s.accumulate != 0, self_clobber(s)});
     all_clob_ = 3;
     for (const Contract &c : con_) all_clob_ &= c.clob;
@@ -619,8 +650,10 @@ class Search {
     if (!ok) path_.pop_back();
     return ok;
   }
+  // blocks interchangeable with the temporaries (only when all blocks have
+  // one shape)
   bool scratch(const State &s, int l) const {
-    return l >= 12 || (l < 8 && (s.written >> l & 1) && !(sp_.preserve >> l & 1));
+    return l >= 12 || (dims_.square() && l < 8 && (s.written >> l & 1) && !(sp_.preserve >> l & 1));
   }
   // Destinations worth trying: one free block of the scratch group stands
   // for all of them, and a block whose value could not be had again is
@@ -687,7 +720,7 @@ class Search {
         if ((d.rd & ~pres) != 0) continue;
         if (d.type == D_ADD) {
           for (int dst = 0; dst < nloc_; ++dst) {
-            if (!(dmask >> dst & 1) || s.loc[dst] == w) continue;
+            if (!(dmask >> dst & 1) || s.loc[dst] == w || !fits(dims_, g_.nodes[w].vec.sp, dst)) continue;
             // read an operand from dst when dst holds it (in place)
             const int lu = s.loc[dst] == d.u ? dst : first_loc(s, d.u);
             const int lv = s.loc[dst] == d.v ? dst : first_loc(s, d.v);
@@ -705,7 +738,7 @@ class Search {
         for (const Contract &c : con_) {
           if (c.acc != (d.type == D_ACC)) continue;
           for (int dst = 0; dst < nloc_; ++dst) {
-            if (!(dmask >> dst & 1)) continue;
+            if (!(dmask >> dst & 1) || !fits(dims_, SP_C, dst)) continue;
             if (d.type == D_ACC && s.loc[dst] != d.v) continue;
             // operand copies: branch over the copies a call overwrites
             for (int la = 0; la < nloc_; ++la) {
@@ -736,7 +769,7 @@ class Search {
         const int from = first_loc(s, x);
         for (int dst = 0; dst < nloc_; ++dst) {
           const int held = s.loc[dst];
-          if (!(dmask >> dst & 1) || held == x) continue;
+          if (!(dmask >> dst & 1) || held == x || !fits(dims_, g_.nodes[x].vec.sp, dst)) continue;
           if (held != kEmpty) continue;  // into a free block
           State n = s;
           n.loc[dst] = (int8_t)x;
@@ -757,6 +790,7 @@ class Search {
   const Graph &g_;
   int N_ = 0, nloc_ = 12;
   uint64_t preserved_ = 0;
+  Dims dims_;
   int all_clob_ = 0;  // operands every allowed call overwrites (bit 0 left, 1 right)
   std::vector<Contract> con_;
   Visited vis_;
@@ -770,6 +804,7 @@ class Search {
 int replay(const swmm_search_spec &sp, const Graph &g, swmm_search_row *rows, int nrows, bool *goal,
            uint32_t *written, uint32_t *temps) {
   const int nloc = 12 + sp.temps;
+  const Dims dm = dims_of(sp);
   int8_t loc[SWMM_NLOC];
   for (int l = 0; l < SWMM_NLOC; ++l) loc[l] = kEmpty;
   for (size_t i = 0; i < g.nodes.size(); ++i)
@@ -794,7 +829,7 @@ int replay(const swmm_search_spec &sp, const Graph &g, swmm_search_row *rows, in
     const bool s1ok = r.s1 >= 0 && r.s1 < nloc && loc[r.s1] != kEmpty;
     if (!s1ok) return i;
     if (r.op == SWMM_ROW_COPY) {
-      if (r.dst == r.s1 || copies >= sp.max_copies) return i;
+      if (r.dst == r.s1 || copies >= sp.max_copies || !fits(dm, g.nodes[loc[r.s1]].vec.sp, r.dst)) return i;
       ++copies;
       loc[r.dst] = loc[r.s1];
       r.node = loc[r.s1];
@@ -809,6 +844,7 @@ int replay(const swmm_search_spec &sp, const Graph &g, swmm_search_row *rows, in
       if (u.sp != v.sp || !scaled(v, r.coef, &cv)) return i;
       const int w = node_of(add(u, cv));
       if (w < 0 || g.nodes[w].input || ((done >> w & 1) && !(sp.recompute && g.nodes[w].vec.sp != SP_C))) return i;
+      if (!fits(dm, u.sp, r.dst)) return i;
       loc[r.dst] = (int8_t)w;
       done |= 1ull << w;
       r.node = w;
@@ -826,7 +862,7 @@ int replay(const swmm_search_spec &sp, const Graph &g, swmm_search_row *rows, in
       for (const Contract &k : kContracts)
         if (k.kind == r.kind) c = k;
     }
-    if (c.kind < 0 || c.acc != (r.accumulate != 0)) return i;
+    if (c.kind < 0 || c.acc != (r.accumulate != 0) || !kind_allowed(dm, c.kind) || !fits(dm, SP_C, r.dst)) return i;
     Vec pv;
     pv.sp = SP_C;
     pv.u[p] = (int8_t)r.sign;
@@ -861,7 +897,8 @@ int replay(const swmm_search_spec &sp, const Graph &g, swmm_search_row *rows, in
 bool spec_ok(const swmm_search_spec *spec) {
   if (!spec || (spec->accumulate != 0 && spec->accumulate != 1)) return false;
   if (spec->temps < 0 || spec->temps > 3 || spec->max_copies < 0 || spec->max_rows < 1 ||
-      spec->max_rows > SWMM_SEARCH_MAX_ROWS || (spec->preserve & ~0xffu) || spec->max_adds > 255)
+      spec->max_rows > SWMM_SEARCH_MAX_ROWS || (spec->preserve & ~0xffu) || spec->max_adds > 255 ||
+      spec->m < 0 || spec->k < 0 || spec->n < 0)
     return false;
   const uint32_t known = (1u << SWMM_T1_DHSS) | (1u << SWMM_T2_HLJJTT) | (1u << SWMM_T3_IP) | (1u << SWMM_T4_OVL) |
                          (1u << SWMM_T5_OVR) | (1u << SWMM_T6_ACLR) | (1u << SWMM_T7_ACCR) | (1u << SWMM_T8_ACR) |

@@ -25,7 +25,8 @@ class _Spec(ctypes.Structure):
     _fields_ = [("accumulate", ctypes.c_int32), ("preserve", ctypes.c_uint32), ("temps", ctypes.c_int32),
                 ("kinds", ctypes.c_uint32), ("max_written", ctypes.c_int32), ("max_copies", ctypes.c_int32),
                 ("recompute", ctypes.c_int32), ("max_rows", ctypes.c_int32), ("max_adds", ctypes.c_int32),
-                ("max_states", ctypes.c_int64), ("exclude", ctypes.c_uint64)]
+                ("max_states", ctypes.c_int64), ("exclude", ctypes.c_uint64), ("m", ctypes.c_int32),
+                ("k", ctypes.c_int32), ("n", ctypes.c_int32)]
 
 
 class _Row(ctypes.Structure):
@@ -85,7 +86,7 @@ def _lib():
 
 
 def _spec(accumulate, preserve, temps, kinds, max_written, max_copies, recompute, max_rows, max_states, max_adds=-1,
-          exclude=()):
+          exclude=(), shape=None):
     pm = 0
     for b in preserve:
         i = LOCS.index(b)
@@ -99,8 +100,9 @@ def _spec(accumulate, preserve, temps, kinds, max_written, max_copies, recompute
     em = 0
     for v in exclude:
         em |= 1 << names.index(v)
+    m, k, n = shape if shape else (0, 0, 0)
     return _Spec(int(bool(accumulate)), pm, temps, km, max_written, max_copies, int(bool(recompute)), max_rows,
-                 max_adds, max_states, em)
+                 max_adds, max_states, em, m, k, n)
 
 
 def node_names(accumulate: bool) -> list:
@@ -120,15 +122,16 @@ def _rows_out(crows, n, accumulate):
 
 
 def schedule_search(*, accumulate=False, preserve=(), temps=0, kinds=(), max_written=-1, max_copies=0,
-                    recompute=False, max_rows=40, max_states=0, max_adds=-1, exclude=()) -> Outcome:
+                    recompute=False, max_rows=40, max_states=0, max_adds=-1, exclude=(), shape=None) -> Outcome:
     """Search for one level's schedule: C <- alpha AB (+ beta C when
     `accumulate`), keeping the blocks named in `preserve`, with `temps`
     temporaries, recursive products of the given `kinds`, at most
     `max_adds` block additions, never forming the values named in
-    `exclude` (see node_names)."""
+    `exclude` (see node_names); `shape` = relative sizes (m, k, n) of the
+    operands, None for square blocks."""
     lib = _lib()
     spec = _spec(accumulate, preserve, temps, kinds, max_written, max_copies, recompute, max_rows, max_states,
-                 max_adds, exclude)
+                 max_adds, exclude, shape)
     rows = (_Row * MAX_ROWS)()
     res = _Result()
     rc = lib.swmm_schedule_search(ctypes.byref(spec), rows, MAX_ROWS, ctypes.byref(res))
@@ -216,11 +219,11 @@ def table_rows(sched: int) -> list:
 
 
 def schedule_check(rows, *, accumulate=False, preserve=(), temps=0, kinds=(), max_copies=0,
-                   recompute=False) -> Outcome:
+                   recompute=False, shape=None) -> Outcome:
     """Replay `rows` (a list of Row) under the same rules; found is True when
     every row is a legal move and the results end in place."""
     lib = _lib()
-    spec = _spec(accumulate, preserve, temps, kinds, -1, max_copies, recompute, MAX_ROWS, 0)
+    spec = _spec(accumulate, preserve, temps, kinds, -1, max_copies, recompute, MAX_ROWS, 0, shape=shape)
     n = len(rows)
     crows = _crows(rows)
     res = _Result()

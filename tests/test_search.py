@@ -492,3 +492,30 @@ def test_shipped_schedules_with_fewer_additions(Z, monkeypatch, name, table):
     assert adds == F.FOUND[name]["search"]["max_adds"]
     assert adds + 3 == sum(r.op == search.ADD for r in search.table_rows(table))
     run_found(Z, monkeypatch, chk.rows, spec["accumulate"], spec["preserve"])
+
+
+@pytest.mark.parametrize("shape,exists", [((2, 1, 1), True), ((1, 1, 2), True), ((3, 1, 2), False),
+                                          ((2, 1, 3), False), ((1, 2, 1), False), ((2, 2, 1), False)])
+def test_in_place_rectangular_shapes(Z, monkeypatch, shape, exists):
+    """Section 5.3: an in-place C <- AB (no temporary) needs k <= min(m, n),
+    and A or B as large as C: it exists for k = n <= m (Table 3) and, with
+    m and n in swapped roles, for k = m <= n; for k < m, n with m != n, or
+    k > min(m, n), the game has no schedule.  A found schedule runs in the
+    oracle on matrices of that shape."""
+    search, swmm = Z
+    o = search.schedule_search(temps=0, kinds=(swmm.T3_IP, search.SELF), shape=shape, max_rows=30)
+    assert o.found == exists and (exists or o.exhausted)
+    if not exists:
+        return
+    chk = search.schedule_check(o.rows, temps=0, kinds=(swmm.T3_IP, search.SELF), shape=shape)
+    assert chk.found
+    table = to_oracle(Z, chk.rows)
+    blocks = frozenset({"L11", "L12", "L21", "L22", "R11", "R12", "R21", "R22"})
+    monkeypatch.setitem(OS.KINDS, "Found", OS.Kind(table, False, blocks, frozenset(), False))
+    R = ring.ModP(65521)
+    m, k, n = (8 * x for x in shape)
+    rng = np.random.default_rng(sum(shape))
+    for depth in (1, 2):
+        A, B = rng.integers(0, R.p, (m, k)), rng.integers(0, R.p, (k, n))
+        out, _, _, _ = OS.run("Found", R, A, B, None, alpha=3, depth=depth)
+        assert np.array_equal(out, classical.muladd_modp(3, A, B, 0, np.zeros((m, n), dtype=np.int64), R.p))
