@@ -519,3 +519,25 @@ def test_in_place_rectangular_shapes(Z, monkeypatch, shape, exists):
         A, B = rng.integers(0, R.p, (m, k)), rng.integers(0, R.p, (k, n))
         out, _, _, _ = OS.run("Found", R, A, B, None, alpha=3, depth=depth)
         assert np.array_equal(out, classical.muladd_modp(3, A, B, 0, np.zeros((m, n), dtype=np.int64), R.p))
+
+
+def test_tables_under_rectangular_shapes(Z):
+    """Replayed with block shapes: Table 3 is legal for k = n <= m and not
+    for k = m < n (it stores products in blocks of A); Table 8 (AcR, the
+    rectangular accumulation of Section 5.3) is legal for every ordering of
+    m, k, n; Table 6 calls square-only schedules and is not."""
+    search, swmm = Z
+    ip = TABLES["IP"]
+    rows = search.table_rows(swmm.T3_IP)
+    assert search.schedule_check(rows, preserve=ip[0], temps=ip[1], kinds=ip[2], shape=(2, 1, 1)).found
+    assert not search.schedule_check(rows, preserve=ip[0], temps=ip[1], kinds=ip[2], shape=(1, 1, 2)).found
+    keep, temps, kinds, _, _ = TABLES["AcR"]
+    rows = search.table_rows(swmm.T8_ACR)
+    for shape in [(1, 2, 4), (4, 2, 1), (2, 4, 1), (1, 4, 2), (4, 1, 2), (2, 1, 4)]:
+        assert search.schedule_check(rows, accumulate=True, preserve=keep, temps=temps, kinds=kinds,
+                                     shape=shape).found, shape
+    keep, temps, kinds, _, _ = TABLES["AcLR"]
+    rows = search.table_rows(swmm.T6_ACLR)
+    assert search.schedule_check(rows, accumulate=True, preserve=keep, temps=temps, kinds=kinds).found
+    assert not search.schedule_check(rows, accumulate=True, preserve=keep, temps=temps, kinds=kinds,
+                                     shape=(2, 1, 1)).found
