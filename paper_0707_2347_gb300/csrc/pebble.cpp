@@ -363,24 +363,27 @@ inline uint64_t mix(uint64_t x) {  // splitmix64 finaliser
   return x ^ (x >> 31);
 }
 
-// Open-addressing set of 128-bit state fingerprints with the rows and the
-// block additions of the cheapest path each was expanded at.
+// Open-addressing set of 128-bit state fingerprints, each with the rows and
+// block additions of the path it was last expanded on.  A state reached
+// again is expanded again unless that path had no more rows and no more
+// additions (then every continuation was already tried within the limits).
+// The table starts small and doubles up to the state limit.
 class Visited {
  public:
-  bool init(int64_t cap_states) {
-    cap_ = 1;
-    while (cap_ < 2 * (uint64_t)cap_states) cap_ <<= 1;
-    tab_ = new (std::nothrow) Slot[cap_]();
-    return tab_ != nullptr;
+  bool init(int64_t max_states) {
+    max_cap_ = 1;
+    while (max_cap_ < 2 * (uint64_t)max_states) max_cap_ <<= 1;
+    return alloc(std::min<uint64_t>(max_cap_, 1u << 16));
   }
-  ~Visited() { delete[] tab_; }
-  // Slot of a fingerprint, or -1 when the state was already expanded with
-  // no more rows and no more additions (nothing to do); *full when the
-  // table has no room.
-  int64_t probe(uint64_t h1, uint64_t h2, int depth, int adds, bool *full) const {
+  // Slot for a fingerprint, or -1 when nothing is to be done (dominated, or
+  // *full: the state limit is reached).
+  int64_t probe(uint64_t h1, uint64_t h2, int depth, int adds, bool *full) {
     h1 |= 1;
-    uint64_t i = h1 & (cap_ - 1);
-    for (;;) {
+    if (size_ * 2 >= cap_ && cap_ < max_cap_ && !grow()) {
+      *full = true;
+      return -1;
+    }
+    for (uint64_t i = h1 & (cap_ - 1);; i = (i + 1) & (cap_ - 1)) {
       const Slot &s = tab_[i];
       if (s.h1 == 0) {
         if (size_ * 2 >= cap_) {
@@ -390,17 +393,15 @@ class Visited {
         return (int64_t)i;
       }
       if (s.h1 == h1 && s.h2 == h2) return (depth < s.depth || adds < s.adds) ? (int64_t)i : -1;
-      i = (i + 1) & (cap_ - 1);
     }
   }
   void insert(int64_t i, uint64_t h1, uint64_t h2, int depth, int adds) {
     Slot &s = tab_[i];
-    const bool fresh = s.h1 == 0;
-    if (fresh) ++size_;
+    if (s.h1 == 0) ++size_;
     s.h1 = h1 | 1;
     s.h2 = h2;
-    s.depth = (uint8_t)(fresh ? depth : std::min<int>(depth, s.depth));
-    s.adds = (uint8_t)(fresh ? adds : std::min<int>(adds, s.adds));
+    s.depth = (uint8_t)depth;
+    s.adds = (uint8_t)adds;
   }
   int64_t size() const { return (int64_t)size_; }
 
@@ -409,8 +410,34 @@ class Visited {
     uint64_t h1, h2;
     uint8_t depth, adds;
   };
-  Slot *tab_ = nullptr;
-  uint64_t cap_ = 0, size_ = 0;
+  bool alloc(uint64_t cap) {
+    std::vector<Slot> t;
+    try {
+      t.assign(cap, Slot{0, 0, 0, 0});
+    } catch (...) {
+      return false;
+    }
+    tab_.swap(t);
+    cap_ = cap;
+    return true;
+  }
+  bool grow() {
+    std::vector<Slot> old;
+    old.swap(tab_);
+    if (!alloc(cap_ * 2)) {
+      tab_.swap(old);
+      return false;
+    }
+    for (const Slot &s : old) {
+      if (s.h1 == 0) continue;
+      uint64_t i = s.h1 & (cap_ - 1);
+      while (tab_[i].h1 != 0) i = (i + 1) & (cap_ - 1);
+      tab_[i] = s;
+    }
+    return true;
+  }
+  std::vector<Slot> tab_;
+  uint64_t cap_ = 0, max_cap_ = 0, size_ = 0;
 };
 
 class Search {
@@ -700,7 +727,8 @@ class Search {
     if (sp_.max_adds >= 0 && adds + adds_bound(s, pres) > sp_.max_adds) return false;
     uint64_t h1, h2;
     fingerprint(s, pres, want, &h1, &h2);
-    const int64_t slot = vis_.probe(h1, h2, depth, adds, &full_);
+    const int cost_adds = sp_.max_adds >= 0 ? adds : 0;  // additions matter only under a limit
+    const int64_t slot = vis_.probe(h1, h2, depth, cost_adds, &full_);
     if (slot < 0) return false;
     // dead states go to a lossy cache (an evicted one is only re-checked)
     uint64_t &dead = dead_[h1 & (kDeadSlots - 1)];
@@ -709,7 +737,7 @@ class Search {
       dead = h2 | 1;
       return false;
     }
-    vis_.insert(slot, h1, h2, depth, adds);
+    vis_.insert(slot, h1, h2, depth, cost_adds);
     const uint32_t dmask = dests(s);
 
     for (uint64_t m = want & ~g_.inputs; m; m &= m - 1) {

@@ -19,7 +19,7 @@ checked against the search that produced it.
          6's contract), 14 block additions against Table 6's 17.
   accr14 C <- alpha AB + beta C overwriting B, two temporaries (Table 7's
          contract), 14 block additions against Table 7's 17.
-The last three are found at run time (a few seconds at most).
+The last two are found at run time (a few seconds).
 """
 from __future__ import annotations
 
@@ -66,8 +66,27 @@ FOUND = {
     "ab12": dict(
         spec=dict(accumulate=False, preserve=_AB, temps=2, kinds=(Q.SELF, swmm.T2_HLJJTT)),
         search=dict(max_adds=12),
-        rows=None,
-    ),
+        rows=[
+            (Q.ADD, "C11", "A21", "A22", 1, False, 1, 0),        # S1
+            (Q.ADD, "C12", "C11", "A11", -1, False, 1, 0),       # S2
+            (Q.ADD, "C21", "A11", "A21", -1, False, 1, 0),       # S3
+            (Q.ADD, "X", "A12", "C12", -1, False, 1, 0),         # S4
+            (Q.ADD, "Y", "B12", "B11", -1, False, 1, 0),         # T1
+            (Q.MUL, "C22", "C11", "Y", 1, False, 1, Q.SELF),     # P5
+            (Q.ADD, "C11", "B22", "B12", -1, False, 1, 0),       # T3
+            (Q.MUL, "Y", "C21", "C11", 1, False, 1, Q.SELF),     # P7
+            (Q.ADD, "C11", "B11", "C11", 1, False, 1, 0),        # T2 = B11 + T3
+            (Q.MUL, "C21", "C12", "C11", 1, False, 1, Q.SELF),   # P6
+            (Q.ADD, "C12", "C11", "B21", -1, False, 1, 0),       # T4
+            (Q.MUL, "C11", "A11", "B11", 1, False, 1, Q.SELF),   # P1
+            (Q.ADD, "C21", "C11", "C21", 1, False, 1, 0),        # U2
+            (Q.ADD, "C21", "Y", "C21", 1, False, 1, 0),          # U3
+            (Q.MUL, "C11", "A12", "B21", 1, True, 1, swmm.T2_HLJJTT),   # U1 = P2 + P1
+            (Q.ADD, "C22", "C22", "C21", 1, False, 1, 0),        # U7
+            (Q.MUL, "C21", "A22", "C12", 1, True, -1, swmm.T2_HLJJTT),  # U6 = U3 - P4
+            (Q.ADD, "C12", "C22", "Y", -1, False, 1, 0),         # U4 = U7 - P7
+            (Q.MUL, "C12", "X", "B22", 1, True, 1, swmm.T2_HLJJTT),     # U5 = U4 + P3
+        ]),
     "aclr14": dict(
         spec=dict(accumulate=True, preserve=(), temps=2, kinds=(swmm.T3_IP, Q.SELF)),
         search=dict(max_adds=14, max_rows=30),
