@@ -787,10 +787,16 @@ int set_schedule(swmm_t h, const swmm_search_spec *spec, const swmm_search_row *
   CustomSchedule cs;
   std::string err;
   if (!lower_schedule(*spec, rows, nrows, &cs, &err)) return fail(h, SWMM_EINVAL, "schedule rejected: " + err);
+  if (!h->graphs.empty()) {
+    // captured calls hold the previous schedule: let them finish, drop them
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e == cudaSuccess && h->cap) e = cudaStreamSynchronize(h->cap);
+    if (e != cudaSuccess) return fail(h, SWMM_ECUDA, cudaGetErrorString(e));
+    h->graphs.clear();
+  }
   h->custom = std::move(cs);
   h->custom_info = KindInfo{"custom", &h->custom.rows, h->custom.accumulate, true};
   h->has_custom = true;
-  h->graphs.clear();  // captured calls hold the previous schedule
   return SWMM_OK;
 }
 
