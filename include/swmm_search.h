@@ -164,7 +164,8 @@ int swmm_schedule_check(const swmm_search_spec *spec, swmm_search_row *rows, int
  * fused tensor-core level, as for the tables).  The operands must be
  * square; the entry point follows the contract (see SWMM_CUSTOM).  Blocks
  * of A and B the spec does not preserve may come back overwritten.  Cached
- * graphs of earlier calls are dropped.  Returns SWMM_OK, or SWMM_EINVAL
+ * graphs of earlier calls are dropped (after the handle's streams finish
+ * the work already issued; SWMM_ECUDA if that wait fails).  Returns SWMM_OK, or SWMM_EINVAL
  * (reason in swmm_last_error) for an illegal or incomplete schedule. */
 int swmm_set_schedule(swmm_t h, const swmm_search_spec *spec, const swmm_search_row *rows, int32_t nrows);
 
