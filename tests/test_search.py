@@ -541,3 +541,31 @@ def test_tables_under_rectangular_shapes(Z):
     assert search.schedule_check(rows, accumulate=True, preserve=keep, temps=temps, kinds=kinds).found
     assert not search.schedule_check(rows, accumulate=True, preserve=keep, temps=temps, kinds=kinds,
                                      shape=(2, 1, 1)).found
+
+
+def test_bench_custom_workloads_plan(Z):
+    """Every benchmark workload that runs a custom schedule (a table with
+    other kinds, or a shipped searched schedule) builds a legal schedule
+    that the planner accepts at the workload's size."""
+    search, swmm = Z
+    import bench
+    from paper_0707_2347_gb300 import schedules_found as F
+    seen = 0
+    for name, w in bench.WORKLOADS.items():
+        if w["sched"] != swmm.CUSTOM:
+            continue
+        if "found" in w:
+            rows, spec = F.rows(w["found"]), F.spec(w["found"])
+        else:
+            rows = search.table_rows(w["table"])
+            for r in rows:
+                if r.op == search.MUL:
+                    r.kind = w["replace"].get(r.kind, r.kind)
+            spec = dict(accumulate=True, preserve=A_ALL + B_ALL, temps=2,
+                        kinds=sorted({r.kind for r in rows if r.op == search.MUL}), recompute=True)
+        assert search.schedule_check(rows, **spec).found, name
+        opts = swmm.Opts(mode=w["mode"], p=w["p"] or 65521, sched=swmm.CUSTOM, depth=w["depth"])
+        _, plan = search.schedule_workspace(rows, w["m"], w["k"], w["n"], opts, **spec)
+        assert plan > 0, name
+        seen += 1
+    assert seen >= 3
