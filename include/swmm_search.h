@@ -107,7 +107,16 @@ typedef struct {
                            block it fits (temporaries hold any), the square
                            tables (4-7, 9) are not called unless m = k = n,
                            Table 3 only when k = n <= m.  0, 0, 0: square */
+  int32_t order;        /* SWMM_ORDER_*: which values the search tries to
+                           form first.  The answer to "does a schedule
+                           exist" does not depend on it; which schedule is
+                           found first and how fast does */
 } swmm_search_spec;
+
+#define SWMM_ORDER_ASCENDING 0  /* candidate list order (operand sums first) */
+#define SWMM_ORDER_DESCENDING 1 /* results and sums of products first */
+#define SWMM_ORDER_PORTFOLIO 2  /* both in turn, budgets growing fourfold
+                                   (2^16, 2^16, 2^18, 2^18, ... states) */
 
 #define SWMM_SEARCH_MAX_ROWS 64
 

@@ -371,6 +371,7 @@ inline uint64_t mix(uint64_t x) {  // splitmix64 finaliser
 class Visited {
  public:
   bool init(int64_t max_states) {
+    size_ = 0;
     max_cap_ = 1;
     while (max_cap_ < 2 * (uint64_t)max_states) max_cap_ <<= 1;
     return alloc(std::min<uint64_t>(max_cap_, 1u << 16));
@@ -459,19 +460,34 @@ class Search {
     });
   }
 
+  // One depth-first search within `cap` states; with the portfolio order,
+  // searches in both orders with budgets growing fourfold, until one finds
+  // a schedule or visits every state (a proof), or the states run out.
   bool run(swmm_search_result *res, std::vector<swmm_search_row> *out) {
     const int64_t cap = sp_.max_states > 0 ? sp_.max_states : (int64_t)1 << 26;
-    if (!vis_.init(cap)) return false;
-    State s{};
-    for (int l = 0; l < SWMM_NLOC; ++l) s.loc[l] = kEmpty;
-    for (int i = 0; i < N_; ++i)
-      if (g_.nodes[i].input) s.loc[g_.nodes[i].home] = (int8_t)i;
-    s.done = g_.inputs;
-    const uint64_t want = normalize(&s);
-    found_ = dfs(s, 0, 0, want);
+    int64_t used = 0;
+    bool done = false;
+    for (int round = 0; !done; ++round) {
+      int64_t budget = cap - used;
+      if (sp_.order == SWMM_ORDER_PORTFOLIO) budget = std::min<int64_t>(budget, (int64_t)1 << (16 + 2 * (round / 2)));
+      descending_ = sp_.order == SWMM_ORDER_DESCENDING || (sp_.order == SWMM_ORDER_PORTFOLIO && round % 2 == 1);
+      if (!vis_.init(budget)) return false;
+      std::fill(dead_.begin(), dead_.end(), 0);
+      full_ = false;
+      path_.clear();
+      State s{};
+      for (int l = 0; l < SWMM_NLOC; ++l) s.loc[l] = kEmpty;
+      for (int i = 0; i < N_; ++i)
+        if (g_.nodes[i].input) s.loc[g_.nodes[i].home] = (int8_t)i;
+      s.done = g_.inputs;
+      const uint64_t want = normalize(&s);
+      found_ = dfs(s, 0, 0, want);
+      used += vis_.size();
+      done = found_ || !full_ || used >= cap || sp_.order != SWMM_ORDER_PORTFOLIO;
+    }
     res->found = found_ ? 1 : 0;
     res->exhausted = (!found_ && !full_) ? 1 : 0;
-    res->states = vis_.size();
+    res->states = used;
     if (found_) *out = best_;
     return true;
   }
@@ -740,8 +756,10 @@ class Search {
     vis_.insert(slot, h1, h2, depth, cost_adds);
     const uint32_t dmask = dests(s);
 
-    for (uint64_t m = want & ~g_.inputs; m; m &= m - 1) {
-      const int w = __builtin_ctzll(m);
+    for (uint64_t m = want & ~g_.inputs; m;) {
+      // values in list order, or (descending) results and sums of products first
+      const int w = descending_ ? 63 - __builtin_clzll(m) : __builtin_ctzll(m);
+      m &= ~(1ull << w);
       if (!to_produce(s, pres, w)) continue;
       for (const Deriv &d : g_.nodes[w].der) {
         if (!can_compute(s, d, w)) continue;
@@ -823,7 +841,7 @@ class Search {
   std::vector<Contract> con_;
   Visited vis_;
   std::vector<swmm_search_row> path_, best_;
-  bool found_ = false, full_ = false;
+  bool found_ = false, full_ = false, descending_ = false;
 };
 
 // ------------------------------------------------------------------ replay
@@ -931,6 +949,7 @@ bool spec_ok(const swmm_search_spec *spec) {
   const uint32_t known = (1u << SWMM_T1_DHSS) | (1u << SWMM_T2_HLJJTT) | (1u << SWMM_T3_IP) | (1u << SWMM_T4_OVL) |
                          (1u << SWMM_T5_OVR) | (1u << SWMM_T6_ACLR) | (1u << SWMM_T7_ACCR) | (1u << SWMM_T8_ACR) |
                          (1u << SWMM_T9_ACC) | (1u << SWMM_T4M_OVL) | (1u << SWMM_SEARCH_SELF);
+  if (spec->order < SWMM_ORDER_ASCENDING || spec->order > SWMM_ORDER_PORTFOLIO) return false;
   return (spec->kinds & ~known) == 0;
 }
 

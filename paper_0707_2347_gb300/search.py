@@ -19,6 +19,7 @@ ADD, MUL, COPY = 0, 1, 2
 COEFS = (1, -1, "b", "-b")  # SWMM_COEF_ONE, NEG, BETA, NBETA
 SELF = 31
 MAX_ROWS = 64
+ASCENDING, DESCENDING, PORTFOLIO = 0, 1, 2  # search orders
 
 
 class _Spec(ctypes.Structure):
@@ -26,7 +27,7 @@ class _Spec(ctypes.Structure):
                 ("kinds", ctypes.c_uint32), ("max_written", ctypes.c_int32), ("max_copies", ctypes.c_int32),
                 ("recompute", ctypes.c_int32), ("max_rows", ctypes.c_int32), ("max_adds", ctypes.c_int32),
                 ("max_states", ctypes.c_int64), ("exclude", ctypes.c_uint64), ("m", ctypes.c_int32),
-                ("k", ctypes.c_int32), ("n", ctypes.c_int32)]
+                ("k", ctypes.c_int32), ("n", ctypes.c_int32), ("order", ctypes.c_int32)]
 
 
 class _Row(ctypes.Structure):
@@ -86,7 +87,7 @@ def _lib():
 
 
 def _spec(accumulate, preserve, temps, kinds, max_written, max_copies, recompute, max_rows, max_states, max_adds=-1,
-          exclude=(), shape=None):
+          exclude=(), shape=None, order=ASCENDING):
     pm = 0
     for b in preserve:
         i = LOCS.index(b)
@@ -102,7 +103,7 @@ def _spec(accumulate, preserve, temps, kinds, max_written, max_copies, recompute
         em |= 1 << names.index(v)
     m, k, n = shape if shape else (0, 0, 0)
     return _Spec(int(bool(accumulate)), pm, temps, km, max_written, max_copies, int(bool(recompute)), max_rows,
-                 max_adds, max_states, em, m, k, n)
+                 max_adds, max_states, em, m, k, n, order)
 
 
 def node_names(accumulate: bool) -> list:
@@ -122,16 +123,19 @@ def _rows_out(crows, n, accumulate):
 
 
 def schedule_search(*, accumulate=False, preserve=(), temps=0, kinds=(), max_written=-1, max_copies=0,
-                    recompute=False, max_rows=40, max_states=0, max_adds=-1, exclude=(), shape=None) -> Outcome:
+                    recompute=False, max_rows=40, max_states=0, max_adds=-1, exclude=(), shape=None,
+                    order=ASCENDING) -> Outcome:
     """Search for one level's schedule: C <- alpha AB (+ beta C when
     `accumulate`), keeping the blocks named in `preserve`, with `temps`
     temporaries, recursive products of the given `kinds`, at most
     `max_adds` block additions, never forming the values named in
     `exclude` (see node_names); `shape` = relative sizes (m, k, n) of the
-    operands, None for square blocks."""
+    operands, None for square blocks; `order`: ASCENDING, DESCENDING or
+    PORTFOLIO (both in turn; often much faster to find a schedule when one
+    order alone is slow)."""
     lib = _lib()
     spec = _spec(accumulate, preserve, temps, kinds, max_written, max_copies, recompute, max_rows, max_states,
-                 max_adds, exclude, shape)
+                 max_adds, exclude, shape, order)
     rows = (_Row * MAX_ROWS)()
     res = _Result()
     rc = lib.swmm_schedule_search(ctypes.byref(spec), rows, MAX_ROWS, ctypes.byref(res))

@@ -569,3 +569,16 @@ def test_bench_custom_workloads_plan(Z):
         assert plan > 0, name
         seen += 1
     assert seen >= 3
+
+
+@pytest.mark.parametrize("order", [0, 1, 2])
+def test_search_orders_agree(Z, order):
+    """Whether a schedule exists does not depend on the order the search
+    tries values in: Table 1's contract has no schedule with one temporary
+    and has one with two, in every order (the portfolio alternates both)."""
+    search, _ = Z
+    keep = A_ALL + B_ALL
+    o = search.schedule_search(preserve=keep, temps=1, kinds=(search.SELF,), order=order)
+    assert not o.found and o.exhausted
+    o = search.schedule_search(preserve=keep, temps=2, kinds=(search.SELF,), order=order)
+    assert o.found and search.schedule_check(o.rows, preserve=keep, temps=2, kinds=(search.SELF,)).found
