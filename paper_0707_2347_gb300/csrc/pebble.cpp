@@ -31,7 +31,9 @@
 // result can no longer be obtained (a value it needs was overwritten and
 // cannot be computed again), a block that must be preserved is lost, or an
 // admissible bound (rows, block additions, input blocks overwritten) shows
-// that the spec's limits cannot be met from it.
+// that the spec's limits cannot be met from it.  The order in which values
+// are tried (list order, results first, or both in turn with growing
+// budgets) changes what is found first, never whether a schedule exists.
 #include "swmm.h"
 #include "swmm_search.h"
 #include "schedules.h"
