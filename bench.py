@@ -109,7 +109,7 @@ DEFAULT = "t9_8192_p65521"
 # depth-1 workload) read 75.6 MB and wrote 2.2 MB; the 8192^2 depth-3 step
 # merges its 49 fused levels into 27 launches, and the traffic per fused
 # level is the same operands and targets, so the average launch moves
-# 77.8 MB x 49 / 27.  See profiles/gemm_kernel_fused_level_7x1024_p65521.md.
+# 77.8 MB x 49 / 27.
 TRAFFIC = {"t9_8192_p65521": 77.8e6 * 49 / 27, "t9_2048_p65521_d1": 77.8e6}
 
 
@@ -187,56 +187,75 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def cpu_baseline(w, A, B, C, budget_s: float = 12.0):
-    """The oracle's classical product on a bounded sample of rows."""
+def _oracle_rows(w, A, B, C, sel):
     from oracle import classical
-    m, k, n = w["m"], w["k"], w["n"]
-    rng = np.random.default_rng(5)
-    rows = 2
-    while True:
-        sel = rng.choice(m, rows, replace=False)
+    if w["mode"] == MODP:
+        classical.rows_muladd_modp(sel, 1, A, B, 1, C, w["p"])
+    else:
+        classical.rows_muladd_f64(sel, 1.0, A, B, 1.0, C)
+
+
+def _oracle_parallel(w, A, B, C, rows, threads, seed):
+    """The oracle's classical product on `threads` host threads at once, each
+    on its own sample of `rows` rows (numpy's integer and float matmul loops
+    release the interpreter lock, so the threads run on separate cores).
+    Returns the wall time."""
+    from concurrent.futures import ThreadPoolExecutor
+    m = w["m"]
+    rng = np.random.default_rng(seed)
+    sels = [rng.choice(m, rows, replace=False) for _ in range(threads)]
+    with ThreadPoolExecutor(threads) as ex:
         t0 = time.perf_counter()
-        if w["mode"] == MODP:
-            classical.rows_muladd_modp(sel, 1, A, B, 1, C, w["p"])
-        else:
-            classical.rows_muladd_f64(sel, 1.0, A, B, 1.0, C)
-        dt = time.perf_counter() - t0
-        if dt > budget_s / 4 or rows >= m:
+        list(ex.map(lambda sel: _oracle_rows(w, A, B, C, sel), sels))
+        return time.perf_counter() - t0
+
+
+def cpu_baseline(w, A, B, C, budget_s: float = 16.0):
+    """The oracle's classical product on every host core, each core on a
+    bounded sample of rows of the same product; the one-core figure beside it."""
+    m, k, n = w["m"], w["k"], w["n"]
+    cores = os.cpu_count() or 1
+    rows = 2
+    while True:  # one core: size the sample to about a quarter of the budget
+        t0 = time.perf_counter()
+        _oracle_rows(w, A, B, C, np.random.default_rng(5).choice(m, rows, replace=False))
+        dt1 = time.perf_counter() - t0
+        if dt1 > budget_s / 8 or rows >= m:
             break
-        rows = min(m, max(rows * 2, int(rows * budget_s / 4 / max(dt, 1e-3))))
-    gops = 2.0 * rows * n * k / dt / 1e9
-    return {"value": round(gops, 4), "unit": "GOP/s", "cores": 1, "kind": "oracle",
-            "sample": f"{rows} of {m} rows of the same product (numpy int64 matmul mod p, one core), {dt:.1f} s"}
+        rows = min(m, max(rows * 2, int(rows * budget_s / 8 / max(dt1, 1e-3))))
+    one = 2.0 * rows * n * k / dt1 / 1e9
+    dt = _oracle_parallel(w, A, B, C, rows, cores, 7)
+    gops = 2.0 * rows * cores * n * k / dt / 1e9
+    return {"value": round(gops, 4), "unit": "GOP/s", "cores": cores, "kind": "oracle",
+            "single_core_value": round(one, 4),
+            "sample": (f"{cores} threads x {rows} of {m} rows of the same product (numpy "
+                       f"{'int64 matmul mod p' if w['mode'] == MODP else 'float64 matmul'}), {dt:.1f} s; "
+                       f"one core {rows} rows in {dt1:.1f} s")}
 
 
 def run_reference(args, w, rank, world):
     if rank != 0:
         return
     A, B, C = make_inputs(w)
-    from oracle import classical
     m, k, n = w["m"], w["k"], w["n"]
-    rng = np.random.default_rng(6)
-    rows = max(1, min(m, 8))
+    cores = os.cpu_count() or 1
+    rows = 8
     ts = []
     for step in range(args.warmup + args.steps):
-        sel = rng.choice(m, rows, replace=False)
-        t0 = time.perf_counter()
-        if w["mode"] == MODP:
-            classical.rows_muladd_modp(sel, 1, A, B, 1, C, w["p"])
-        else:
-            classical.rows_muladd_f64(sel, 1.0, A, B, 1.0, C)
+        dt = _oracle_parallel(w, A, B, C, rows, cores, 6 + step)
         if step >= args.warmup:
-            ts.append(time.perf_counter() - t0)
+            ts.append(dt)
     t = sum(ts) / len(ts)
-    value = 2.0 * rows * n * k / t / 1e9
+    value = 2.0 * rows * cores * n * k / t / 1e9
     line = {
         "impl": "reference", "metric": "effective GOP/s (2mnk/t)", "value": round(value, 4), "unit": "GOP/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t * 1e3, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "int64 mod p" if w["mode"] == MODP else "f64", "data": "synthetic",
-        "config": {"workload": w["desc"], "m": m, "k": k, "n": n, "p": w["p"]},
-        "cpu_baseline": {"value": round(value, 4), "unit": "GOP/s", "cores": 1, "kind": "oracle",
-                         "sample": f"{rows} rows of the {m}x{n} product per step"},
+        "config": {"workload": w["desc"], "m": m, "k": k, "n": n, "p": w["p"],
+                   "schedule": "classical definition (the oracle)", "depth": 0},
+        "cpu_baseline": {"value": round(value, 4), "unit": "GOP/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{cores} threads x {rows} rows of the {m}x{n} product per step"},
         "e2e": {"value": round(value, 4), "unit": "GOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -378,6 +397,62 @@ def run_batch(args, w, S, h, torch, dev, dist, world, rank):
         dist.destroy_process_group()
 
 
+# Large accumulate products (the n >= 16384 range): Table 9 at the depths
+# that pay against the classical product of the same library.
+LARGE = ((16384, (1, 2)), (32768, (2,)))
+
+
+def run_large(args, S, h, torch, dev):
+    """C <- A B + C over Z/65521 at n = 16384 (Table 9 depth 1 and 2) and
+    n = 32768 (depth 2), each against this library's classical tcgen05
+    product on the same inputs: ms per step (CUDA events, graph replays,
+    inputs resident and far larger than L2), clocks sampled while timing.
+    n = 16384 inputs come from the seeded host generator; n = 32768 inputs
+    are drawn on the device (a seeded torch generator) to keep the run short."""
+    p = 65521
+    out = []
+    steps = max(3, min(args.steps, 5))
+    for n, depths in LARGE:
+        if n <= 16384:
+            A, B, C = (torch.from_numpy(synth.modp_matrix(sd, n, n, p)).to(dev)
+                       for sd in (synth.SEED_A, synth.SEED_B, synth.SEED_C))
+        else:
+            gen = torch.Generator(device=dev)
+            gen.manual_seed(n)
+            A, B, C = (torch.randint(0, p, (n, n), generator=gen, device=dev, dtype=torch.int32) for _ in range(3))
+        flops = 2.0 * n ** 3
+
+        def timed(o):
+            for _ in range(args.warmup):
+                h.muladd(1, A, B, 1, C, o)
+            h.sync()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            with Clocks(torch.cuda.current_device()) as clk:
+                e0.record()
+                for _ in range(steps):
+                    h.muladd(1, A, B, 1, C, o)
+                e1.record()
+                torch.cuda.synchronize()
+            h.sync()
+            return e0.elapsed_time(e1) / steps, clk.summary()
+
+        cms, cclk = timed(S.Opts(mode=S.MODP, p=p, sched=S.CLASSICAL, depth=0, flags=S.FLAG_GRAPH))
+        for d in depths:
+            ms, clk = timed(S.Opts(mode=S.MODP, p=p, sched=S.T9_ACC, depth=d, flags=S.FLAG_GRAPH))
+            st = h.stats()
+            out.append({"n": n, "schedule": "Acc (Table 9)", "depth": d, "ms_per_step": round(ms, 3),
+                        "gops": round(flops / (ms * 1e-3) / 1e9, 1), "classical_ms_per_step": round(cms, 3),
+                        "classical_gops": round(flops / (cms * 1e-3) / 1e9, 1),
+                        "speedup_vs_classical": round(cms / ms, 4),
+                        "extra_elems": st["plan_extra_elems"], "paper_extra_elems": st["paper_extra_elems"],
+                        "staging_bytes": st["staging_bytes"], "clocks": clk, "classical_clocks": cclk,
+                        "inputs": "seeded host generator" if n <= 16384 else "seeded device generator"})
+        del A, B, C
+        torch.cuda.empty_cache()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -391,6 +466,8 @@ def main():
     ap.add_argument("--no-graph", action="store_true", help="launch kernels directly instead of a CUDA graph")
     ap.add_argument("--serial", action="store_true",
                     help="capture the graph in row order on one stream (no dataflow overlap)")
+    ap.add_argument("--no-large", action="store_true",
+                    help="skip the n = 16384 / 32768 Table 9 vs classical record of the default workload")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     w = WORKLOADS[args.workload]
@@ -489,6 +566,13 @@ def main():
     opts = S.Opts(mode=mode, p=p or 65521, sched=w["sched"], depth=w["depth"], flags=gflag, **extra)
     with Clocks(local) as clk:
         ms = timed(opts, args.steps, args.warmup)
+    # device memory one call holds, measured on an eager call (graph memory
+    # is shared between the graphs a handle keeps, so its marks do not
+    # separate one call's use)
+    eager = S.Opts(mode=mode, p=p or 65521, sched=w["sched"], depth=w["depth"], flags=0, **extra)
+    with h.measure_peak() as mpk:
+        call(eager, dC, sA, sB)
+        h.sync()
     # Per-launch GEMM durations: the same K steps again with an event pair
     # around every leaf GEMM launch (recorded on the launching stream, inside
     # the graph).  The event nodes cost ~5 us each, so the value above is
@@ -518,11 +602,16 @@ def main():
         "gpu_launches": int((st["leaf_launches"] + st["ew_launches"]) * args.steps),
         "cuda_graph": not args.no_graph,
         "memory": {"workspace_bytes": st["workspace_bytes"], "plan_extra_elems": st["plan_extra_elems"],
-                   "paper_extra_elems_same_levels": st["paper_extra_elems"], "staging_bytes": st["staging_bytes"]},
-        "roofline": {"bound": "tensor", "achieved": round(achieved, 1), "peak": sustained, "unit": "TFLOP/s",
-                     "frac": round(achieved / sustained, 4), "traffic": TRAFFIC.get(args.workload),
+                   "paper_extra_elems_same_levels": st["paper_extra_elems"], "staging_bytes": st["staging_bytes"],
+                   "measured_peak_bytes": mpk.peak,
+                   "measured": "rise of the device's default memory pool during one eager call"},
+        # the leaf launches are short (a step lasts milliseconds): the burst
+        # figure is the denominator; the sustained one is kept beside it
+        "roofline": {"bound": "tensor", "achieved": round(achieved, 1), "peak": burst, "unit": "TFLOP/s",
+                     "frac": round(achieved / burst, 4), "traffic": TRAFFIC.get(args.workload),
                      "kernel": "gemm_kernel (leaf products, fp16 limb MMAs counted)",
-                     "peak_kind": f"{peak_kind} bf16 sustained", "launches_per_step": st["leaf_launches"],
+                     "peak_kind": f"{peak_kind} bf16 burst", "peak_sustained": sustained,
+                     "frac_of_sustained": round(achieved / sustained, 4), "launches_per_step": st["leaf_launches"],
                      "gemm_ms_per_step": round(gemm_ms / max(gemm_launches, 1) * st["leaf_launches"], 4),
                      "timing_pass_ms_per_step": round(tms, 4),
                      "timing_pass": "event pair per GEMM launch, graph captured in row order"},
@@ -593,6 +682,22 @@ def main():
         line["e2e"] = {"value": round(world * flops / (ems * 1e-3) / 1e9, 2), "unit": "GOP/s",
                        "h2d_bytes_per_step": int(A.nbytes + B.nbytes), "d2h_bytes_per_step": int(C.nbytes),
                        "ms_per_step": round(ems, 4), "entry": "device call, torch copies"}
+    if args.workload == DEFAULT and not args.no_large:
+        # the same step with operand staging bounded (SWMM_FLAG_LOWMEM)
+        dC.copy_(dC0)
+        lo = S.Opts(mode=mode, p=p or 65521, sched=w["sched"], depth=w["depth"], flags=gflag | S.FLAG_LOWMEM)
+        with Clocks(local) as lclk:
+            lms = timed(lo, args.steps, args.warmup)
+        lst = h.stats()
+        with h.measure_peak() as lpk:
+            call(S.Opts(mode=mode, p=p or 65521, sched=w["sched"], depth=w["depth"], flags=S.FLAG_LOWMEM), dC)
+            h.sync()
+        line["bounded_staging"] = {
+            "flag": "SWMM_FLAG_LOWMEM", "ms_per_step": round(lms, 4), "value": round(world * flops / (lms * 1e-3) / 1e9, 2),
+            "slowdown": round(lms / ms, 4), "staging_bytes": lst["staging_bytes"],
+            "workspace_bytes": lst["workspace_bytes"], "measured_peak_bytes": lpk.peak,
+            "paper_extra_bytes": 4 * lst["paper_extra_elems"], "clocks": lclk.summary()}
+        line["large"] = run_large(args, S, h, torch, dev)
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(w, A, B, C)
     if rank == 0:

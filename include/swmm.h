@@ -63,8 +63,11 @@ extern "C" {
 
 /* arithmetic modes */
 #define SWMM_MODP 0 /* exact arithmetic over Z/pZ, 2 < p < 2^16 */
-#define SWMM_FP32 1 /* float32 storage, 3 x bf16 split products (Section 2
-                       algorithm over the reals; accuracy mode) */
+#define SWMM_FP32 1 /* float32 storage (Section 2 algorithm over the reals;
+                       accuracy mode): each leaf operand is scaled by a
+                       power of two from its max |x| and split into fp16
+                       hi + lo (22 significant bits); hi*hi + hi*lo + lo*hi
+                       are accumulated in fp32 and the scales undone */
 
 /* schedules (the table numbers of the paper) */
 #define SWMM_CLASSICAL 0 /* one classical product, no Winograd level */
@@ -115,6 +118,16 @@ extern "C" {
                                   areas in turn) */
 #define SWMM_FLAG_SERIAL 16u   /* with SWMM_FLAG_GRAPH: capture every launch
                                   in row order on one stream */
+#define SWMM_FLAG_LOWMEM 32u   /* bound the tensor-core operand staging to
+                                  SWMM_LOWMEM_STAGE_BYTES: one staging area,
+                                  leaf launches not merged, and a fused level
+                                  (or a group of classical problems) staged
+                                  and multiplied in groups of products that
+                                  fit the bound; a single product whose
+                                  operands exceed it is staged whole.  Slower
+                                  (more, smaller launches), never different
+                                  results */
+#define SWMM_LOWMEM_STAGE_BYTES (64ll << 20)
 
 typedef struct swmm_ctx *swmm_t;
 
@@ -221,7 +234,10 @@ int swmm_muladd_host(swmm_t h, int64_t m, int64_t k, int64_t n, const void *alph
  * looks the array's device address up (cudaGetSymbolAddress); make that
  * first call before any stream capture.  All calls share the array: calls
  * whose work overlaps on the GPU (different streams, or several handles)
- * race on it and must be serialised by the caller. */
+ * race on it and must be serialised by the caller.  These calls always run
+ * eagerly in row order on the handle's stream: SWMM_FLAG_GRAPH,
+ * SWMM_FLAG_SERIAL and SWMM_FLAG_TIMING are ignored, leaf launches are not
+ * merged, and swmm_leaf_timing reports no launches after such a call. */
 #define SWMM_NOALLOC_SCRATCH_BYTES (32ll << 20)
 int swmm_muladd_noalloc(swmm_t h, int64_t m, int64_t k, int64_t n, const void *alpha,
                         const void *A, int64_t lda, const void *B, int64_t ldb,
@@ -309,12 +325,53 @@ int swmm_residual(swmm_t h, int64_t m, int64_t k, int64_t n,
                   const void *y0, const void *C, int64_t ldc, const void *x,
                   void *r, const swmm_opts *opts);
 
+/* Measured device memory of the library's calls (the paper counts extra
+ * memory in Table 10; this is the same quantity in bytes, as the device saw
+ * it).  Waits for the handle's streams, then writes out[0] = bytes of the
+ * device's default memory pool in use now (workspace and staging of eager
+ * calls come from it), out[1] = its high-water mark since the last reset,
+ * out[2] = bytes of graph memory in use now (the same for calls captured
+ * with SWMM_FLAG_GRAPH; graphs a handle keeps may hold some), out[3] = its
+ * high-water mark.  reset != 0 then sets both marks back to the current
+ * use, so the peak extra memory of the calls that follow is
+ * max(out[1] - out[0], out[3] - out[2]) read after them against the values
+ * read at the reset.  Both are per device: other users of the default pool
+ * or of graph memory on the device count too. */
+int swmm_memory_use(swmm_t h, int reset, int64_t *out);
+
 /* Statistics of the last completed call on this handle. */
 int swmm_get_stats(swmm_t h, swmm_stats *out);
 
 /* Wait for the handle's stream and report device-side errors
  * (SWMM_ETIMEOUT if a kernel's bounded wait gave up). */
 int swmm_sync(swmm_t h);
+
+/* Failure injection for tests of the error paths (the paper has no
+ * counterpart).  Failures are made on the host or by a device wait that is
+ * bounded: nothing faults, traps or hangs the GPU.
+ *   SWMM_HOOK_WAIT_NS      every mbarrier wait of the leaf GEMM kernel
+ *                          gives up after `value` ns (value <= 0: the
+ *                          default, 4 s); on expiry the kernel drains the
+ *                          copies and products it issued, frees its tensor
+ *                          memory and returns, and swmm_sync reports
+ *                          SWMM_ETIMEOUT.
+ *   SWMM_HOOK_STALL_GEMMS  the next `value` leaf GEMM launches first wait
+ *                          on a barrier that nothing arrives at, so that
+ *                          wait runs out (their results are undefined).
+ *   SWMM_HOOK_FAIL_ALLOCS  the next `value` device allocations of the
+ *                          handle's calls fail: the call returns
+ *                          SWMM_ENOMEM before any launch.
+ *   SWMM_HOOK_LOWMEM_BYTES the staging bound of SWMM_FLAG_LOWMEM calls on
+ *                          this handle (value <= 0: SWMM_LOWMEM_STAGE_BYTES),
+ *                          so that small products exercise the grouping.
+ * Settings apply to calls made afterwards on this handle; graphs captured
+ * earlier (SWMM_FLAG_GRAPH) keep what they captured.  Returns SWMM_EINVAL
+ * for an unknown hook. */
+#define SWMM_HOOK_WAIT_NS 1
+#define SWMM_HOOK_STALL_GEMMS 2
+#define SWMM_HOOK_FAIL_ALLOCS 3
+#define SWMM_HOOK_LOWMEM_BYTES 4
+int swmm_test_hook(swmm_t h, int32_t hook, int64_t value);
 
 const char *swmm_strerror(int code);
 /* Text of the last error on this handle (empty if none). */

@@ -69,6 +69,8 @@ bool make_target_tmap(CUtensorMap *map, const void *base, int64_t rows, int64_t 
 }
 
 // Event pairs around leaf GEMM launches (SWMM_FLAG_TIMING).
+constexpr uint64_t kDefaultWaitNs = 4000000000ull;  // 4 s
+
 struct EventTimer : TimingHook {
   std::vector<cudaEvent_t> ev;  // pairs: 2i = begin, 2i + 1 = end
   std::vector<double> flops;
@@ -127,6 +129,12 @@ struct swmm_ctx {
   cudaStream_t stream = nullptr;
   int num_sms = 152;
   int *d_err = nullptr;
+  // swmm_test_hook: bound of the device-side waits, GEMM launches still to
+  // stall, device allocations still to fail
+  uint64_t wait_ns = kDefaultWaitNs;
+  int stall_left = 0;
+  int fail_allocs = 0;
+  int64_t lowmem_bytes = SWMM_LOWMEM_STAGE_BYTES;  // staging bound of SWMM_FLAG_LOWMEM calls
   swmm_stats stats;
   std::string last_error;
   EventTimer timer;
@@ -162,6 +170,13 @@ struct swmm_ctx {
 };
 
 namespace {
+
+// swmm_test_hook(SWMM_HOOK_FAIL_ALLOCS): true when this allocation is to fail
+bool injected_alloc_failure(swmm_t h) {
+  if (h->fail_allocs <= 0) return false;
+  --h->fail_allocs;
+  return true;
+}
 
 int fail(swmm_t h, int code, const std::string &msg) {
   if (h) h->last_error = msg;
@@ -252,7 +267,7 @@ void reset_counts(Exec &x) {
   x.ws_top = x.ws_peak = x.stage_need = 0;
   x.tmp_elems = x.tmp_peak_elems = 0;
   x.add_elems = x.leaf_flops = x.leaf_launches = x.ew_launches = x.leaf_products = 0;
-  x.lazy = false;
+  x.lazy_views.clear();
   x.stage_turn = 0;
 }
 
@@ -399,6 +414,9 @@ int make_plan(swmm_t h, const Req &q, const swmm_opts *o, bool check_ptrs, Plan 
   x.fused = !(o->flags & SWMM_FLAG_UNFUSED);
   x.simt = (o->flags & SWMM_FLAG_SIMT_LEAF) != 0;
   x.num_sms = h->num_sms;
+  x.stage_budget = (o->flags & SWMM_FLAG_LOWMEM) ? h->lowmem_bytes : 0;
+  x.wait_ns = h->wait_ns;
+  x.stall_left = &h->stall_left;
   x.err = h->d_err;
   x.custom = h->has_custom ? &h->custom_info : nullptr;
   if (x.fp32) {
@@ -429,7 +447,8 @@ int make_plan(swmm_t h, const Req &q, const swmm_opts *o, bool check_ptrs, Plan 
   x.flush();
   if (!x.fail.empty()) return fail(h, SWMM_EINVAL, x.fail);
   // small leaf launches share launches (four staging slots in turn)
-  if (x.stage_need > 0 && x.stage_need <= kMergeStageBytes && !x.simt && x.leaf_launches > 1) {
+  if (x.stage_need > 0 && x.stage_need <= kMergeStageBytes && !x.simt && x.leaf_launches > 1 &&
+      x.stage_budget == 0) {
     reset_counts(x);
     x.merge = true;
     x.stage_slots = 4;
@@ -447,6 +466,30 @@ int make_plan(swmm_t h, const Req &q, const swmm_opts *o, bool check_ptrs, Plan 
   return SWMM_OK;
 }
 
+// The lazy blocks of an executor that overlap `d` (clipped to d when they
+// are views of the same root; whole otherwise).
+std::vector<View> lazy_in(const Exec &r, const View &d) {
+  std::vector<View> out;
+  const Rect rd = rect_of(d);
+  for (const View &x : r.lazy_views) {
+    const Rect rx = rect_of(x);
+    if (!overlaps(rx, rd)) continue;
+    if (rx.base == rd.base && rx.ld == rd.ld && rx.ld > 0) {
+      const int64_t r0 = std::max(rx.r0, rd.r0), c0 = std::max(rx.c0, rd.c0);
+      const int64_t r1 = std::min(rx.r0 + rx.rows, rd.r0 + rd.rows), c1 = std::min(rx.c0 + rx.cols, rd.c0 + rd.cols);
+      out.push_back(d.sub(r0 - rd.r0, c0 - rd.c0, r1 - r0, c1 - c0));
+    } else {
+      out.push_back(x);
+    }
+  }
+  return out;
+}
+
+// Canonical pass over the lazy parts of block b (host-operand copies back).
+void canon_lazy(Exec &r, const View &b) {
+  for (const View &v : lazy_in(r, b)) r.canon(v);
+}
+
 // Issue a planned call on `stream`: workspace, kernels, final canonical
 // pass, release.  Adds its counters to `st`.
 int enqueue(swmm_t h, const Plan &P, cudaStream_t stream, TimingHook *timing, const Scratch *ext, swmm_stats &st,
@@ -454,10 +497,10 @@ int enqueue(swmm_t h, const Plan &P, cudaStream_t stream, TimingHook *timing, co
   const Exec &x = P.x;
   Exec r = x;
   r.merge = x.merge && !ext;
-  r.stage_slots = r.merge ? 4 : (use_flow ? 2 : 1);
+  r.stage_slots = r.merge ? 4 : (use_flow && x.stage_budget == 0 ? 2 : 1);
   const int64_t stage_bytes = r.stage_slots * ((x.stage_need + 1023) / 1024 * 1024);
   r.dry = false;
-  r.lazy = false;
+  r.lazy_views.clear();
   r.stream = stream;
   r.timing = timing;
   r.ws_top = r.ws_peak = 0;
@@ -473,12 +516,18 @@ int enqueue(swmm_t h, const Plan &P, cudaStream_t stream, TimingHook *timing, co
                       std::to_string(ext->bytes) + "-byte static scratch");
     r.ws = x.ws_peak > 0 ? ext->base : nullptr;
     r.stage = x.stage_need > 0 ? ext->base + ws_bytes : nullptr;
+    r.ws_limit = ws_bytes;
+    r.stage_limit = stage_bytes;
   } else {
-    if (x.ws_peak > 0 && cudaMallocAsync((void **)&r.ws, x.ws_peak, stream) != cudaSuccess) {
+    r.ws_limit = x.ws_peak;
+    r.stage_limit = stage_bytes;
+    if (x.ws_peak > 0 &&
+        (injected_alloc_failure(h) || cudaMallocAsync((void **)&r.ws, x.ws_peak, stream) != cudaSuccess)) {
       cudaGetLastError();
       return fail(h, SWMM_ENOMEM, "workspace allocation failed");
     }
-    if (x.stage_need > 0 && cudaMallocAsync((void **)&r.stage, stage_bytes, stream) != cudaSuccess) {
+    if (x.stage_need > 0 &&
+        (injected_alloc_failure(h) || cudaMallocAsync((void **)&r.stage, stage_bytes, stream) != cudaSuccess)) {
       cudaGetLastError();
       if (r.ws) cudaFreeAsync(r.ws, stream);
       return fail(h, SWMM_ENOMEM, "staging allocation failed");
@@ -504,11 +553,10 @@ int enqueue(swmm_t h, const Plan &P, cudaStream_t stream, TimingHook *timing, co
     for (int q = 0; q < 4; ++q) {
       const int i = q / 2, j = q % 2;
       const View b = block_of(P.D, i, j);
-      if (r.lazy) r.canon(b);
+      canon_lazy(r, b);
       const int64_t r0 = i ? P.D.rows / 2 : 0, c0 = j ? P.D.cols / 2 : 0;
       r.copy_out(P.hC + 4 * (r0 * P.hldc + c0), P.hldc, b, tok_out);
     }
-    r.lazy = false;
   };
   if (use_flow) {
     Flow flow(stream, h->flow_streams, h->flow_events);
@@ -529,13 +577,17 @@ int enqueue(swmm_t h, const Plan &P, cudaStream_t stream, TimingHook *timing, co
     r.flush();
     host_out();
   }
-  if (r.lazy && r.ok()) {
-    // fused levels leave unreduced representatives: one canonicalising pass
-    ++r.ew_launches;
-    cudaError_t e = launch_canon_modp(P.D, r.p, stream);
-    if (e != cudaSuccess) {
-      r.cuda_err = e;
-      r.fail = std::string("canonical pass: ") + cudaGetErrorString(e);
+  if (r.ok()) {
+    // blocks of C whose last writer was a fused level's reduce-add hold
+    // unreduced representatives: one canonicalising pass over each
+    for (const View &v : lazy_in(r, P.D)) {
+      ++r.ew_launches;
+      cudaError_t e = launch_canon_modp(v, r.p, stream);
+      if (e != cudaSuccess) {
+        r.cuda_err = e;
+        r.fail = std::string("canonical pass: ") + cudaGetErrorString(e);
+        break;
+      }
     }
   }
   if (!ext && r.ws) cudaFreeAsync(r.ws, stream);
@@ -583,6 +635,7 @@ int run_plans(swmm_t h, const std::vector<Plan> &plans, uint32_t flags, const Sc
   std::memset(&st, 0, sizeof(st));
   if (!(flags & SWMM_FLAG_GRAPH) || ext) {
     h->last_timer = &h->timer;
+    if (ext) h->timer.used = 0;  // static-scratch calls record no leaf timing
     for (const Plan &P : plans) {
       int rc = enqueue(h, P, h->stream, timing ? &h->timer : nullptr, ext, st);
       if (rc != SWMM_OK) return rc;
@@ -893,8 +946,9 @@ int swmm_muladd_host(swmm_t h, int64_t m, int64_t k, int64_t n, const void *alph
     if (h->io_buf) cudaFree(h->io_buf);
     h->io_buf = nullptr;
     h->io_bytes = 0;
-    if (cudaMalloc((void **)&h->io_buf, need) != cudaSuccess) {
+    if (injected_alloc_failure(h) || cudaMalloc((void **)&h->io_buf, need) != cudaSuccess) {
       cudaGetLastError();
+      h->io_buf = nullptr;
       return fail(h, SWMM_ENOMEM, "device copies of the operands");
     }
     h->io_bytes = need;
@@ -1122,7 +1176,8 @@ int swmm_residual(swmm_t h, int64_t m, int64_t k, int64_t n, const void *alpha, 
   const size_t es = modp ? 4 : 8;
   char *tmp = nullptr;
   const size_t bytes = (size_t)(k + 2 * m) * es;
-  cudaError_t e = cudaMallocAsync((void **)&tmp, bytes, h->stream);
+  cudaError_t e = injected_alloc_failure(h) ? cudaErrorMemoryAllocation
+                                             : cudaMallocAsync((void **)&tmp, bytes, h->stream);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return fail(h, SWMM_ENOMEM, "probe temporaries");
@@ -1159,6 +1214,49 @@ int swmm_sync(swmm_t h) {
     return fail(h, SWMM_ETIMEOUT, "a kernel's bounded wait expired");
   }
   return SWMM_OK;
+}
+
+int swmm_memory_use(swmm_t h, int reset, int64_t *out) {
+  if (!h || !out) return SWMM_EINVAL;
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  if (e == cudaSuccess && h->cap) e = cudaStreamSynchronize(h->cap);
+  cudaMemPool_t pool = nullptr;
+  if (e == cudaSuccess) e = cudaDeviceGetDefaultMemPool(&pool, h->device);
+  cuuint64_t v[4] = {0, 0, 0, 0};
+  if (e == cudaSuccess) e = cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &v[0]);
+  if (e == cudaSuccess) e = cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemHigh, &v[1]);
+  if (e == cudaSuccess) e = cudaDeviceGetGraphMemAttribute(h->device, cudaGraphMemAttrUsedMemCurrent, &v[2]);
+  if (e == cudaSuccess) e = cudaDeviceGetGraphMemAttribute(h->device, cudaGraphMemAttrUsedMemHigh, &v[3]);
+  if (e == cudaSuccess && reset) {
+    cuuint64_t zero = 0;
+    e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrUsedMemHigh, &zero);
+    if (e == cudaSuccess) e = cudaDeviceSetGraphMemAttribute(h->device, cudaGraphMemAttrUsedMemHigh, &zero);
+  }
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(h, SWMM_ECUDA, std::string("memory pool query: ") + cudaGetErrorString(e));
+  }
+  for (int i = 0; i < 4; ++i) out[i] = (int64_t)v[i];
+  return SWMM_OK;
+}
+
+int swmm_test_hook(swmm_t h, int32_t hook, int64_t value) {
+  if (!h) return SWMM_EINVAL;
+  switch (hook) {
+    case SWMM_HOOK_WAIT_NS:
+      h->wait_ns = value > 0 ? (uint64_t)value : kDefaultWaitNs;
+      return SWMM_OK;
+    case SWMM_HOOK_STALL_GEMMS:
+      h->stall_left = value > 0 ? (int)std::min<int64_t>(value, 1 << 30) : 0;
+      return SWMM_OK;
+    case SWMM_HOOK_FAIL_ALLOCS:
+      h->fail_allocs = value > 0 ? (int)std::min<int64_t>(value, 1 << 30) : 0;
+      return SWMM_OK;
+    case SWMM_HOOK_LOWMEM_BYTES:
+      h->lowmem_bytes = value > 0 ? value : SWMM_LOWMEM_STAGE_BYTES;
+      return SWMM_OK;
+  }
+  return fail(h, SWMM_EINVAL, "unknown test hook");
 }
 
 const char *swmm_strerror(int code) {

@@ -20,7 +20,32 @@ namespace {
 struct V {
   char *ptr;
   int64_t ld;
+  int esz;  // 4: 32-bit elements; 2: 16-bit values in [0, p)
 };
+
+// four consecutive elements from column c of row r (16-byte / 8-byte loads)
+__device__ __forceinline__ uint4 ld4(const V &v, int64_t r, int64_t c) {
+  if (v.esz == 4) return *reinterpret_cast<const uint4 *>(v.ptr + 4 * (r * v.ld + c));
+  const uint2 h = *reinterpret_cast<const uint2 *>(v.ptr + 2 * (r * v.ld + c));
+  return make_uint4(h.x & 0xFFFFu, h.x >> 16, h.y & 0xFFFFu, h.y >> 16);
+}
+__device__ __forceinline__ void st4(const V &v, int64_t r, int64_t c, uint4 o) {
+  if (v.esz == 4) {
+    *reinterpret_cast<uint4 *>(v.ptr + 4 * (r * v.ld + c)) = o;
+  } else {
+    *reinterpret_cast<uint2 *>(v.ptr + 2 * (r * v.ld + c)) = make_uint2(o.x | (o.y << 16), o.z | (o.w << 16));
+  }
+}
+__device__ __forceinline__ uint32_t ld1(const V &v, int64_t r, int64_t c) {
+  if (v.esz == 4) return *reinterpret_cast<const uint32_t *>(v.ptr + 4 * (r * v.ld + c));
+  return *reinterpret_cast<const uint16_t *>(v.ptr + 2 * (r * v.ld + c));
+}
+__device__ __forceinline__ void st1(const V &v, int64_t r, int64_t c, uint32_t x) {
+  if (v.esz == 4)
+    *reinterpret_cast<uint32_t *>(v.ptr + 4 * (r * v.ld + c)) = x;
+  else
+    *reinterpret_cast<uint16_t *>(v.ptr + 2 * (r * v.ld + c)) = (uint16_t)x;
+}
 
 __device__ __forceinline__ uint32_t red2p(uint32_t r, uint32_t p) {
   // r in [0, 2p) -> [0, p): the wrapped r - p is huge when r < p
@@ -62,18 +87,16 @@ __global__ void add_modp_kernel(V d, V s1, V s2, int64_t rows, int64_t cols, uin
        i += (int64_t)gridDim.x * blockDim.x) {
     int64_t r = i / cw, c = i - r * cw;
     if (VEC) {
-      const uint4 a = *reinterpret_cast<const uint4 *>(s1.ptr + 4 * (r * s1.ld + 4 * c));
-      const uint4 b = *reinterpret_cast<const uint4 *>(s2.ptr + 4 * (r * s2.ld + 4 * c));
+      const uint4 a = ld4(s1, r, 4 * c);
+      const uint4 b = ld4(s2, r, 4 * c);
       uint4 o;
       o.x = comb<K1, K2>(a.x, b.x, u1, u2, p, m);
       o.y = comb<K1, K2>(a.y, b.y, u1, u2, p, m);
       o.z = comb<K1, K2>(a.z, b.z, u1, u2, p, m);
       o.w = comb<K1, K2>(a.w, b.w, u1, u2, p, m);
-      *reinterpret_cast<uint4 *>(d.ptr + 4 * (r * d.ld + 4 * c)) = o;
+      st4(d, r, 4 * c, o);
     } else {
-      uint32_t a = *reinterpret_cast<const uint32_t *>(s1.ptr + 4 * (r * s1.ld + c));
-      uint32_t b = *reinterpret_cast<const uint32_t *>(s2.ptr + 4 * (r * s2.ld + c));
-      *reinterpret_cast<uint32_t *>(d.ptr + 4 * (r * d.ld + c)) = comb<K1, K2>(a, b, u1, u2, p, m);
+      st1(d, r, c, comb<K1, K2>(ld1(s1, r, c), ld1(s2, r, c), u1, u2, p, m));
     }
   }
 }
@@ -136,8 +159,9 @@ __global__ void convert_kernel(V d, int64_t rows, int64_t cols, uint32_t coef, f
   }
 }
 
+// four elements per access: 16 (32-bit) or 8 (16-bit) aligned bytes
 bool vec_ok(const View &v) {
-  return ((uintptr_t)v.ptr % 16 == 0) && (v.ld % 4 == 0) && (v.cols % 4 == 0);
+  return ((uintptr_t)v.ptr % (4 * v.esz) == 0) && (v.ld % 4 == 0) && (v.cols % 4 == 0);
 }
 
 void grid_for(int64_t work, int &blocks, int &threads) {
@@ -148,7 +172,19 @@ void grid_for(int64_t work, int &blocks, int &threads) {
   blocks = (int)(b < 1 ? 1 : (b > cap ? cap : b));
 }
 
-V mk(const View &v) { return V{v.ptr, v.ld}; }
+V mk(const View &v) { return V{v.ptr, v.ld, v.esz}; }
+
+// d <- s element by element, between 32-bit and 16-bit storage (a 16-bit
+// destination receives the value reduced to [0, p))
+__global__ void copy_kernel(V d, V s, int64_t rows, int64_t cols, uint32_t p, uint32_t m) {
+  const int64_t total = rows * cols;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = i / cols, c = i - r * cols;
+    const uint32_t x = ld1(s, r, c);
+    st1(d, r, c, d.esz == 2 ? bred(x, p, m) : x);
+  }
+}
 
 template <int K1, int K2>
 cudaError_t add_dispatch_vec(View d, View s1, View s2, uint32_t u1, uint32_t u2, uint32_t p, cudaStream_t s) {
@@ -222,12 +258,19 @@ cudaError_t launch_scale_modp(View d, uint32_t coef, uint32_t p, cudaStream_t s)
 cudaError_t launch_canon_modp(View d, uint32_t p, cudaStream_t s) { return conv<4>(d, 0, 0.f, p, s); }
 cudaError_t launch_zero(View d, cudaStream_t s) {
   if (d.rows == 0 || d.cols == 0) return cudaSuccess;
-  return cudaMemset2DAsync(d.ptr, d.ld * 4, 0, d.cols * 4, d.rows, s);
+  return cudaMemset2DAsync(d.ptr, d.ld * d.esz, 0, d.cols * d.esz, d.rows, s);
 }
 
-cudaError_t launch_copy(View d, View src, cudaStream_t s) {
+cudaError_t launch_copy(View d, View src, uint32_t p, cudaStream_t s) {
   if (d.rows == 0 || d.cols == 0) return cudaSuccess;
-  return cudaMemcpy2DAsync(d.ptr, d.ld * 4, src.ptr, src.ld * 4, d.cols * 4, d.rows, cudaMemcpyDeviceToDevice, s);
+  if (d.esz == src.esz)
+    return cudaMemcpy2DAsync(d.ptr, d.ld * d.esz, src.ptr, src.ld * src.esz, d.cols * d.esz, d.rows,
+                             cudaMemcpyDeviceToDevice, s);
+  if (p == 0) return cudaErrorInvalidValue;  // 16-bit storage is mod p only
+  int b, t;
+  grid_for(d.rows * d.cols, b, t);
+  copy_kernel<<<b, t, 0, s>>>(mk(d), mk(src), d.rows, d.cols, p, (uint32_t)(0x100000000ull / p));
+  return cudaGetLastError();
 }
 
 }  // namespace swmm

@@ -72,11 +72,39 @@ View Exec::alloc_tmp(int64_t rows, int64_t cols) {
   v.cols = cols;
   v.ld = cols;
   v.ptr = ws ? ws + ws_top : nullptr;
+  if (!dry && ws_limit >= 0 && ws_top + rows * cols * 4 > ws_limit) {
+    // the planning pass sized the area: a real run must never need more
+    if (fail.empty()) fail = "temporaries exceed the planned workspace";
+    v.ptr = nullptr;
+  }
   ws_top += rup(rows * cols * 4, 256);
   ws_peak = std::max(ws_peak, ws_top);
   tmp_elems += rows * cols;
   tmp_peak_elems = std::max(tmp_peak_elems, tmp_elems);
   return v;
+}
+
+// every element of `in` lies in `out` (exact for views of one root and
+// leading dimension; false otherwise)
+static bool contains(const Rect &out, const Rect &in) {
+  return out.base == in.base && out.ld == in.ld && out.ld > 0 && in.r0 >= out.r0 && in.c0 >= out.c0 &&
+         in.r0 + in.rows <= out.r0 + out.rows && in.c0 + in.cols <= out.c0 + out.cols;
+}
+
+void Exec::mark_lazy(const View &v) {
+  if (fp32 || v.rows == 0 || v.cols == 0) return;
+  const Rect r = rect_of(v);
+  for (const View &x : lazy_views)
+    if (contains(rect_of(x), r)) return;
+  lazy_views.push_back(v);
+}
+
+void Exec::mark_canonical(const View &v) {
+  if (lazy_views.empty()) return;
+  const Rect r = rect_of(v);
+  lazy_views.erase(std::remove_if(lazy_views.begin(), lazy_views.end(),
+                                  [&](const View &x) { return contains(r, rect_of(x)); }),
+                   lazy_views.end());
 }
 
 static bool any_overlap(const std::vector<Rect> &a, const std::vector<Rect> &b) {
@@ -141,6 +169,12 @@ void Exec::flush() {
   if (!dry) {
     pend.P.nprod = pend.n;
     pend.P.total_tiles = pend.tiles;
+    pend.P.wait_ns = wait_ns;
+    pend.P.test_stall = 0;
+    if (stall_left && *stall_left > 0) {
+      --*stall_left;
+      pend.P.test_stall = 1;
+    }
     flushing = true;
     cudaStream_t st = op_begin(pend.rd, pend.wr);
     flushing = false;
@@ -158,7 +192,13 @@ void Exec::flush() {
 
 char *Exec::next_stage() {
   const int64_t slot = rup(stage_need, 1024);
-  return stage + (stage_turn++ % stage_slots) * slot;
+  const int64_t off = (stage_turn++ % stage_slots) * slot;
+  if (stage_limit >= 0 && off + stage_need > stage_limit) {
+    // the planning pass sized the area: a real run must never need more
+    if (fail.empty()) fail = "operand staging exceeds the planned area";
+    return nullptr;
+  }
+  return stage + off;
 }
 
 // FP32 mode: zero the two amax words at the head of a staging slot, then
@@ -196,6 +236,7 @@ void Exec::fp32_amax(uint32_t *amax, const View *a, int na, const View *b, int n
 void Exec::add(View d, View s1, View s2, Scalar c1, Scalar c2) {
   add_elems += d.rows * d.cols;
   ++ew_launches;
+  mark_canonical(d);
   if (dry) return;
   cudaStream_t st = op_begin({rect_of(s1), rect_of(s2)}, {rect_of(d)});
   if (fp32)
@@ -207,6 +248,7 @@ void Exec::add(View d, View s1, View s2, Scalar c1, Scalar c2) {
 
 void Exec::scale(View d, bool keep, Scalar beta) {
   ++ew_launches;
+  mark_canonical(d);
   if (dry) return;
   cudaStream_t st = op_begin({}, {rect_of(d)});
   if (fp32)
@@ -248,6 +290,20 @@ void Exec::leaf(Scalar alpha, bool acc, Scalar beta, View L, View R, View D) {
     return;
   }
   if (!simt) {
+    const int pl = planes_of(mode);
+    const int64_t per_k = pl * (rup(m, kBM) + rup(n, bn_of(mode))) * 2;  // staging bytes per unit of k
+    const int64_t hdr = fp32 ? 1024 : 0;
+    if (stage_budget > 0 && k > kBK && hdr + per_k * rup(k, kBK) > stage_budget) {
+      // under a staging bound: K-slabs whose operands fit it, each after the
+      // first accumulating into D (D <- alpha L_j R_j + D)
+      const int64_t ks = std::max<int64_t>(kBK, (stage_budget - hdr) / per_k / kBK * kBK);
+      for (int64_t k0 = 0; k0 < k; k0 += ks) {
+        const int64_t kk = std::min(ks, k - k0);
+        const LeafJob job{L.sub(0, k0, m, kk), R.sub(k0, 0, kk, n), D};
+        leaf_group(alpha, k0 == 0 ? acc : true, k0 == 0 ? beta : one(), &job, 1);
+      }
+      return;
+    }
     const LeafJob job{L, R, D};
     leaf_group(alpha, acc, beta, &job, 1);
     return;
@@ -275,6 +331,7 @@ void Exec::leaf(Scalar alpha, bool acc, Scalar beta, View L, View R, View D) {
   S.M = (int)m;
   S.N = (int)n;
   S.K = (int)k;
+  mark_canonical(D);
   cudaStream_t st = op_begin({rect_of(L), rect_of(R)}, {rect_of(D)});
   check(launch_leaf_simt(S, P, mode, st), "simt leaf");
   op_end();
@@ -293,6 +350,33 @@ void Exec::leaf_group(Scalar alpha, bool acc, Scalar beta, const LeafJob *jobs, 
   }
   const int pl = planes_of(mode), bn = bn_of(mode);
   const int64_t hdr = fp32 ? 1024 : 0;  // FP32 mode: the operands' amax words
+  if (stage_budget > 0 && njobs > 1) {
+    // under a staging bound: launches of consecutive problems whose staging
+    // fits it (a problem larger than the bound is staged alone)
+    int64_t bytes[kMaxProducts], total = 0;
+    for (int i = 0; i < njobs; ++i) {
+      const int64_t m = jobs[i].L.rows, k = jobs[i].L.cols, n = jobs[i].R.cols;
+      bytes[i] = hdr + rup(pl * rup(m, kBM) * rup(k, kBK) * 2, 1024) + rup(pl * rup(n, bn) * rup(k, kBK) * 2, 1024);
+      total += bytes[i];
+    }
+    if (total > stage_budget) {
+      const int64_t keep = stage_budget;
+      stage_budget = 0;
+      int first = 0;
+      int64_t sum = 0;
+      for (int i = 0; i < njobs; ++i) {
+        if (i > first && sum + bytes[i] > keep) {
+          leaf_group(alpha, acc, beta, jobs + first, i - first);
+          first = i;
+          sum = 0;
+        }
+        sum += bytes[i];
+      }
+      leaf_group(alpha, acc, beta, jobs + first, njobs - first);
+      stage_budget = keep;
+      return;
+    }
+  }
   int64_t Mp[kMaxProducts], Np[kMaxProducts], Kp[kMaxProducts], ab[kMaxProducts], bb[kMaxProducts],
       off[kMaxProducts];
   int64_t total = 0;
@@ -317,6 +401,7 @@ void Exec::leaf_group(Scalar alpha, bool acc, Scalar beta, const LeafJob *jobs, 
     return;
   }
   char *base = next_stage();
+  if (!base) return;
   GemmParams P;
   fill_common(P, *this, alpha, acc, beta, EPI_STORE);
   std::vector<Rect> grd, gwr;
@@ -335,6 +420,7 @@ void Exec::leaf_group(Scalar alpha, bool acc, Scalar beta, const LeafJob *jobs, 
     pa.src[0][0] = L.ptr;
     pa.ld[0][0] = L.ld;
     pa.tsign[0] = 1;
+    pa.tesz[0] = (int8_t)L.esz;
     pa.nterm = 1;
     pa.nsrc = 1;
     pa.out[0] = Ap;
@@ -352,6 +438,7 @@ void Exec::leaf_group(Scalar alpha, bool acc, Scalar beta, const LeafJob *jobs, 
     PackArgs pb = pa;
     pb.src[0][0] = R.ptr;
     pb.ld[0][0] = R.ld;
+    pb.tesz[0] = (int8_t)R.esz;
     pb.out[0] = Bp;
     pb.rows = (int)k;
     pb.cols = (int)n;
@@ -389,6 +476,7 @@ void Exec::leaf_group(Scalar alpha, bool acc, Scalar beta, const LeafJob *jobs, 
     grd.push_back(rb);
     grd.push_back(rh);
     gwr.push_back(rect_of(D));
+    mark_canonical(D);
   }
   P.nprod = njobs;
   P.total_tiles = tiles;
@@ -434,6 +522,10 @@ void Exec::fused_level(Scalar alpha, bool acc, Scalar beta, const Lin &LL, const
   static const int8_t tgt[7][4] = {
       {1, 1, 1, 1}, {1, 0, 0, 0}, {0, 1, 0, 0}, {0, 0, -1, 0}, {0, 1, 0, 1}, {0, 1, 1, 1}, {0, 0, 1, 1},
   };
+  // Order of the products in a launch: most targets first (P1, P6, P5, P7,
+  // then P2, P3, P4), so the reduce-adds of a launch's last wave, which no
+  // longer overlap any multiplication, are single-target ones.
+  static const int ord[7] = {0, 5, 4, 6, 1, 2, 3};
   const int64_t hm = L.rows / 2, hk = L.cols / 2, hn = R.cols / 2;
   View Dq[4] = {D.quad(0, 0), D.quad(0, 1), D.quad(1, 0), D.quad(1, 1)};
   leaf_flops += 7 * 2 * hm * hn * hk;
@@ -441,7 +533,7 @@ void Exec::fused_level(Scalar alpha, bool acc, Scalar beta, const Lin &LL, const
   // prologue: D <- beta D; nothing when beta = 1, zeros for C <- alpha AB.
   // The products are then added as unreduced representatives (mod p), so D
   // stays lazy until a consumer or the final pass reduces it.
-  lazy = lazy || !fp32;
+  mark_lazy(D);
   const bool keep = acc && (fp32 ? beta.f == 1.f : beta.u == 1u);
   if (!keep) {
     ++ew_launches;
@@ -500,53 +592,74 @@ void Exec::fused_level(Scalar alpha, bool acc, Scalar beta, const Lin &LL, const
     const int64_t Mp = rup(hm, kBM), Np = rup(hn, bn), Kp = rup(hk, kBK);
     const int64_t abytes = rup(pl * Mp * Kp * 2, 1024), bbytes = rup(pl * Np * Kp * 2, 1024);
     const int64_t hdr = fp32 ? 1024 : 0;  // FP32 mode: the operands' amax words
-    stage_need = std::max(stage_need, hdr + 7 * (abytes + bbytes));
-    ew_launches += fp32 ? 2 : 1;
-    if (!dry) {
+    // Products staged and multiplied together: all seven (one pack forms
+    // every operand of the level from one read of the quadrants), or, under
+    // a staging budget, groups of consecutive products whose operands fit it
+    // (each group's pack reads only the quadrants its operands use).
+    int group = 7;
+    if (stage_budget > 0)
+      group = (int)std::max<int64_t>(1, std::min<int64_t>(7, (stage_budget - hdr) / (abytes + bbytes)));
+    const int ngroups = (7 + group - 1) / group;
+    stage_need = std::max(stage_need, hdr + group * (abytes + bbytes));
+    ew_launches += ngroups * (fp32 ? 2 : 1);
+    const double pflops = 2.0 * hm * hn * hk * limb_products();
+    if (dry) {
+      for (int g0 = 0; g0 < 7; g0 += group) queue_gemm(nullptr, {}, {}, true, std::min(group, 7 - g0) * pflops,
+                                                       std::min(group, 7 - g0));
+      return;
+    }
+    // the quadrants of every term of an operand, as pack sources
+    std::vector<Rect> rdA, rdB;
+    for (int t = 0; t < LL.n; ++t) rdA.push_back(rect_of(LL.v[t]));
+    for (int t = 0; t < RL.n; ++t) rdB.push_back(rect_of(RL.v[t]));
+    for (int g0 = 0; g0 < 7; g0 += group) {
+      const int gn = std::min(group, 7 - g0);
       char *base = next_stage();
+      if (!base) return;
       uint32_t *amax = fp32 ? reinterpret_cast<uint32_t *>(base) : nullptr;
       char *stg = base + hdr;
-      const Rect ra = rect_bytes(stg, 7 * abytes), rb = rect_bytes(stg + 7 * abytes, 7 * bbytes);
+      const Rect ra = rect_bytes(stg, gn * abytes), rb = rect_bytes(stg + gn * abytes, gn * bbytes);
       const Rect rh = rect_bytes(base, 8);
       if (fp32) fp32_amax(amax, LL.v, LL.n, RL.v, RL.n);
       PackArgs pa, pb;
       std::memset(&pa, 0, sizeof(pa));
       std::memset(&pb, 0, sizeof(pb));
-      // source q of the pack = quadrant q of every term of the operand
-      std::vector<Rect> rdA{rh}, rdB{rh};
-      for (int t = 0; t < LL.n; ++t) {
-        const View &v = LL.v[t];
-        const View qd[4] = {v.quad(0, 0), v.quad(0, 1), v.quad(1, 0), v.quad(1, 1)};
+      // sources: the quadrants the group's operands use (all four for a
+      // whole level), each the signed sum of that quadrant of every term
+      auto sources = [&](const Lin &LIN, const int8_t (*cf)[4], PackArgs &pk) {
+        int map[4], ns = 0;
         for (int q = 0; q < 4; ++q) {
-          pa.src[q][t] = qd[q].ptr;
-          pa.ld[q][t] = qd[q].ld;
+          bool used = false;
+          for (int i = g0; i < g0 + gn; ++i) used = used || cf[ord[i]][q] != 0;
+          map[q] = used ? ns++ : -1;
+          if (!used) continue;
+          for (int t = 0; t < LIN.n; ++t) {
+            const View qd = LIN.v[t].quad(q / 2, q % 2);
+            pk.src[map[q]][t] = qd.ptr;
+            pk.ld[map[q]][t] = qd.ld;
+          }
         }
-        pa.tsign[t] = LL.s[t];
-        rdA.push_back(rect_of(v));
-      }
-      for (int t = 0; t < RL.n; ++t) {
-        const View &v = RL.v[t];
-        const View qd[4] = {v.quad(0, 0), v.quad(0, 1), v.quad(1, 0), v.quad(1, 1)};
-        for (int q = 0; q < 4; ++q) {
-          pb.src[q][t] = qd[q].ptr;
-          pb.ld[q][t] = qd[q].ld;
+        for (int t = 0; t < LIN.n; ++t) {
+          pk.tsign[t] = LIN.s[t];
+          pk.tesz[t] = (int8_t)LIN.v[t].esz;
         }
-        pb.tsign[t] = RL.s[t];
-        rdB.push_back(rect_of(v));
-      }
-      pa.nterm = LL.n;
-      pb.nterm = RL.n;
-      pa.nsrc = pb.nsrc = 4;
-      pa.nout = pb.nout = 7;
-      pa.set = PACK_WINOGRAD_A;  // the chains of acoef / bcoef, formed once per element
-      pb.set = PACK_WINOGRAD_B;
-      for (int i = 0; i < 7; ++i) {
-        pa.out[i] = reinterpret_cast<uint16_t *>(stg + i * abytes);
-        pb.out[i] = reinterpret_cast<uint16_t *>(stg + 7 * abytes + i * bbytes);
-        for (int q = 0; q < 4; ++q) {
-          pa.coef[i][q] = acoef[i][q];
-          pb.coef[i][q] = bcoef[i][q];
-        }
+        pk.nterm = LIN.n;
+        pk.nsrc = ns;
+        pk.nout = gn;
+        for (int j = 0; j < gn; ++j)
+          for (int q = 0; q < 4; ++q)
+            if (map[q] >= 0) pk.coef[j][map[q]] = cf[ord[g0 + j]][q];
+      };
+      sources(LL, acoef, pa);
+      sources(RL, bcoef, pb);
+      // a whole level forms the chains S2 = S1 - A11, S4 = A12 - S2 and
+      // T2 = B22 - T1, T4 = T2 - B21 once per element, output i holding
+      // product i; a group's generic pack writes its products in launch order
+      pa.set = gn == 7 ? PACK_WINOGRAD_A : PACK_GENERIC;
+      pb.set = gn == 7 ? PACK_WINOGRAD_B : PACK_GENERIC;
+      for (int j = 0; j < gn; ++j) {
+        pa.out[j] = reinterpret_cast<uint16_t *>(stg + j * abytes);
+        pb.out[j] = reinterpret_cast<uint16_t *>(stg + gn * abytes + j * bbytes);
       }
       pa.rows = (int)hm;
       pa.cols = (int)hk;
@@ -567,15 +680,18 @@ void Exec::fused_level(Scalar alpha, bool acc, Scalar beta, const Lin &LL, const
       pb.amax = amax ? amax + 1 : nullptr;
       pa.terms = 4 * LL.n;
       pb.terms = 4 * RL.n;
-      std::vector<Rect> rdAB = rdA;
+      std::vector<Rect> rdAB{rh};
+      rdAB.insert(rdAB.end(), rdA.begin(), rdA.end());
       rdAB.insert(rdAB.end(), rdB.begin(), rdB.end());
       cudaStream_t st = op_begin(rdAB, {ra, rb});
       check(launch_pack_pair(pa, pb, mode, st), "fused pack");
       op_end();
       int tiles = 0;
-      for (int i = 0; i < 7; ++i) {
-        Product &pr = P.prod[i];
-        if (!make_tmap(&pr.ta, pa.out[i], pl * Mp, Kp, kBM) || !make_tmap(&pr.tb, pb.out[i], pl * Np, Kp, bn)) {
+      for (int j = 0; j < gn; ++j) {
+        const int i = ord[g0 + j];              // the product in launch slot j
+        const int o = gn == 7 ? i : j;          // its pack output
+        Product &pr = P.prod[j];
+        if (!make_tmap(&pr.ta, pa.out[o], pl * Mp, Kp, kBM) || !make_tmap(&pr.tb, pb.out[o], pl * Np, Kp, bn)) {
           if (fail.empty()) fail = "tensor map encoding failed";
           return;
         }
@@ -605,11 +721,9 @@ void Exec::fused_level(Scalar alpha, bool acc, Scalar beta, const Lin &LL, const
         set_scalars(pr, alpha, false, beta, EPI_REDUCE);
         tiles += pr.tiles_m * pr.tiles_n;
       }
-      P.nprod = 7;
+      P.nprod = gn;
       P.total_tiles = tiles;
-      queue_gemm(&P, {ra, rb, rh}, {rect_of(D)}, true, 7 * 2.0 * hm * hn * hk * limb_products(), 7);
-    } else {
-      queue_gemm(nullptr, {}, {}, true, 7 * 2.0 * hm * hn * hk * limb_products(), 7);
+      queue_gemm(&P, {ra, rb, rh}, {rect_of(D)}, true, gn * pflops, gn);
     }
   }
 }
@@ -704,7 +818,15 @@ void Exec::table(Kind k, Scalar alpha, bool acc, Scalar beta, View L, View R, Vi
   loc[LX] = tmp[0];
   loc[LY] = tmp[1];
   loc[LZ] = tmp[2];
-  auto at = [&](Loc l, Shape s) -> View {
+  // 16-bit temporaries.  Over Z/pZ (p < 2^16) a value a row writes into a
+  // temporary and that is an operand of a product (an S or T value, never
+  // a C-shaped one) is stored as 16-bit [0, p) in the temporary's storage,
+  // halving its traffic.  Only where every product of this level is a fused
+  // level: a table call below could overwrite its operand blocks with
+  // C-shaped values (Tables 3-8), which need 32 bits.
+  const bool narrow_ok = !fp32 && !simt && fuses(hm, hk, hn, depth - 1);
+  bool nar[NLOC] = {};  // the value a temporary holds is stored as 16-bit
+  auto at_as = [&](Loc l, Shape s, bool narrow) -> View {
     int64_t r, c;
     dims(s, r, c);
     const View &v = loc[l];
@@ -712,8 +834,11 @@ void Exec::table(Kind k, Scalar alpha, bool acc, Scalar beta, View L, View R, Vi
       if (fail.empty()) fail = std::string(K.name) + ": value does not fit its location (shape precondition)";
       return v;
     }
-    return v.sub(0, 0, r, c);
+    return narrow ? v.narrow().sub(0, 0, r, c) : v.sub(0, 0, r, c);
   };
+  auto at = [&](Loc l, Shape s) -> View { return at_as(l, s, nar[l]); };
+  // representation of a new value of shape s written into l
+  auto narrow_for = [&](Loc l, Shape s) { return narrow_ok && (l == LX || l == LY || l == LZ) && s != SH_C; };
   auto coef = [&](Coef c) -> Scalar {
     switch (c) {
       case CF_ONE: return one();
@@ -769,7 +894,7 @@ void Exec::table(Kind k, Scalar alpha, bool acc, Scalar beta, View L, View R, Vi
     }
   };
   auto same = [](const View &x, const View &y) {
-    return x.ptr == y.ptr && x.ld == y.ld && x.rows == y.rows && x.cols == y.cols;
+    return x.ptr == y.ptr && x.ld == y.ld && x.rows == y.rows && x.cols == y.cols && x.esz == y.esz;
   };
   // c1 x + c2 y as a Lin of at most kMaxTerm unit-coefficient terms
   auto compose = [&](const Lin &x, int c1, const Lin &y, int c2, Lin &r) {
@@ -802,7 +927,10 @@ void Exec::table(Kind k, Scalar alpha, bool acc, Scalar beta, View L, View R, Vi
   for (const Row &row : *K.table) {
     if (!ok()) return;
     if (row.op == OP_ADD) {
-      const View d = at(row.dst, row.shape), a = at(row.s1, row.shape), b = at(row.s2, row.shape);
+      const View a = at(row.s1, row.shape), b = at(row.s2, row.shape);
+      const bool nd = narrow_for(row.dst, row.shape);
+      const View d = at_as(row.dst, row.shape, nd);
+      nar[row.dst] = nd;
       bool recorded = false;
       const bool unit = (row.c1 == CF_ONE || row.c1 == CF_NEG) && (row.c2 == CF_ONE || row.c2 == CF_NEG);
       if (virt && unit && is_tmp(row.dst) && row.shape != SH_C &&
@@ -824,21 +952,34 @@ void Exec::table(Kind k, Scalar alpha, bool acc, Scalar beta, View L, View R, Vi
         add(d, a, b, coef(row.c1), coef(row.c2));
       }
     } else if (row.op == OP_COPY) {
-      View d = at(row.dst, row.shape);
       const View src = at(row.s1, row.shape);
+      const bool nd = narrow_for(row.dst, row.shape);
+      View d = at_as(row.dst, row.shape, nd);
+      nar[row.dst] = nd;
       materialize(row.s1);
       before_write(d);
       has[row.dst] = false;
       ++ew_launches;
       add_elems += d.rows * d.cols;
+      {  // a copy keeps the source's representatives
+        bool src_lazy = false;
+        for (const View &x : lazy_views)
+          if (overlaps(rect_of(x), rect_of(src))) src_lazy = true;
+        if (src_lazy)
+          mark_lazy(d);
+        else
+          mark_canonical(d);
+      }
       if (!dry) {
         cudaStream_t st = op_begin({rect_of(src)}, {rect_of(d)});
-        check(launch_copy(d, src, st), "copy");
+        check(launch_copy(d, src, p, st), "copy");
         op_end();
       }
     } else {
       const KindInfo &S = info(row.kind);
-      const View a = at(row.s1, SH_A), b = at(row.s2, SH_B), d = at(row.dst, SH_C);
+      const View a = at(row.s1, SH_A), b = at(row.s2, SH_B);
+      nar[row.dst] = false;  // a product is C-shaped: 32-bit
+      const View d = at(row.dst, SH_C);
       const Scalar al = coef(row.c1), be = row.acc ? coef(row.cacc) : Scalar{};
       before_write(d);
       if (virt) {
@@ -954,6 +1095,7 @@ void Exec::copy_out(char *host, int64_t hld, View dv, const Rect &token) {
 
 void Exec::canon(View v) {
   ++ew_launches;
+  mark_canonical(v);
   if (dry || v.rows == 0 || v.cols == 0) return;
   cudaStream_t st = op_begin({}, {rect_of(v)});
   check(launch_canon_modp(v, p, st), "canonical pass");

@@ -65,19 +65,26 @@ struct Exec {
   cudaStream_t stream = nullptr;
   int num_sms = 152;
   int *err = nullptr;
+  uint64_t wait_ns = 4000000000ull;  // bound of the GEMM's device-side waits
+  int *stall_left = nullptr;         // test hook: GEMM launches still to stall (handle counter)
   TimingHook *timing = nullptr;
   // the handle's own schedule (K_CUSTOM), if any
   const KindInfo *custom = nullptr;
   const KindInfo &info(Kind k) const { return k == K_CUSTOM ? *custom : kind_info(k); }
 
-  // workspace for temporaries (bump allocator, bytes)
+  // workspace for temporaries (bump allocator, bytes); ws_limit >= 0 is the
+  // size of the area given to a real run (a temporary past it fails the
+  // call instead of writing beyond the area)
   char *ws = nullptr;
-  int64_t ws_top = 0, ws_peak = 0;
+  int64_t ws_top = 0, ws_peak = 0, ws_limit = -1;
   // tensor-core operand staging (bytes): stage_slots areas of stage_need
   // bytes used in turn by successive leaf launches (two under a Flow, so
   // the next leaf's operands are packed while the current one multiplies)
   char *stage = nullptr;
-  int64_t stage_need = 0;
+  int64_t stage_need = 0, stage_limit = -1;  // stage_limit >= 0: bytes of the area at `stage`
+  // > 0: operand staging bound (SWMM_FLAG_LOWMEM); products of a fused level
+  // or of a leaf group are staged and multiplied in groups that fit it
+  int64_t stage_budget = 0;
   int stage_slots = 1;
   int stage_turn = 0;
   // dataflow ordering over capture streams (null: every launch on `stream`)
@@ -102,7 +109,12 @@ struct Exec {
   int64_t tmp_elems = 0, tmp_peak_elems = 0;
   int64_t add_elems = 0, leaf_flops = 0, leaf_launches = 0, ew_launches = 0, leaf_products = 0;
 
-  bool lazy = false;  // some destination holds unreduced representatives (mod p)
+  // Blocks holding unreduced representatives mod p (destinations of a fused
+  // level's reduce-adds) that no later operation has brought back to
+  // [0, p); only these need the final canonical pass.
+  std::vector<View> lazy_views;
+  void mark_lazy(const View &v);
+  void mark_canonical(const View &v);  // every element of v is now in [0, p)
 
   cudaError_t cuda_err = cudaSuccess;
   std::string fail;  // first failure description

@@ -8,14 +8,16 @@ namespace swmm {
 Rect rect_of(const View &v) {
   Rect r;
   r.base = v.base ? v.base : v.ptr;
-  r.ld = v.ld;
-  const int64_t off = (int64_t)(v.ptr - r.base) / 4;
+  // 16-bit views get their own leading dimension (twice the 32-bit one), so
+  // against 32-bit views of the same root only their byte spans are compared
+  r.ld = v.esz == 4 ? v.ld : -v.ld;
+  const int64_t off = (int64_t)(v.ptr - r.base) / v.esz;
   r.r0 = v.ld > 0 ? off / v.ld : 0;
   r.c0 = v.ld > 0 ? off % v.ld : off;
   r.rows = v.rows;
   r.cols = v.cols;
   r.lo = (uintptr_t)v.ptr;
-  r.hi = (v.rows > 0 && v.cols > 0) ? r.lo + 4 * (uintptr_t)((v.rows - 1) * v.ld + v.cols) : r.lo;
+  r.hi = (v.rows > 0 && v.cols > 0) ? r.lo + v.esz * (uintptr_t)((v.rows - 1) * v.ld + v.cols) : r.lo;
   return r;
 }
 
@@ -31,7 +33,7 @@ Rect rect_bytes(const void *p, int64_t bytes) {
 bool overlaps(const Rect &a, const Rect &b) {
   if (a.lo >= a.hi || b.lo >= b.hi) return false;
   if (a.hi <= b.lo || b.hi <= a.lo) return false;
-  if (a.base == b.base && a.ld == b.ld && a.ld > 0)
+  if (a.base == b.base && a.ld == b.ld && a.ld != 0)
     return a.r0 < b.r0 + b.rows && b.r0 < a.r0 + a.rows && a.c0 < b.c0 + b.cols && b.c0 < a.c0 + a.cols;
   return true;
 }

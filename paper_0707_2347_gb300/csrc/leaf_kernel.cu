@@ -216,11 +216,39 @@ __device__ __forceinline__ void emit_all(const PackArgs &a, const uint32_t (&v)[
   }
 }
 
-// n consecutive elements (n = 8 or 4) of row r from column c of one block;
-// 0 outside rows x cols; 16-byte loads when aligned
+// n consecutive elements (n = 8 or 4) of row r from column c of one block of
+// 32-bit (esz 4) or 16-bit (esz 2) elements; 0 outside rows x cols; vector
+// loads when aligned
 template <int N>
-__device__ __forceinline__ void load_row(const char *blk, int64_t ld, int r, int c, int rows, int cols, uint32_t *w) {
-  const char *base = blk + 4 * ((int64_t)r * ld + c);
+__device__ __forceinline__ void load_row(const char *blk, int64_t ld, int r, int c, int rows, int cols, uint32_t *w,
+                                         int esz) {
+  const char *base = blk + esz * ((int64_t)r * ld + c);
+  if (esz == 2) {
+    if (r < rows && c + N <= cols && ((uintptr_t)base & (2 * N - 1)) == 0) {
+      uint32_t h[N / 2];
+      if constexpr (N == 8) {
+        const uint4 x = *reinterpret_cast<const uint4 *>(base);
+        h[0] = x.x;
+        h[1] = x.y;
+        h[2] = x.z;
+        h[3] = x.w;
+      } else {
+        const uint2 x = *reinterpret_cast<const uint2 *>(base);
+        h[0] = x.x;
+        h[1] = x.y;
+      }
+#pragma unroll
+      for (int i = 0; i < N / 2; ++i) {
+        w[2 * i] = h[i] & 0xFFFFu;
+        w[2 * i + 1] = h[i] >> 16;
+      }
+    } else {
+#pragma unroll
+      for (int e = 0; e < N; ++e)
+        w[e] = (r < rows && c + e < cols) ? (uint32_t) reinterpret_cast<const uint16_t *>(base)[e] : 0u;
+    }
+    return;
+  }
   if (r < rows && c + N <= cols && ((uintptr_t)base & 15) == 0) {
 #pragma unroll
     for (int i = 0; i < N / 4; ++i) {
@@ -239,7 +267,7 @@ __device__ __forceinline__ void load_row(const char *blk, int64_t ld, int r, int
 // source q at (r, c..c+N): sum_t tsign[t] * term t, every term reduced first
 template <int MODE, int N>
 __device__ __forceinline__ void load_source(const PackArgs &a, int q, int r, int c, uint32_t *v) {
-  load_row<N>(a.src[q][0], a.ld[q][0], r, c, a.rows, a.cols, v);
+  load_row<N>(a.src[q][0], a.ld[q][0], r, c, a.rows, a.cols, v, a.tesz[0]);
 #pragma unroll
   for (int e = 0; e < N; ++e) v[e] = source_value<MODE>(v[e], a.p, a.barrett);
   if (a.nterm == 1 && a.tsign[0] > 0) return;  // one plain block (every launch but symbolic sums)
@@ -249,7 +277,7 @@ __device__ __forceinline__ void load_source(const PackArgs &a, int q, int r, int
   }
   for (int t = 1; t < a.nterm; ++t) {
     uint32_t w[N];
-    load_row<N>(a.src[q][t], a.ld[q][t], r, c, a.rows, a.cols, w);
+    load_row<N>(a.src[q][t], a.ld[q][t], r, c, a.rows, a.cols, w, a.tesz[t]);
 #pragma unroll
     for (int e = 0; e < N; ++e) {
       const uint32_t x = source_value<MODE>(w[e], a.p, a.barrett);
@@ -370,7 +398,6 @@ __global__ void __launch_bounds__(256) amax_kernel(const __grid_constant__ AmaxA
 constexpr int kThreads = 320;                 // producer, MMA, 8 epilogue warps
 constexpr int kEpiThreads = 256;
 constexpr int kChunkKB = 15;                  // k-blocks between in-place reductions
-constexpr uint64_t kWaitNs = 4000000000ull;  // bounded wait: 4 s
 constexpr int kPlaneBytes = kBM * kBK * 2;    // 16 KB
 constexpr int kEpiBytes = 2 * kBM * 32 * 4;   // 32 KB: 128 rows x 64 columns, 2 boxes of 32
 
@@ -429,8 +456,12 @@ __device__ __forceinline__ uint64_t gtime() {
 struct Ctl {
   volatile int abort;
   uint32_t tmem_base;
+  uint64_t wait_ns;  // bound of every wait
 };
 
+// Wait for phase `parity` of barrier b.  Gives up when another warp of the
+// CTA has aborted, or after ctl->wait_ns (then it aborts the CTA and records
+// SWMM_ETIMEOUT in the error word).
 __device__ __forceinline__ bool wait_bar(uint64_t *b, uint32_t parity, Ctl *ctl, int *err) {
   if (mbar_try(b, parity)) return true;
   const uint64_t t0 = gtime();
@@ -438,7 +469,7 @@ __device__ __forceinline__ bool wait_bar(uint64_t *b, uint32_t parity, Ctl *ctl,
     if (mbar_try(b, parity)) return true;
     if ((it & 63) == 63) {
       if (ctl->abort) return false;
-      if (gtime() - t0 > kWaitNs) {
+      if (gtime() - t0 > ctl->wait_ns) {
         ctl->abort = 1;
         if (err) atomicExch(err, kErrTimeout);
         return false;
@@ -446,8 +477,35 @@ __device__ __forceinline__ bool wait_bar(uint64_t *b, uint32_t parity, Ctl *ctl,
     }
   }
 }
+// Wait for work this CTA already issued (TMA loads, MMAs) to land before it
+// exits, whether or not the CTA has aborted; bounded by ctl->wait_ns too.
+__device__ __forceinline__ void wait_done(uint64_t *b, uint32_t parity, Ctl *ctl, int *err) {
+  if (mbar_try(b, parity)) return;
+  const uint64_t t0 = gtime();
+  for (uint32_t it = 0;; ++it) {
+    if (mbar_try(b, parity)) return;
+    if ((it & 63) == 63 && gtime() - t0 > ctl->wait_ns) {
+      ctl->abort = 1;
+      if (err) atomicExch(err, kErrTimeout);
+      return;
+    }
+  }
+}
 
 __device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kEpiThreads) : "memory"); }
+// Epilogue barrier that also agrees on the abort flag: true on every
+// epilogue thread when no thread saw it set, false on every thread
+// otherwise, so all of them take the same path to the next barrier.
+__device__ __forceinline__ bool epi_agree(const Ctl *ctl) {
+  uint32_t ok;
+  const uint32_t mine = ctl->abort ? 0u : 1u;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.and.pred q, 1, %2, p;\n selp.u32 %0, 1, 0, q;\n}"
+      : "=r"(ok)
+      : "r"(mine), "n"(kEpiThreads)
+      : "memory");
+  return ok != 0;
+}
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
@@ -630,11 +688,11 @@ __device__ __forceinline__ void modp_finish(const Product &pr, const Epi &E, int
 
 // p < 2^16, one accumulator buffer, released in two halves: columns
 // [0, 2 BN) hold hh | hl and [2 BN, 4 BN) hold lh | ll.  First every
-// X = fr(2^8 fr(hh) + fr(hl)) of the thread's 64 columns is formed and the
-// first half released (the next tile's A_h products may start), then
-// v = fr(2^8 fr(X + fr(lh)) + fr(ll)) = 2^16 hh + 2^8 (hl + lh) + ll mod p
-// and the second half released.  Every intermediate is an exact fp32
-// integer (below 2^24).
+// X = 2^8 fr(hh) + fr(hl) of the thread's 64 columns is formed (|X| <
+// 2^23 + 2^15) and the first half released (the next tile's A_h products
+// may start), then v = fr(2^8 fr(X + fr(lh)) + fr(ll)) = 2^16 hh + 2^8 (hl +
+// lh) + ll mod p and the second half released.  Every intermediate is an
+// exact fp32 integer (below 2^24).
 __device__ __forceinline__ void modp2_drain_split(const Product &pr, const Epi &E, uint32_t d, int hsel, int sign,
                                                   uint32_t (&vals)[2][32], uint64_t *half0, uint64_t *half1) {
   float X[4][16];
@@ -648,7 +706,7 @@ __device__ __forceinline__ void modp2_drain_split(const Product &pr, const Epi &
     reg_fence16(a);
     reg_fence16(b);
 #pragma unroll
-    for (int e = 0; e < 16; ++e) X[g][e] = E.fr(__fmaf_rn(256.f, E.fr(a[e]), E.fr(b[e])));
+    for (int e = 0; e < 16; ++e) X[g][e] = __fmaf_rn(256.f, E.fr(a[e]), E.fr(b[e]));
   }
   tc_fence_before();
   mbar_arrive(half0);
@@ -742,8 +800,9 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_kernel(const __grid_constant
   uint64_t *drain_full = acc_empty + 2;
   uint64_t *drain_empty = drain_full + 1;
   uint64_t *final_bar = drain_empty + 1;
-  uint64_t *cbar = final_bar + 1;  // beta source tile loaded
-  Ctl *ctl = reinterpret_cast<Ctl *>(cbar + 1);
+  uint64_t *cbar = final_bar + 1;       // beta source tile loaded
+  uint64_t *stall_bar = cbar + 1;       // test hook: nothing ever arrives here
+  Ctl *ctl = reinterpret_cast<Ctl *>(stall_bar + 1);
 
   const int tid = threadIdx.x;
   const int warp = tid >> 5;
@@ -762,7 +821,9 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_kernel(const __grid_constant
     mbar_init(drain_empty, kEpiThreads);
     mbar_init(final_bar, 1);
     mbar_init(cbar, 1);
+    mbar_init(stall_bar, 1);
     ctl->abort = 0;
+    ctl->wait_ns = P.wait_ns;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) {
@@ -779,7 +840,10 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_kernel(const __grid_constant
     if (lane == 0) {
       int stage = 0;
       uint32_t phase = 0;
-      for (int g = blockIdx.x; g < P.total_tiles; g += gridDim.x) {
+      uint32_t issued = 0, last_phase = 0;  // per stage: a load was issued; its phase parity
+      // test hook: a wait that nothing completes runs out (SWMM_ETIMEOUT)
+      const bool stalled = P.test_stall && !wait_bar(stall_bar, 0, ctl, P.err);
+      for (int g = blockIdx.x; g < P.total_tiles && !stalled; g += gridDim.x) {
         const TileInfo ti = decode<BN>(P, g);
         const Product &pr = P.prod[ti.pi];
         const int nkb = pr.Kpad / kBK;
@@ -792,6 +856,8 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_kernel(const __grid_constant
           const uint32_t sA = smem_u32(smem + stage * SB);
           const uint32_t sB = sA + C::A_PLANES * kPlaneBytes;
           mbar_expect_tx(&full[stage], SB);
+          issued |= 1u << stage;
+          last_phase = (last_phase & ~(1u << stage)) | (phase << stage);
           const int k0 = kb * kBK;
           tma_load(sA, &pr.ta, k0, ti.m0, &full[stage]);
           if (C::A_PLANES == 2) tma_load(sA + kPlaneBytes, &pr.ta, k0, pr.a_plane_rows + ti.m0, &full[stage]);
@@ -808,6 +874,10 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_kernel(const __grid_constant
         }
         if (bad) break;
       }
+      // no load may still be writing shared memory when the CTA exits (after
+      // an abort some were never consumed)
+      for (int st = 0; st < C::STAGES; ++st)
+        if (issued >> st & 1) wait_done(&full[st], last_phase >> st & 1, ctl, P.err);
     }
     __syncwarp();
   } else if (warp == 1) {
@@ -918,7 +988,7 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_kernel(const __grid_constant
         tc_commit(&acc_full[buf]);
       }
       tc_commit(final_bar);  // no MMA may still run when the allocation is freed
-      wait_bar(final_bar, 0, ctl, nullptr);
+      wait_done(final_bar, 0, ctl, P.err);
     }
     __syncwarp();
   } else {
@@ -962,8 +1032,7 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_kernel(const __grid_constant
         const int ndrain = (nkb - 1) / kChunkKB;
         for (int q = 0; q < ndrain; ++q, ++dcount) {
           wait_bar(drain_full, dcount & 1, ctl, P.err);
-          epi_sync();  // every epilogue thread takes the same exit on a timeout
-          if (ctl->abort) {
+          if (!epi_agree(ctl)) {  // every epilogue thread takes the same exit
             bad = true;
             break;
           }
@@ -986,8 +1055,7 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_kernel(const __grid_constant
         if (bad) break;
       }
       wait_bar(&acc_full[buf], use & 1, ctl, P.err);
-      epi_sync();
-      if (ctl->abort) break;
+      if (!epi_agree(ctl)) break;
       tc_fence_after();
       constexpr int NCH = BN / 64;
       // With a single accumulator buffer the next tile's MMAs wait for this
@@ -1037,7 +1105,7 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_kernel(const __grid_constant
           }
           epi_sync();
           if (with_beta) {
-            wait_bar(cbar, cphase, ctl, P.err);
+            wait_done(cbar, cphase, ctl, P.err);  // the load lands even after an abort
             cphase ^= 1;
           }
           const uint32_t rowbase = eb + hsel * 16384 + row * 128;
@@ -1055,8 +1123,7 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_kernel(const __grid_constant
             sts128(a, w);
           }
           fence_proxy_async();
-          epi_sync();
-          if (ctl->abort) {
+          if (!epi_agree(ctl)) {
             bad = true;
             break;
           }

@@ -369,11 +369,13 @@ inline uint64_t mix(uint64_t x) {  // splitmix64 finaliser
 // block additions of the path it was last expanded on.  A state reached
 // again is expanded again unless that path had no more rows and no more
 // additions (then every continuation was already tried within the limits).
-// The table starts small and doubles up to the state limit.
+// The table starts small and doubles up to the state limit; it never holds
+// more than the limit's number of states.
 class Visited {
  public:
   bool init(int64_t max_states) {
     size_ = 0;
+    limit_ = (uint64_t)std::max<int64_t>(max_states, 1);
     max_cap_ = 1;
     while (max_cap_ < 2 * (uint64_t)max_states) max_cap_ <<= 1;
     return alloc(std::min<uint64_t>(max_cap_, 1u << 16));
@@ -389,7 +391,7 @@ class Visited {
     for (uint64_t i = h1 & (cap_ - 1);; i = (i + 1) & (cap_ - 1)) {
       const Slot &s = tab_[i];
       if (s.h1 == 0) {
-        if (size_ * 2 >= cap_) {
+        if (size_ * 2 >= cap_ || size_ >= limit_) {
           *full = true;
           return -1;
         }
@@ -440,7 +442,7 @@ class Visited {
     return true;
   }
   std::vector<Slot> tab_;
-  uint64_t cap_ = 0, max_cap_ = 0, size_ = 0;
+  uint64_t cap_ = 0, max_cap_ = 0, size_ = 0, limit_ = 1;
 };
 
 class Search {

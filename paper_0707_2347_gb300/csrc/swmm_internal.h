@@ -11,12 +11,15 @@ namespace swmm {
 
 constexpr int kErrTimeout = 5;  // matches SWMM_ETIMEOUT
 
-// A strided 2-D block of 32-bit elements (int32 mod p or float).
+// A strided 2-D block of 32-bit elements (int32 mod p or float), or of
+// 16-bit elements (esz = 2: values in [0, p) of a schedule temporary over
+// Z/pZ with p < 2^16).
 struct View {
   char *ptr = nullptr;
   int64_t rows = 0, cols = 0, ld = 0;  // ld in elements
   char *base = nullptr;                // root of the matrix the view was cut from (null: ptr)
-  char *at(int64_t r, int64_t c) const { return ptr + 4 * (r * ld + c); }
+  int esz = 4;                         // bytes per element
+  char *at(int64_t r, int64_t c) const { return ptr + esz * (r * ld + c); }
   View sub(int64_t r0, int64_t c0, int64_t nr, int64_t nc) const {
     View v;
     v.base = base ? base : ptr;
@@ -24,6 +27,18 @@ struct View {
     v.rows = nr;
     v.cols = nc;
     v.ld = ld;
+    v.esz = esz;
+    return v;
+  }
+  // the same rows as 16-bit elements: same row pitch in bytes, each row's
+  // values in the first half of its bytes (so a view carved from a larger
+  // block stays inside that block)
+  View narrow() const {
+    View v = *this;
+    if (esz == 4) {
+      v.esz = 2;
+      v.ld = 2 * ld;
+    }
     return v;
   }
   // quadrant (i, j) in {0,1}^2 of an even-sized block (Section 2 split)
@@ -62,6 +77,7 @@ struct PackArgs {
   const char *src[kMaxSrc][kMaxTerm];
   int64_t ld[kMaxSrc][kMaxTerm];
   int8_t tsign[kMaxTerm];
+  int8_t tesz[kMaxTerm];  // bytes per element of each term's blocks: 4, or 2 (16-bit mod p values)
   int32_t nterm;  // >= 1
   int32_t nsrc;
   uint16_t *out[kMaxOut];
@@ -143,6 +159,8 @@ struct GemmParams {
   float inv_p;       // 1/p rounded to float
   int32_t use_beta;  // STORE: read T0 and add beta * T0
   int *err;          // device error word (bounded waits)
+  uint64_t wait_ns;  // bound of every mbarrier wait (globaltimer ns)
+  int32_t test_stall;  // test hook: the producer first waits on a barrier nothing arrives at
 };
 static_assert(sizeof(GemmParams) <= 32764, "kernel parameter space");
 
@@ -209,7 +227,7 @@ cudaError_t launch_canon_modp(View dst, uint32_t p, cudaStream_t s);
 // dst <- 0
 cudaError_t launch_zero(View dst, cudaStream_t s);
 // dst <- src
-cudaError_t launch_copy(View dst, View src, cudaStream_t s);
+cudaError_t launch_copy(View dst, View src, uint32_t p, cudaStream_t s);
 
 // ------------------------------------------------------- residual probe
 // y = M x for a row-major rows x cols matrix (mod p: int32 elements, uint32

@@ -16,6 +16,7 @@ LIB_PATH = os.path.join(HERE, "_lib", "libswmm.so")
 
 # return codes
 OK, EINVAL, ENOMEM, EUNSUPPORTED, ECUDA, ETIMEOUT = range(6)
+HOOK_WAIT_NS, HOOK_STALL_GEMMS, HOOK_FAIL_ALLOCS, HOOK_LOWMEM_BYTES = 1, 2, 3, 4  # swmm_test_hook
 # modes
 MODP, FP32 = 0, 1
 # schedules (paper table numbers)
@@ -26,7 +27,8 @@ SCHED_NAMES = {CLASSICAL: "classical", T1_DHSS: "T1", T2_HLJJTT: "T2", T3_IP: "I
                T5_OVR: "OvR", T6_ACLR: "AcLR", T7_ACCR: "AccR", T8_ACR: "AcR", T9_ACC: "Acc",
                IPMM: "IPMM", T4M_OVL: "OvLM", IP0VMM: "IP0vMM", TBLOCK: "Sec7.2", CUSTOM: "custom"}
 # flags
-FLAG_UNFUSED, FLAG_SIMT_LEAF, FLAG_TIMING, FLAG_GRAPH, FLAG_SERIAL = 1, 2, 4, 8, 16
+FLAG_UNFUSED, FLAG_SIMT_LEAF, FLAG_TIMING, FLAG_GRAPH, FLAG_SERIAL, FLAG_LOWMEM = 1, 2, 4, 8, 16, 32
+LOWMEM_STAGE_BYTES = 64 << 20
 
 
 class SwmmError(RuntimeError):
@@ -63,6 +65,7 @@ EXPORTS = ["swmm_create", "swmm_destroy", "swmm_set_stream", "swmm_mul", "swmm_m
            "swmm_mul_inplace",
            "swmm_muladd_batched", "swmm_autotune", "swmm_workspace_elems", "swmm_leaf_timing", "swmm_get_stats",
            "swmm_sync", "swmm_strerror", "swmm_last_error", "swmm_matvec", "swmm_residual", "swmm_muladd_host",
+           "swmm_test_hook", "swmm_memory_use",
            # include/swmm_search.h (host only, see search.py)
            "swmm_schedule_search", "swmm_schedule_check", "swmm_search_node_name", "swmm_search_node_count",
            "swmm_set_schedule", "swmm_schedule_workspace", "swmm_table_rows"]
@@ -99,6 +102,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.swmm_leaf_timing.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64),
                                      ctypes.POINTER(ctypes.c_double)]
     lib.swmm_sync.argtypes = [vp]
+    lib.swmm_test_hook.argtypes = [vp, ctypes.c_int32, i64]
+    lib.swmm_memory_use.argtypes = [vp, ctypes.c_int, ctypes.POINTER(i64)]
     lib.swmm_matvec.argtypes = [vp, i64, i64, cvp, i64, cvp, vp, ctypes.POINTER(_Opts)]
     lib.swmm_muladd_host.argtypes = [vp, i64, i64, i64, cvp, cvp, i64, cvp, i64, cvp, vp, i64,
                                      ctypes.POINTER(_Opts)]
@@ -332,3 +337,31 @@ class Handle:
 
     def sync(self):
         self._check(self.lib.swmm_sync(self.h))
+
+    def memory_use(self, reset: bool = False):
+        """(pool_current, pool_high, graph_current, graph_high) in bytes
+        (swmm_memory_use); reset sets both high-water marks to the current use."""
+        out = (ctypes.c_int64 * 4)()
+        self._check(self.lib.swmm_memory_use(self.h, 1 if reset else 0, out))
+        return tuple(out)
+
+    def measure_peak(self):
+        """Context manager: .peak = the largest rise of device memory (default
+        pool or graph memory) above its use at entry, while inside."""
+        handle = self
+
+        class _Peak:
+            def __enter__(self):
+                self.start = handle.memory_use(reset=True)
+                return self
+
+            def __exit__(self, *exc):
+                if exc[0] is None:
+                    end = handle.memory_use()
+                    self.peak = max(end[1] - self.start[0], end[3] - self.start[2], 0)
+
+        return _Peak()
+
+    def test_hook(self, hook: int, value: int):
+        """Failure injection for error-path tests (swmm_test_hook)."""
+        self._check(self.lib.swmm_test_hook(self.h, hook, value))

@@ -582,3 +582,15 @@ def test_search_orders_agree(Z, order):
     assert not o.found and o.exhausted
     o = search.schedule_search(preserve=keep, temps=2, kinds=(search.SELF,), order=order)
     assert o.found and search.schedule_check(o.rows, preserve=keep, temps=2, kinds=(search.SELF,)).found
+
+
+@pytest.mark.parametrize("order,limit", [(0, 5000), (2, 5000), (2, 70000), (1, 3001)])
+def test_search_respects_state_limit(Z, order, limit):
+    """A search given a state limit visits at most that many states in total,
+    in one order or across the portfolio's rounds (each round's table is
+    capped at what the limit leaves)."""
+    search, _ = Z
+    keep = A_ALL + B_ALL
+    o = search.schedule_search(preserve=keep, temps=1, kinds=(search.SELF,), order=order, max_states=limit)
+    assert not o.found
+    assert 0 < o.states <= limit
