@@ -106,11 +106,11 @@ DEFAULT = "t9_8192_p65521"
 
 # DRAM bytes (read + write) per leaf GEMM launch.  One ncu capture of the
 # same kernel build on one fused level (7 products of 1024^3, the 2048^2
-# depth-1 workload) read 75.6 MB and wrote 2.2 MB; the 8192^2 depth-3 step
+# depth-1 workload) read 75.6 MB and wrote 1.4 MB; the 8192^2 depth-3 step
 # merges its 49 fused levels into 27 launches, and the traffic per fused
 # level is the same operands and targets, so the average launch moves
-# 77.8 MB x 49 / 27.
-TRAFFIC = {"t9_8192_p65521": 77.8e6 * 49 / 27, "t9_2048_p65521_d1": 77.8e6}
+# 77.0 MB x 49 / 27.
+TRAFFIC = {"t9_8192_p65521": 77.0e6 * 49 / 27, "t9_2048_p65521_d1": 77.0e6}
 
 
 def peaks():
@@ -466,11 +466,19 @@ def main():
     ap.add_argument("--no-graph", action="store_true", help="launch kernels directly instead of a CUDA graph")
     ap.add_argument("--serial", action="store_true",
                     help="capture the graph in row order on one stream (no dataflow overlap)")
+    ap.add_argument("--depth", type=int, default=None, help="override the workload's recursion depth")
+    ap.add_argument("--cutoff", type=int, default=None, help="override an IPMM workload's cut-off")
     ap.add_argument("--no-large", action="store_true",
                     help="skip the n = 16384 / 32768 Table 9 vs classical record of the default workload")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
-    w = WORKLOADS[args.workload]
+    w = dict(WORKLOADS[args.workload])
+    if args.depth is not None:
+        w["depth"] = args.depth
+        w["desc"] = w["desc"] + f" (depth {args.depth})"
+    if args.cutoff is not None:
+        w["cutoff"] = args.cutoff
+        w["desc"] = w["desc"] + f" (cut-off {args.cutoff})"
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

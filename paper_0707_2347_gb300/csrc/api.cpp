@@ -35,8 +35,9 @@ static EncodeTiledFn encode_fn() {
   return fn;
 }
 
-// 2-D map over `rows` rows of `kpad` 16-bit values; boxes of 64 x box_rows
-// land in shared memory with the 128-byte swizzle the MMA descriptors use.
+// 2-D map over `rows` rows of `kpad` 16-bit values; boxes of kBK x box_rows
+// land in shared memory with the swizzle (64-byte rows: 64-byte swizzle)
+// the MMA descriptors use.
 bool make_tmap(CUtensorMap *map, const void *base, int64_t rows, int64_t kpad, int box_rows) {
   EncodeTiledFn fn = encode_fn();
   if (!fn) return false;
@@ -45,8 +46,8 @@ bool make_tmap(CUtensorMap *map, const void *base, int64_t rows, int64_t kpad, i
   cuuint32_t box[2] = {(cuuint32_t)kBK, (cuuint32_t)box_rows};
   cuuint32_t estr[2] = {1, 1};
   CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, const_cast<void *>(base), dims, strides, box, estr,
-                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, kBK * 2 == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
 }
 

@@ -397,24 +397,26 @@ __global__ void __launch_bounds__(256) amax_kernel(const __grid_constant__ AmaxA
 // ------------------------------------------------------------ GEMM glue
 constexpr int kThreads = 320;                 // producer, MMA, 8 epilogue warps
 constexpr int kEpiThreads = 256;
-constexpr int kChunkKB = 15;                  // k-blocks between in-place reductions
-constexpr int kPlaneBytes = kBM * kBK * 2;    // 16 KB
+constexpr int kChunkKB = 960 / kBK;           // k-blocks between in-place reductions (960 K)
+constexpr int kNoDrainKB = 1024 / kBK;        // up to 1024 K no reduction is needed
+constexpr int kStageScale = 64 / kBK;         // stages per 64 K of operands
+constexpr int kPlaneBytes = kBM * kBK * 2;    // one A limb plane of a stage
 constexpr int kEpiBytes = 2 * kBM * 32 * 4;   // 32 KB: 128 rows x 64 columns, 2 boxes of 32
 
 template <int MODE>
 struct Cfg;
 template <>
 struct Cfg<MODE_MODP1> {
-  static constexpr int BN = 256, A_PLANES = 1, STAGES = 4, ACC_BUFS = 2, BUF_COLS = 256;
+  static constexpr int BN = 256, A_PLANES = 1, STAGES = 4 * kStageScale, ACC_BUFS = 2, BUF_COLS = 256;
 };
 template <>
 struct Cfg<MODE_MODP2> {
-  static constexpr int BN = kModp2BN, A_PLANES = 2, STAGES = kModp2BN == 64 ? 4 : 3;
+  static constexpr int BN = kModp2BN, A_PLANES = 2, STAGES = (kModp2BN == 64 ? 4 : 3) * kStageScale;
   static constexpr int ACC_BUFS = kModp2BN == 64 ? 2 : 1, BUF_COLS = 4 * kModp2BN;
 };
 template <>
 struct Cfg<MODE_FP32> {
-  static constexpr int BN = 128, A_PLANES = 2, STAGES = 3, ACC_BUFS = 2, BUF_COLS = 256;
+  static constexpr int BN = 128, A_PLANES = 2, STAGES = 3 * kStageScale, ACC_BUFS = 2, BUF_COLS = 256;
 };
 template <int MODE>
 __host__ __device__ constexpr int b_rows() {  // B rows per stage: one plane (p <= 256) or [hi | lo]
@@ -428,6 +430,9 @@ template <int MODE>
 __host__ __device__ constexpr int smem_bytes() {
   return Cfg<MODE>::STAGES * stage_bytes<MODE>() + kEpiBytes + 1024 + 256;
 }
+static_assert(smem_bytes<MODE_MODP1>() <= 232448 && smem_bytes<MODE_MODP2>() <= 232448 &&
+                  smem_bytes<MODE_FP32>() <= 232448,
+              "shared memory per CTA");
 
 __device__ __forceinline__ void mbar_init(uint64_t *b, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count));
@@ -587,14 +592,17 @@ __device__ __forceinline__ void sts128(uint32_t a, uint4 v) {
   asm volatile("st.shared.v4.b32 [%0], {%1,%2,%3,%4};" ::"r"(a), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w) : "memory");
 }
 
-// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row
-// core groups 1024 bytes apart (stride byte offset), descriptor version 1.
+// Shared-memory matrix descriptor: K-major operand whose rows are kBK fp16
+// values (kBK * 2 bytes, swizzled over that width), 8-row core groups
+// 8 * kBK * 2 bytes apart (stride byte offset), descriptor version 1.
+// Swizzle field: 2 = 128-byte, 4 = 64-byte.
 __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+  constexpr uint64_t kRowBytes = kBK * 2;
   uint64_t d = (uint64_t)((saddr & 0x3FFFF) >> 4);
-  d |= (uint64_t)1 << 16;            // leading byte offset (unused for this layout)
-  d |= (uint64_t)(1024 >> 4) << 32;  // stride byte offset
-  d |= (uint64_t)1 << 46;            // version
-  d |= (uint64_t)2 << 61;            // 128-byte swizzle
+  d |= (uint64_t)1 << 16;                          // leading byte offset (unused for this layout)
+  d |= (uint64_t)((8 * kRowBytes) >> 4) << 32;     // stride byte offset
+  d |= (uint64_t)1 << 46;                          // version
+  d |= (uint64_t)(kRowBytes == 128 ? 2 : 4) << 61;  // swizzle
   return d;
 }
 // Instruction descriptor, kind::f16: D fp32, A/B fp16 (fmt 0; 1 would be bf16),
@@ -695,37 +703,45 @@ __device__ __forceinline__ void modp_finish(const Product &pr, const Epi &E, int
 // exact fp32 integer (below 2^24).
 __device__ __forceinline__ void modp2_drain_split(const Product &pr, const Epi &E, uint32_t d, int hsel, int sign,
                                                   uint32_t (&vals)[2][32], uint64_t *half0, uint64_t *half1) {
+  // Eight groups of 16 columns (four of hh | hl, then four of lh | ll), read
+  // out of tensor memory with the next group's loads in flight while the
+  // current one is combined, so only the first load's latency is exposed.
   float X[4][16];
+  float a[2][16], b[2][16];
+  auto issue = [&](int g, int s) {
+    const int col = (g & 2) * 32 + hsel * 32 + (g & 1) * 16 + (g < 4 ? 0 : 2 * kModp2BN);
+    tmem_ld16(d + col, a[s]);
+    tmem_ld16(d + kModp2BN + col, b[s]);
+  };
+  issue(0, 0);
+  tmem_wait_ld();
+  reg_fence16(a[0]);
+  reg_fence16(b[0]);
 #pragma unroll
-  for (int g = 0; g < 4; ++g) {
-    const int col = (g >> 1) * 64 + hsel * 32 + (g & 1) * 16;
-    float a[16], b[16];
-    tmem_ld16(d + col, a);
-    tmem_ld16(d + kModp2BN + col, b);
-    tmem_wait_ld();
-    reg_fence16(a);
-    reg_fence16(b);
+  for (int g = 0; g < 8; ++g) {
+    const int s = g & 1;
+    if (g + 1 < 8) issue(g + 1, s ^ 1);
+    if (g < 4) {
 #pragma unroll
-    for (int e = 0; e < 16; ++e) X[g][e] = __fmaf_rn(256.f, E.fr(a[e]), E.fr(b[e]));
-  }
-  tc_fence_before();
-  mbar_arrive(half0);
+      for (int e = 0; e < 16; ++e) X[g][e] = __fmaf_rn(256.f, E.fr(a[s][e]), E.fr(b[s][e]));
+      if (g == 3) {  // hh | hl read out: the next tile's A_h products may start
+        tc_fence_before();
+        mbar_arrive(half0);
+      }
+    } else {
+      uint32_t *v = vals[(g - 4) >> 1] + (g & 1) * 16;
 #pragma unroll
-  for (int g = 0; g < 4; ++g) {
-    const int col = (g >> 1) * 64 + hsel * 32 + (g & 1) * 16;
-    float a[16], b[16];
-    tmem_ld16(d + 2 * kModp2BN + col, a);
-    tmem_ld16(d + 3 * kModp2BN + col, b);
-    tmem_wait_ld();
-    reg_fence16(a);
-    reg_fence16(b);
-    uint32_t *v = vals[g >> 1] + (g & 1) * 16;
-#pragma unroll
-    for (int e = 0; e < 16; ++e) {
-      const float y = E.fr(X[g][e] + E.fr(a[e]));
-      v[e] = E.out(E.fr(__fmaf_rn(256.f, y, E.fr(b[e]))));
+      for (int e = 0; e < 16; ++e) {
+        const float y = E.fr(X[g - 4][e] + E.fr(a[s][e]));
+        v[e] = E.out(E.fr(__fmaf_rn(256.f, y, E.fr(b[s][e]))));
+      }
+      modp_finish(pr, E, sign, v);
     }
-    modp_finish(pr, E, sign, v);
+    if (g + 1 < 8) {
+      tmem_wait_ld();
+      reg_fence16(a[s ^ 1]);
+      reg_fence16(b[s ^ 1]);
+    }
   }
   tc_fence_before();
   mbar_arrive(half1);
@@ -973,7 +989,7 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_kernel(const __grid_constant
             stage = 0;
             phase ^= 1;
           }
-          if (modp && nkb > 16 && (kb + 1) % kChunkKB == 0 && kb + 1 < nkb) {
+          if (modp && nkb > kNoDrainKB && (kb + 1) % kChunkKB == 0 && kb + 1 < nkb) {
             // keep every fp32 partial sum below 2^24: reduce mod p in place
             tc_commit(drain_full);
             if (!wait_bar(drain_empty, dcount & 1, ctl, P.err)) {
@@ -1028,7 +1044,7 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_kernel(const __grid_constant
       const bool with_beta = pr.epilogue == EPI_STORE && pr.use_beta;
       const int sign = pr.t[0].sign;
       bool bad = false;
-      if (modp && nkb > 16) {
+      if (modp && nkb > kNoDrainKB) {
         const int ndrain = (nkb - 1) / kChunkKB;
         for (int q = 0; q < ndrain; ++q, ++dcount) {
           wait_bar(drain_full, dcount & 1, ctl, P.err);
