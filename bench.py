@@ -468,6 +468,9 @@ def main():
                     help="capture the graph in row order on one stream (no dataflow overlap)")
     ap.add_argument("--depth", type=int, default=None, help="override the workload's recursion depth")
     ap.add_argument("--cutoff", type=int, default=None, help="override an IPMM workload's cut-off")
+    ap.add_argument("--shape", default=None, help="override the workload's m,k,n")
+    ap.add_argument("--sched", type=int, default=None, help="override the workload's schedule id")
+    ap.add_argument("--fp32", action="store_true", help="run the workload in FP32 mode")
     ap.add_argument("--no-large", action="store_true",
                     help="skip the n = 16384 / 32768 Table 9 vs classical record of the default workload")
     args = ap.parse_args()
@@ -479,6 +482,15 @@ def main():
     if args.cutoff is not None:
         w["cutoff"] = args.cutoff
         w["desc"] = w["desc"] + f" (cut-off {args.cutoff})"
+    if args.shape is not None:
+        w["m"], w["k"], w["n"] = (int(x) for x in args.shape.split(","))
+        w["desc"] = w["desc"] + f" (shape {args.shape})"
+    if args.sched is not None:
+        w["sched"] = args.sched
+        w["desc"] = w["desc"] + f" (schedule {args.sched})"
+    if args.fp32:
+        w["mode"], w["p"] = FP32, 0
+        w["desc"] = w["desc"] + " (FP32 mode)"
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
