@@ -128,6 +128,17 @@ extern "C" {
                                   (more, smaller launches), never different
                                   results */
 #define SWMM_LOWMEM_STAGE_BYTES (64ll << 20)
+#define SWMM_FLAG_TUNE 64u     /* swmm_muladd_batched: problems with SWMM_AUTO
+                                  and 2 m k n >= 2 * 3072^3 get the measured
+                                  choice instead of the model's: the classical
+                                  product and one Winograd level (Table 2, or
+                                  Table 9 if square) are each run on a scratch
+                                  copy of C (device memory for one C, taken
+                                  from and returned to the stream-ordered
+                                  pool) and timed on the GPU the first time a
+                                  shape and mode is seen; the handle keeps the
+                                  result.  The first call with new shapes
+                                  waits for those runs */
 
 typedef struct swmm_ctx *swmm_t;
 

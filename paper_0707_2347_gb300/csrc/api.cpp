@@ -158,6 +158,8 @@ struct swmm_ctx {
   bool has_custom = false;
   // autotuner decisions: (m, k, n, mode, p) -> (sched, depth, est_us, elems)
   std::vector<std::pair<std::array<int64_t, 5>, std::tuple<int32_t, int32_t, double, int64_t>>> tuned;
+  // measured decisions of batched calls with SWMM_FLAG_TUNE: (m, k, n, mode, p) -> (sched, depth)
+  std::vector<std::pair<std::array<int64_t, 5>, std::pair<int32_t, int32_t>>> measured;
   ~swmm_ctx() {
     graphs.clear();
     for (cudaStream_t s : flow_streams)
@@ -268,6 +270,7 @@ void reset_counts(Exec &x) {
   x.ws_top = x.ws_peak = x.stage_need = 0;
   x.tmp_elems = x.tmp_peak_elems = 0;
   x.add_elems = x.leaf_flops = x.leaf_launches = x.ew_launches = x.leaf_products = 0;
+  x.pack_bytes = 0;
   x.lazy_views.clear();
   x.stage_turn = 0;
 }
@@ -1053,6 +1056,84 @@ int swmm_autotune(swmm_t h, int64_t m, int64_t k, int64_t n, int32_t mode, uint3
   return SWMM_OK;
 }
 
+// SWMM_FLAG_TUNE: problems below this size (2 m k n) take the model's choice;
+// a Winograd level cannot pay for its packs there (measured: Table 2 depth 1
+// against the classical product, 1.00x at 4096^3 over Z/65521).
+constexpr double kTuneMinFlops = 2.0 * 3072.0 * 3072.0 * 3072.0;
+
+// The measured choice for one batched problem (SWMM_FLAG_TUNE): the classical
+// product and one Winograd level (Table 2, or Table 9 for square problems),
+// each run on a scratch copy of C on the handle's stream, once to warm up and
+// twice timed with events; the faster wins and is kept per shape and mode.
+int measure_pick(swmm_t h, const swmm_problem &pb, int32_t *s, int32_t *d) {
+  const std::array<int64_t, 5> key{pb.m, pb.k, pb.n, pb.mode, pb.mode == SWMM_FP32 ? 0 : (int64_t)pb.p};
+  for (auto &e : h->measured)
+    if (e.first == key) {
+      *s = e.second.first;
+      *d = e.second.second;
+      return SWMM_OK;
+    }
+  char *scr = nullptr;
+  const int64_t bytes = 4 * pb.m * pb.n;
+  if (injected_alloc_failure(h) || cudaMallocAsync((void **)&scr, bytes, h->stream) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(h, SWMM_ENOMEM, "tuning scratch");
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int rc = SWMM_OK;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) rc = SWMM_ECUDA;
+  const void *al = pb.mode == SWMM_FP32 ? (const void *)&pb.alpha_f : (const void *)&pb.alpha_u;
+  const void *be = pb.mode == SWMM_FP32 ? (const void *)&pb.beta_f : (const void *)&pb.beta_u;
+  const int cands[3][2] = {{SWMM_CLASSICAL, 0}, {SWMM_T2_HLJJTT, 1}, {SWMM_T9_ACC, 1}};
+  const bool square = pb.m == pb.k && pb.k == pb.n;
+  float best = 1e30f;
+  int bs = SWMM_CLASSICAL, bd = 0;
+  for (int c = 0; c < 3 && rc == SWMM_OK; ++c) {
+    if (cands[c][0] == SWMM_T9_ACC && !square) continue;
+    if (cands[c][0] == SWMM_T2_HLJJTT && square) continue;  // Table 9 takes the square ones
+    swmm_opts o;
+    std::memset(&o, 0, sizeof(o));
+    o.mode = pb.mode;
+    o.p = pb.p;
+    o.sched = cands[c][0];
+    o.depth = cands[c][1];
+    Req q{1, pb.m, pb.k, pb.n, pb.A, pb.B, scr, pb.lda, pb.ldb, pb.n, al, be};
+    if (cudaMemcpy2DAsync(scr, 4 * pb.n, pb.C, 4 * pb.ldc, 4 * pb.n, pb.m, cudaMemcpyDeviceToDevice, h->stream) !=
+        cudaSuccess) {
+      rc = SWMM_ECUDA;
+      break;
+    }
+    rc = run(h, q, &o);
+    if (rc != SWMM_OK) break;
+    if (cudaEventRecord(e0, h->stream) != cudaSuccess) rc = SWMM_ECUDA;
+    for (int r = 0; r < 2 && rc == SWMM_OK; ++r) rc = run(h, q, &o);
+    if (rc != SWMM_OK) break;
+    float ms = 0.f;
+    if (cudaEventRecord(e1, h->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+        cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+      rc = SWMM_ECUDA;
+      break;
+    }
+    if (ms < best) {
+      best = ms;
+      bs = cands[c][0];
+      bd = cands[c][1];
+    }
+  }
+  cudaFreeAsync(scr, h->stream);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (rc == SWMM_ECUDA) {
+    cudaError_t e = cudaGetLastError();
+    return fail(h, SWMM_ECUDA, std::string("tuning run: ") + cudaGetErrorString(e));
+  }
+  if (rc != SWMM_OK) return rc;
+  if (h->measured.size() < 4096) h->measured.push_back({key, {bs, bd}});
+  *s = bs;
+  *d = bd;
+  return SWMM_OK;
+}
+
 int swmm_muladd_batched(swmm_t h, int count, swmm_problem *probs, uint32_t flags) {
   if (!h) return SWMM_EINVAL;
   h->last_error.clear();
@@ -1075,7 +1156,13 @@ int swmm_muladd_batched(swmm_t h, int count, swmm_problem *probs, uint32_t flags
     swmm_problem &pb = probs[i];
     int32_t s = pb.sched, d = pb.depth;
     if (s == SWMM_AUTO) {
-      int rc = swmm_autotune(h, pb.m, pb.k, pb.n, pb.mode, pb.p, &s, &d, nullptr, nullptr);
+      // a malformed problem keeps the model's choice and fails in make_plan below
+      const bool sane = pb.A && pb.B && pb.C && pb.m > 0 && pb.k > 0 && pb.n > 0 && pb.lda >= pb.k &&
+                        pb.ldb >= pb.n && pb.ldc >= pb.n;
+      const bool big = sane && 2.0 * (double)pb.m * (double)pb.k * (double)pb.n >= kTuneMinFlops;
+      int rc = (flags & SWMM_FLAG_TUNE) && big ? measure_pick(h, pb, &s, &d)
+                                              : swmm_autotune(h, pb.m, pb.k, pb.n, pb.mode, pb.p, &s, &d, nullptr,
+                                                              nullptr);
       if (rc != SWMM_OK) return rc;
     }
     pb.chosen_sched = s;

@@ -390,6 +390,7 @@ void Exec::leaf_group(Scalar alpha, bool acc, Scalar beta, const LeafJob *jobs, 
     bb[i] = rup(pl * Np[i] * Kp[i] * 2, 1024);
     off[i] = total;
     total += hdr + ab[i] + bb[i];
+    pack_bytes += (int64_t)jobs[i].L.esz * m * k + (int64_t)jobs[i].R.esz * k * n + ab[i] + bb[i];
     leaf_flops += 2 * m * n * k;
     ++leaf_products;
     tflops += 2.0 * m * n * k * limb_products();
@@ -602,6 +603,21 @@ void Exec::fused_level(Scalar alpha, bool acc, Scalar beta, const Lin &LL, const
     const int ngroups = (7 + group - 1) / group;
     stage_need = std::max(stage_need, hdr + group * (abytes + bbytes));
     ew_launches += ngroups * (fp32 ? 2 : 1);
+    for (int g0 = 0; g0 < 7; g0 += group) {  // each group reads the quadrants its operands use
+      int qa = 0, qb = 0;
+      for (int q = 0; q < 4; ++q) {
+        bool ua = false, ub = false;
+        for (int i = g0; i < std::min(7, g0 + group); ++i) {
+          ua = ua || acoef[ord[i]][q] != 0;
+          ub = ub || bcoef[ord[i]][q] != 0;
+        }
+        qa += ua;
+        qb += ub;
+      }
+      for (int t = 0; t < LL.n; ++t) pack_bytes += (int64_t)qa * LL.v[t].esz * hm * hk;
+      for (int t = 0; t < RL.n; ++t) pack_bytes += (int64_t)qb * RL.v[t].esz * hk * hn;
+      pack_bytes += std::min(group, 7 - g0) * (abytes + bbytes);
+    }
     const double pflops = 2.0 * hm * hn * hk * limb_products();
     if (dry) {
       for (int g0 = 0; g0 < 7; g0 += group) queue_gemm(nullptr, {}, {}, true, std::min(group, 7 - g0) * pflops,

@@ -27,7 +27,7 @@ SCHED_NAMES = {CLASSICAL: "classical", T1_DHSS: "T1", T2_HLJJTT: "T2", T3_IP: "I
                T5_OVR: "OvR", T6_ACLR: "AcLR", T7_ACCR: "AccR", T8_ACR: "AcR", T9_ACC: "Acc",
                IPMM: "IPMM", T4M_OVL: "OvLM", IP0VMM: "IP0vMM", TBLOCK: "Sec7.2", CUSTOM: "custom"}
 # flags
-FLAG_UNFUSED, FLAG_SIMT_LEAF, FLAG_TIMING, FLAG_GRAPH, FLAG_SERIAL, FLAG_LOWMEM = 1, 2, 4, 8, 16, 32
+FLAG_UNFUSED, FLAG_SIMT_LEAF, FLAG_TIMING, FLAG_GRAPH, FLAG_SERIAL, FLAG_LOWMEM, FLAG_TUNE = 1, 2, 4, 8, 16, 32, 64
 LOWMEM_STAGE_BYTES = 64 << 20
 
 

@@ -13,8 +13,9 @@ back bit-identical, and the planned temporaries equal the paper's count.
   * FP32 mode, 16384^2, Table 9 at depths 1-4: max |C - C64| / (|A| |B|)
     on spot rows within 1e-5 n^0.6.
   * 512 uneven C <- A B + C problems (m, k, n uniform in [384, 6144]; even
-    index mod 65521, odd FP32) in one batched call with the autotuner's
-    schedule per problem: every problem checked by its residual.
+    index mod 65521, odd FP32) in one batched call, the large problems'
+    schedules measured on the GPU (SWMM_FLAG_TUNE): every problem checked
+    by its residual.
   * The shipped searched schedules for Tables 6 and 7's contracts and the
     mixed schedule Table 9 over Table 2, bit-exact at 512^2 and 1024^2.
 """
@@ -113,9 +114,11 @@ def test_config5_batch512(handle):
         A, B, C = mk(m, k), mk(k, n), mk(m, n)
         keep.append(C.clone())
         probs.append(dict(A=A, B=B, C=C, mode=mode, p=65521, alpha=1, beta=1, sched=S.AUTO))
-    chosen = handle.muladd_batched(probs, S.FLAG_GRAPH)
+    chosen = handle.muladd_batched(probs, S.FLAG_GRAPH | S.FLAG_TUNE)
     handle.sync()
     assert len(chosen) == 512
+    measured = [c for c, (m, k, n) in zip(chosen, shapes) if m * k * n >= 3072 ** 3]
+    assert measured and set(measured) <= {(S.CLASSICAL, 0), (S.T2_HLJJTT, 1), (S.T9_ACC, 1)}
 
     def job(i):
         q = probs[i]

@@ -135,3 +135,39 @@ def test_batched_classical_grouped(handle, graph):
     handle.sync()
     _check(probs, refs)
     assert handle.stats()["leaf_launches"] <= 4
+
+
+@pytest.mark.parametrize("graph", [False, True], ids=["eager", "graph"])
+def test_batched_measured_tuning(handle, graph):
+    """SWMM_FLAG_TUNE: the large problems' schedules are chosen by timing the
+    classical product and one Winograd level on the GPU; results stay exact
+    (Freivalds over Z/65521) or within the FP32 bound (FP64 residual), and a
+    second call reuses the measured choices."""
+    shapes = [(3200, 3328, 3456), (3456, 3200, 3328), (3328, 3328, 3328), (3584, 3584, 3584)]
+    probs, refs = [], []
+    for i, (m, k, n) in enumerate(shapes):
+        if i % 2 == 0:
+            A, B, C = modp_inputs(m, k, n, 65521, tag=200 + i)
+            probs.append(dict(A=dev(A), B=dev(B), C=dev(C), mode=S.MODP, p=65521, alpha=1, beta=1))
+            refs.append(("modp", A, B, C))
+        else:
+            A, B, C = fp_inputs(m, k, n, tag=200 + i)
+            probs.append(dict(A=dev(A), B=dev(B), C=dev(C), mode=S.FP32, alpha=1.0, beta=1.0))
+            refs.append(("fp", A, B, C))
+    flags = S.FLAG_TUNE | (S.FLAG_GRAPH if graph else 0)
+    chosen = handle.muladd_batched(probs, flags)
+    handle.sync()
+    for (s, d), (m, k, n) in zip(chosen, shapes):
+        square = m == k == n
+        assert (s, d) in ((S.CLASSICAL, 0), (S.T9_ACC if square else S.T2_HLJJTT, 1))
+    for q, (kind, A, B, C) in zip(probs, refs):
+        out = host(q["C"])
+        if kind == "modp":
+            assert probes.freivalds_modp(1, A, B, 1, C, out, 65521, vectors=2)
+        else:
+            assert probes.residual_f64(1.0, A, B, 1.0, C, out) <= probes.fp_bound(max(A.shape + B.shape))
+    for q, (kind, A, B, C) in zip(probs, refs):
+        q["C"].copy_(dev(C))
+    again = handle.muladd_batched(probs, flags)
+    handle.sync()
+    assert again == chosen
