@@ -265,12 +265,16 @@ struct Scratch {
 
 // operand staging per slot up to which leaf launches are merged
 constexpr int64_t kMergeStageBytes = 96ll << 20;
+// base of the temporaries in a planning pass (a placeholder above any device
+// address; the pass never dereferences it)
+char *const kPlanWorkspace = reinterpret_cast<char *>(uintptr_t(4) << 44);
 
 void reset_counts(Exec &x) {
   x.ws_top = x.ws_peak = x.stage_need = 0;
   x.tmp_elems = x.tmp_peak_elems = 0;
   x.add_elems = x.leaf_flops = x.leaf_launches = x.ew_launches = x.leaf_products = 0;
   x.pack_bytes = 0;
+  x.level_packs = false;
   x.lazy_views.clear();
   x.stage_turn = 0;
 }
@@ -445,8 +449,11 @@ int make_plan(swmm_t h, const Req &q, const swmm_opts *o, bool check_ptrs, Plan 
   P.cutoff = o->ipmm_cutoff > 0 ? o->ipmm_cutoff : 1024;
   P.ipmm_acc = o->ipmm_acc == SWMM_T9_ACC ? K_ACC : K_T2;
   P.tblock = tb;
-  // planning pass: sizes and counts, no launches
+  // planning pass: sizes and counts, no launches.  Temporaries get
+  // placeholder addresses above every real one (never dereferenced), so the
+  // pass sees the same overlaps between blocks as the run.
   x.dry = true;
+  x.ws = kPlanWorkspace;
   execute(P, x);
   x.flush();
   if (!x.fail.empty()) return fail(h, SWMM_EINVAL, x.fail);
@@ -460,6 +467,7 @@ int make_plan(swmm_t h, const Req &q, const swmm_opts *o, bool check_ptrs, Plan 
     x.flush();
     if (!x.fail.empty()) return fail(h, SWMM_EINVAL, x.fail);
   }
+  x.ws = nullptr;
   // levels that materialise temporaries: all but a fused last one
   const int tmp_levels = (x.fused && lv > 0 && sched != SWMM_IPMM) ? lv - 1 : lv;
   if (sched == SWMM_TBLOCK)  // one block call's temporaries (Section 7.2)
@@ -501,7 +509,7 @@ int enqueue(swmm_t h, const Plan &P, cudaStream_t stream, TimingHook *timing, co
   const Exec &x = P.x;
   Exec r = x;
   r.merge = x.merge && !ext;
-  r.stage_slots = r.merge ? 4 : (use_flow && x.stage_budget == 0 ? 2 : 1);
+  r.stage_slots = r.merge ? 4 : (use_flow && x.stage_budget == 0 && !x.level_packs ? 2 : 1);
   const int64_t stage_bytes = r.stage_slots * ((x.stage_need + 1023) / 1024 * 1024);
   r.dry = false;
   r.lazy_views.clear();
@@ -790,8 +798,10 @@ std::vector<Plan> group_classical(std::vector<Plan> &each) {
         x.merge = false;
         x.stage_slots = 1;
         x.dry = true;
+        x.ws = kPlanWorkspace;
         execute(G, x);
         x.flush();
+        x.ws = nullptr;
       }
       out.push_back(std::move(G));
       a = b;
@@ -812,9 +822,21 @@ double model_us(const Plan &P) {
   const double tiles = per_product / (2.0 * 128.0 * 128.0 * 1024.0);  // 128 x 128 x 1024 tile units
   const double eff = 0.95 * tiles / (tiles + 6.0) + 0.05;
   const double rate = 1.75e9 * eff;  // flop/us at the sustained tensor peak
-  const double bytes = (double)x.add_elems * 12.0 + (double)x.stage_need * 3.0;
+  const double bytes = (double)x.add_elems * 12.0 + (double)x.pack_bytes;
   const double launches = (double)(x.leaf_launches + x.ew_launches);
   return flops / rate + bytes / 5.5e6 + launches * 2.5;
+}
+
+// A call without operands, for planning only: placeholder addresses, never
+// dereferenced, disjoint from each other and from the planning pass's
+// temporaries, so the plan sees the same overlaps as a call with real
+// operands (packed leading dimensions).
+Req placeholder_req(int entry, int64_t m, int64_t k, int64_t n, const void *alpha, const void *beta) {
+  const void *fa = reinterpret_cast<const void *>(uintptr_t(1) << 44);
+  const void *fb = reinterpret_cast<const void *>(uintptr_t(2) << 44);
+  void *fc = reinterpret_cast<void *>(uintptr_t(3) << 44);
+  return Req{entry, m, k, n, fa, fb, fc, std::max<int64_t>(k, 1), std::max<int64_t>(n, 1), std::max<int64_t>(n, 1),
+             alpha, beta};
 }
 
 // The dry run of a call with no operands: the entry point the schedule's
@@ -834,8 +856,8 @@ int plan_only(swmm_t h, int64_t m, int64_t k, int64_t n, const swmm_opts *opts, 
     acc_inplace = !ro && h->custom.accumulate;
   }
   static const uint32_t one = 1;
-  Req q{entry, m, k, n, nullptr, nullptr, nullptr, k, n, n, &one, acc_inplace || entry == 1 ? &one : nullptr};
-  return make_plan(h, q, opts, false, P);
+  return make_plan(h, placeholder_req(entry, m, k, n, &one, acc_inplace || entry == 1 ? &one : nullptr), opts, false,
+                   P);
 }
 
 // The handle's own schedule: checked in the pebble game, lowered to rows.
@@ -1033,10 +1055,8 @@ int swmm_autotune(swmm_t h, int64_t m, int64_t k, int64_t n, int32_t mode, uint3
       o.p = p;
       o.sched = c;
       o.depth = d;
-      Req q{1, m, k, n, nullptr, nullptr, nullptr, std::max<int64_t>(k, 1), std::max<int64_t>(n, 1),
-            std::max<int64_t>(n, 1), sc, sc};
       Plan P;
-      if (make_plan(h, q, &o, false, P) != SWMM_OK) continue;
+      if (make_plan(h, placeholder_req(1, m, k, n, sc, sc), &o, false, P) != SWMM_OK) continue;
       const double t = model_us(P);
       if (t < best) {
         best = t;

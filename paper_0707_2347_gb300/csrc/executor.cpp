@@ -40,6 +40,35 @@ struct Range {
   }
 };
 bool aligned16(const void *p, int64_t ld) { return ((uintptr_t)p % 16 == 0) && (ld % 4 == 0); }
+
+// One Winograd level as a fused level computes it (Section 2's sums).
+// Operand coefficients over (X11, X12, X21, X22), product i in row i:
+const int8_t acoef[7][4] = {
+    {1, 0, 0, 0},    // A11
+    {0, 1, 0, 0},    // A12
+    {1, 1, -1, -1},  // S4 = A12 - A21 - A22 + A11
+    {0, 0, 0, 1},    // A22
+    {0, 0, 1, 1},    // S1 = A21 + A22
+    {-1, 0, 1, 1},   // S2 = A21 + A22 - A11
+    {1, 0, -1, 0},   // S3 = A11 - A21
+};
+const int8_t bcoef[7][4] = {
+    {1, 0, 0, 0},    // B11
+    {0, 0, 1, 0},    // B21
+    {0, 0, 0, 1},    // B22
+    {1, -1, -1, 1},  // T4 = B22 - B12 + B11 - B21
+    {-1, 1, 0, 0},   // T1 = B12 - B11
+    {1, -1, 0, 1},   // T2 = B22 - B12 + B11
+    {0, -1, 0, 1},   // T3 = B22 - B12
+};
+// targets: quadrant index (0 = C11, 1 = C12, 2 = C21, 3 = C22) and sign
+const int8_t tgt[7][4] = {
+    {1, 1, 1, 1}, {1, 0, 0, 0}, {0, 1, 0, 0}, {0, 0, -1, 0}, {0, 1, 0, 1}, {0, 1, 1, 1}, {0, 0, 1, 1},
+};
+// Order of the products in a launch: most targets first (P1, P6, P5, P7,
+// then P2, P3, P4), so the reduce-adds of a launch's last wave, which no
+// longer overlap any multiplication, are single-target ones.
+const int ord[7] = {0, 5, 4, 6, 1, 2, 3};
 }  // namespace
 
 // tensor-core products per leaf product: 1 limb (p <= 256), 2 x 2 limbs,
@@ -497,36 +526,87 @@ bool Exec::fuses(int64_t m, int64_t k, int64_t n, int depth) const {
   return fused && depth == 1 && m >= 2 && k >= 2 && n >= 2 && m % 2 == 0 && k % 2 == 0 && n % 2 == 0;
 }
 
-void Exec::fused_level(Scalar alpha, bool acc, Scalar beta, const Lin &LL, const Lin &RL, View D) {
+// Staged sizes of one product of a fused level over L (m x k) and R (k x n).
+void Exec::level_bytes(const View &L, const View &R, int64_t &abytes, int64_t &bbytes) const {
+  const int pl = planes_of(mode), bn = bn_of(mode);
+  const int64_t Mp = rup(L.rows / 2, kBM), Np = rup(R.cols / 2, bn), Kp = rup(L.cols / 2, kBK);
+  abytes = rup(pl * Mp * Kp * 2, 1024);
+  bbytes = rup(pl * Np * Kp * 2, 1024);
+}
+
+// Pack arguments of products [g0, g0 + gn) (in launch order) of the fused
+// level over LL x RL, outputs at stg (the gn A operands, then the gn B
+// operands).  The sources are the quadrants the group's operands use (all
+// four for a whole level), each the signed sum of that quadrant of every
+// term.  A whole level forms the chains S2 = S1 - A11, S4 = A12 - S2 and
+// T2 = B22 - T1, T4 = T2 - B21 once per element, output i holding product
+// i; a group's generic pack writes its products in launch order.
+void Exec::pack_args(const Lin &LL, const Lin &RL, int g0, int gn, char *stg, const uint32_t *amax, PackArgs &pa,
+                     PackArgs &pb) const {
+  const View &L = LL.shape(), &R = RL.shape();
+  const int64_t hm = L.rows / 2, hk = L.cols / 2, hn = R.cols / 2;
+  const int64_t Mp = rup(hm, kBM), Np = rup(hn, bn_of(mode)), Kp = rup(hk, kBK);
+  int64_t abytes, bbytes;
+  level_bytes(L, R, abytes, bbytes);
+  std::memset(&pa, 0, sizeof(pa));
+  std::memset(&pb, 0, sizeof(pb));
+  auto sources = [&](const Lin &LIN, const int8_t (*cf)[4], PackArgs &pk) {
+    int map[4], ns = 0;
+    for (int q = 0; q < 4; ++q) {
+      bool used = false;
+      for (int i = g0; i < g0 + gn; ++i) used = used || cf[ord[i]][q] != 0;
+      map[q] = used ? ns++ : -1;
+      if (!used) continue;
+      for (int t = 0; t < LIN.n; ++t) {
+        const View qd = LIN.v[t].quad(q / 2, q % 2);
+        pk.src[map[q]][t] = qd.ptr;
+        pk.ld[map[q]][t] = qd.ld;
+      }
+    }
+    for (int t = 0; t < LIN.n; ++t) {
+      pk.tsign[t] = LIN.s[t];
+      pk.tesz[t] = (int8_t)LIN.v[t].esz;
+    }
+    pk.nterm = LIN.n;
+    pk.nsrc = ns;
+    pk.nout = gn;
+    for (int j = 0; j < gn; ++j)
+      for (int q = 0; q < 4; ++q)
+        if (map[q] >= 0) pk.coef[j][map[q]] = cf[ord[g0 + j]][q];
+  };
+  sources(LL, acoef, pa);
+  sources(RL, bcoef, pb);
+  pa.set = gn == 7 ? PACK_WINOGRAD_A : PACK_GENERIC;
+  pb.set = gn == 7 ? PACK_WINOGRAD_B : PACK_GENERIC;
+  for (int j = 0; j < gn; ++j) {
+    pa.out[j] = reinterpret_cast<uint16_t *>(stg + j * abytes);
+    pb.out[j] = reinterpret_cast<uint16_t *>(stg + gn * abytes + j * bbytes);
+  }
+  pa.rows = (int)hm;
+  pa.cols = (int)hk;
+  pa.prow_pad = (int)Mp;
+  pa.pcol_pad = (int)Kp;
+  pa.transpose = 0;
+  pa.p = p;
+  pa.barrett = p ? (uint32_t)(0x100000000ull / p) : 0;
+  pb.barrett = pa.barrett;
+  pb.rows = (int)hk;
+  pb.cols = (int)hn;
+  pb.prow_pad = (int)Np;
+  pb.pcol_pad = (int)Kp;
+  pb.transpose = 1;
+  pb.p = p;
+  // |S4|, |T4| <= 4 max|source|, a source <= nterm max|term entry|
+  pa.amax = amax;
+  pb.amax = amax ? amax + 1 : nullptr;
+  pa.terms = 4 * LL.n;
+  pb.terms = 4 * RL.n;
+}
+
+void Exec::fused_level(Scalar alpha, bool acc, Scalar beta, const Lin &LL, const Lin &RL, View D,
+                       const Prepacked *pre) {
   const View &L = LL.shape(), &R = RL.shape();
   const Range nv(!dry, "fused level", L.rows, L.cols, R.cols, 1);
-  // operand coefficients over (X11, X12, X21, X22)
-  static const int8_t acoef[7][4] = {
-      {1, 0, 0, 0},    // A11
-      {0, 1, 0, 0},    // A12
-      {1, 1, -1, -1},  // S4 = A12 - A21 - A22 + A11
-      {0, 0, 0, 1},    // A22
-      {0, 0, 1, 1},    // S1 = A21 + A22
-      {-1, 0, 1, 1},   // S2 = A21 + A22 - A11
-      {1, 0, -1, 0},   // S3 = A11 - A21
-  };
-  static const int8_t bcoef[7][4] = {
-      {1, 0, 0, 0},    // B11
-      {0, 0, 1, 0},    // B21
-      {0, 0, 0, 1},    // B22
-      {1, -1, -1, 1},  // T4 = B22 - B12 + B11 - B21
-      {-1, 1, 0, 0},   // T1 = B12 - B11
-      {1, -1, 0, 1},   // T2 = B22 - B12 + B11
-      {0, -1, 0, 1},   // T3 = B22 - B12
-  };
-  // targets: quadrant index (0 = C11, 1 = C12, 2 = C21, 3 = C22) and sign
-  static const int8_t tgt[7][4] = {
-      {1, 1, 1, 1}, {1, 0, 0, 0}, {0, 1, 0, 0}, {0, 0, -1, 0}, {0, 1, 0, 1}, {0, 1, 1, 1}, {0, 0, 1, 1},
-  };
-  // Order of the products in a launch: most targets first (P1, P6, P5, P7,
-  // then P2, P3, P4), so the reduce-adds of a launch's last wave, which no
-  // longer overlap any multiplication, are single-target ones.
-  static const int ord[7] = {0, 5, 4, 6, 1, 2, 3};
   const int64_t hm = L.rows / 2, hk = L.cols / 2, hn = R.cols / 2;
   View Dq[4] = {D.quad(0, 0), D.quad(0, 1), D.quad(1, 0), D.quad(1, 1)};
   leaf_flops += 7 * 2 * hm * hn * hk;
@@ -598,12 +678,16 @@ void Exec::fused_level(Scalar alpha, bool acc, Scalar beta, const Lin &LL, const
     // a staging budget, groups of consecutive products whose operands fit it
     // (each group's pack reads only the quadrants its operands use).
     int group = 7;
-    if (stage_budget > 0)
+    if (stage_budget > 0 && !pre)
       group = (int)std::max<int64_t>(1, std::min<int64_t>(7, (stage_budget - hdr) / (abytes + bbytes)));
     const int ngroups = (7 + group - 1) / group;
-    stage_need = std::max(stage_need, hdr + group * (abytes + bbytes));
-    ew_launches += ngroups * (fp32 ? 2 : 1);
-    for (int g0 = 0; g0 < 7; g0 += group) {  // each group reads the quadrants its operands use
+    // prepacked (`pre`): the table level's one pack formed this level's
+    // operands at pre->stg (FP32 amax words at pre->base), and counted them
+    if (!pre) {
+      stage_need = std::max(stage_need, hdr + group * (abytes + bbytes));
+      ew_launches += ngroups * (fp32 ? 2 : 1);
+    }
+    for (int g0 = 0; g0 < 7 && !pre; g0 += group) {  // each group reads the quadrants its operands use
       int qa = 0, qb = 0;
       for (int q = 0; q < 4; ++q) {
         bool ua = false, ub = false;
@@ -630,78 +714,23 @@ void Exec::fused_level(Scalar alpha, bool acc, Scalar beta, const Lin &LL, const
     for (int t = 0; t < RL.n; ++t) rdB.push_back(rect_of(RL.v[t]));
     for (int g0 = 0; g0 < 7; g0 += group) {
       const int gn = std::min(group, 7 - g0);
-      char *base = next_stage();
+      char *base = pre ? pre->base : next_stage();
       if (!base) return;
       uint32_t *amax = fp32 ? reinterpret_cast<uint32_t *>(base) : nullptr;
-      char *stg = base + hdr;
+      char *stg = pre ? pre->stg : base + hdr;
       const Rect ra = rect_bytes(stg, gn * abytes), rb = rect_bytes(stg + gn * abytes, gn * bbytes);
       const Rect rh = rect_bytes(base, 8);
-      if (fp32) fp32_amax(amax, LL.v, LL.n, RL.v, RL.n);
+      if (fp32 && !pre) fp32_amax(amax, LL.v, LL.n, RL.v, RL.n);
       PackArgs pa, pb;
-      std::memset(&pa, 0, sizeof(pa));
-      std::memset(&pb, 0, sizeof(pb));
-      // sources: the quadrants the group's operands use (all four for a
-      // whole level), each the signed sum of that quadrant of every term
-      auto sources = [&](const Lin &LIN, const int8_t (*cf)[4], PackArgs &pk) {
-        int map[4], ns = 0;
-        for (int q = 0; q < 4; ++q) {
-          bool used = false;
-          for (int i = g0; i < g0 + gn; ++i) used = used || cf[ord[i]][q] != 0;
-          map[q] = used ? ns++ : -1;
-          if (!used) continue;
-          for (int t = 0; t < LIN.n; ++t) {
-            const View qd = LIN.v[t].quad(q / 2, q % 2);
-            pk.src[map[q]][t] = qd.ptr;
-            pk.ld[map[q]][t] = qd.ld;
-          }
-        }
-        for (int t = 0; t < LIN.n; ++t) {
-          pk.tsign[t] = LIN.s[t];
-          pk.tesz[t] = (int8_t)LIN.v[t].esz;
-        }
-        pk.nterm = LIN.n;
-        pk.nsrc = ns;
-        pk.nout = gn;
-        for (int j = 0; j < gn; ++j)
-          for (int q = 0; q < 4; ++q)
-            if (map[q] >= 0) pk.coef[j][map[q]] = cf[ord[g0 + j]][q];
-      };
-      sources(LL, acoef, pa);
-      sources(RL, bcoef, pb);
-      // a whole level forms the chains S2 = S1 - A11, S4 = A12 - S2 and
-      // T2 = B22 - T1, T4 = T2 - B21 once per element, output i holding
-      // product i; a group's generic pack writes its products in launch order
-      pa.set = gn == 7 ? PACK_WINOGRAD_A : PACK_GENERIC;
-      pb.set = gn == 7 ? PACK_WINOGRAD_B : PACK_GENERIC;
-      for (int j = 0; j < gn; ++j) {
-        pa.out[j] = reinterpret_cast<uint16_t *>(stg + j * abytes);
-        pb.out[j] = reinterpret_cast<uint16_t *>(stg + gn * abytes + j * bbytes);
+      pack_args(LL, RL, g0, gn, stg, amax, pa, pb);
+      if (!pre) {
+        std::vector<Rect> rdAB{rh};
+        rdAB.insert(rdAB.end(), rdA.begin(), rdA.end());
+        rdAB.insert(rdAB.end(), rdB.begin(), rdB.end());
+        cudaStream_t st = op_begin(rdAB, {ra, rb});
+        check(launch_pack_pair(pa, pb, mode, st), "fused pack");
+        op_end();
       }
-      pa.rows = (int)hm;
-      pa.cols = (int)hk;
-      pa.prow_pad = (int)Mp;
-      pa.pcol_pad = (int)Kp;
-      pa.transpose = 0;
-      pa.p = p;
-      pa.barrett = p ? (uint32_t)(0x100000000ull / p) : 0;
-      pb.barrett = pa.barrett;
-      pb.rows = (int)hk;
-      pb.cols = (int)hn;
-      pb.prow_pad = (int)Np;
-      pb.pcol_pad = (int)Kp;
-      pb.transpose = 1;
-      pb.p = p;
-      // |S4|, |T4| <= 4 max|source|, a source <= nterm max|term entry|
-      pa.amax = amax;
-      pb.amax = amax ? amax + 1 : nullptr;
-      pa.terms = 4 * LL.n;
-      pb.terms = 4 * RL.n;
-      std::vector<Rect> rdAB{rh};
-      rdAB.insert(rdAB.end(), rdA.begin(), rdA.end());
-      rdAB.insert(rdAB.end(), rdB.begin(), rdB.end());
-      cudaStream_t st = op_begin(rdAB, {ra, rb});
-      check(launch_pack_pair(pa, pb, mode, st), "fused pack");
-      op_end();
       int tiles = 0;
       for (int j = 0; j < gn; ++j) {
         const int i = ord[g0 + j];              // the product in launch slot j
@@ -940,6 +969,138 @@ void Exec::table(Kind k, Scalar alpha, bool acc, Scalar beta, View L, View R, Vi
     }
     return r.n > 0;
   };
+  // One pack for every fused level of this table level.  When each product
+  // row's operands are signed sums of operand quadrants that no row
+  // overwrites (found by replaying the rows' symbolic sums, issuing
+  // nothing), the seven levels' 49 operands per side are formed in one
+  // pass that reads each sub-block of A and B once, instead of one pack per
+  // level re-reading the quadrants of every term (Table 9 reads 14 per
+  // side).  It stages all 49 operand pairs at once.
+  constexpr int64_t kLevelPackMaxBytes = 32ll << 30;
+  Prepacked pre[7] = {};
+  bool prepacked = false;
+  Lin pla[7], plb[7];
+  if (virt && stage_budget == 0) {
+    int nmul = 0;
+    bool okp = true;
+    bool hs[NLOC] = {};
+    Lin ss[NLOC];
+    auto operand = [&](Loc l, Shape sh, Lin &out) {
+      if (hs[l]) {
+        out = ss[l];
+        return true;
+      }
+      if (!operand_quad(l, sh)) return false;
+      out = Lin::of(at(l, sh));
+      return true;
+    };
+    for (const Row &row : *K.table) {
+      if ((row.dst >= A11 && row.dst <= A22) || (row.dst >= B11 && row.dst <= B22)) okp = false;
+      if (!okp) break;
+      if (row.op == OP_ADD) {
+        const bool unit = (row.c1 == CF_ONE || row.c1 == CF_NEG) && (row.c2 == CF_ONE || row.c2 == CF_NEG);
+        Lin x, y, r;
+        if (unit && is_tmp(row.dst) && row.shape != SH_C && operand(row.s1, row.shape, x) &&
+            operand(row.s2, row.shape, y) && compose(x, row.c1 == CF_ONE ? 1 : -1, y, row.c2 == CF_ONE ? 1 : -1, r)) {
+          ss[row.dst] = r;
+          hs[row.dst] = true;
+          continue;
+        }
+        okp = !hs[row.s1] && !hs[row.s2];  // a recorded sum would be written out
+        hs[row.dst] = false;
+      } else if (row.op == OP_COPY) {
+        okp = !hs[row.s1];
+        hs[row.dst] = false;
+      } else {
+        okp = nmul < 7 && operand(row.s1, SH_A, pla[nmul]) && operand(row.s2, SH_B, plb[nmul]);
+        ++nmul;
+        hs[row.dst] = false;
+      }
+    }
+    // each level's operand over the four operand quadrants of its side
+    int8_t qc[2][7][4] = {};
+    for (int j = 0; j < nmul && okp; ++j)
+      for (int side = 0; side < 2 && okp; ++side) {
+        const Lin &lj = side ? plb[j] : pla[j];
+        const View *quads = side ? Rq : Lq;
+        for (int t = 0; t < lj.n && okp; ++t) {
+          int Q = 0;
+          while (Q < 4 && !same(lj.v[t], quads[Q])) ++Q;
+          okp = Q < 4 && qc[side][j][Q] == 0;
+          if (okp) qc[side][j][Q] = lj.s[t];
+        }
+      }
+    int64_t abytes = 0, bbytes = 0;
+    if (okp && nmul == 7) level_bytes(pla[0].shape(), plb[0].shape(), abytes, bbytes);
+    const int64_t hdr = fp32 ? 1024 : 0, per = 7 * (abytes + bbytes);
+    if (okp && nmul == 7 && hdr + 7 * per <= kLevelPackMaxBytes) {
+      prepacked = true;
+      level_packs = true;
+      stage_need = std::max(stage_need, hdr + 7 * per);
+      ew_launches += fp32 ? 3 : 2;
+      pack_bytes += 4 * (L.rows * L.cols + R.rows * R.cols) + 7 * per;
+      if (!dry) {
+        char *base = next_stage();
+        if (!base) return;
+        uint32_t *amax = fp32 ? reinterpret_cast<uint32_t *>(base) : nullptr;
+        if (fp32) fp32_amax(amax, Lq, 4, Rq, 4);
+        PackLevel PL;
+        std::memset(&PL, 0, sizeof(PL));
+        PL.n = 7;
+        for (int side = 0; side < 2; ++side)
+          for (int Q = 0; Q < 4; ++Q) {
+            const View &qd = side ? Rq[Q] : Lq[Q];
+            for (int q = 0; q < 4; ++q) PL.src[side][Q][q] = qd.quad(q / 2, q % 2).ptr;
+            PL.ld[side][Q] = qd.ld;
+            PL.esz[side][Q] = (int8_t)qd.esz;
+          }
+        for (int j = 0; j < 7; ++j) {
+          pre[j].base = base;
+          pre[j].stg = base + hdr + j * per;
+          PackArgs pa, pb;  // extents, scale terms and output places of level j
+          pack_args(pla[j], plb[j], 0, 7, pre[j].stg, amax, pa, pb);
+          PL.out[0][j] = pa.out[0];
+          PL.out[1][j] = pb.out[0];
+          PL.terms[0][j] = pa.terms;
+          PL.terms[1][j] = pb.terms;
+          for (int side = 0; side < 2; ++side)
+            for (int Q = 0; Q < 4; ++Q) PL.coef[side][j][Q] = qc[side][j][Q];
+          if (j == 0) {
+            PL.rows[0] = pa.rows;
+            PL.cols[0] = pa.cols;
+            PL.prow_pad[0] = pa.prow_pad;
+            PL.pcol_pad[0] = pa.pcol_pad;
+            PL.rows[1] = pb.rows;
+            PL.cols[1] = pb.cols;
+            PL.prow_pad[1] = pb.prow_pad;
+            PL.pcol_pad[1] = pb.pcol_pad;
+            PL.p = pa.p;
+            PL.barrett = pa.barrett;
+          }
+        }
+        PL.ostride[0] = abytes / 2;
+        PL.ostride[1] = bbytes / 2;
+        PL.amax = amax;
+        // the two sides write disjoint parts of every level's staging, so
+        // the dataflow capture can run them at once
+        for (int side = 0; side < 2; ++side) {
+          std::vector<Rect> wr;
+          for (int j = 0; j < 7; ++j)
+            wr.push_back(side ? rect_bytes(pre[j].stg + 7 * abytes, 7 * bbytes) : rect_bytes(pre[j].stg, 7 * abytes));
+          cudaStream_t st = op_begin({side ? rect_of(R) : rect_of(L), rect_bytes(base, 8)}, wr);
+          check(launch_pack_level(PL, side, mode, st), "level pack");
+          op_end();
+        }
+      }
+    }
+  }
+  int jmul = 0;
+  auto same_lin = [&](const Lin &x, const Lin &y) {
+    if (x.n != y.n) return false;
+    for (int t = 0; t < x.n; ++t)
+      if (!same(x.v[t], y.v[t]) || x.s[t] != y.s[t]) return false;
+    return true;
+  };
   for (const Row &row : *K.table) {
     if (!ok()) return;
     if (row.op == OP_ADD) {
@@ -1002,7 +1163,11 @@ void Exec::table(Kind k, Scalar alpha, bool acc, Scalar beta, View L, View R, Vi
         // a fused level reads its operands (symbolic or not) and writes d
         const Lin la = has[row.s1] ? sym[row.s1] : Lin::of(a), lb = has[row.s2] ? sym[row.s2] : Lin::of(b);
         has[row.dst] = false;
-        fused_level(al, S.accumulate, be, la, lb, d);
+        if (prepacked && (jmul >= 7 || !same_lin(la, pla[jmul]) || !same_lin(lb, plb[jmul]))) {
+          if (fail.empty()) fail = "level pack: operands differ from the replay";
+          return;
+        }
+        fused_level(al, S.accumulate, be, la, lb, d, prepacked ? &pre[jmul++] : nullptr);
       } else {
         has[row.dst] = false;
         call(row.kind, al, S.accumulate, be, a, b, d, depth - 1, sub);

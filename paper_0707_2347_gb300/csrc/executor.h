@@ -87,6 +87,9 @@ struct Exec {
   int64_t stage_budget = 0;
   int stage_slots = 1;
   int stage_turn = 0;
+  // a table level packed the operands of all its fused levels in one launch
+  // (their staging is one area, so a Flow gets one slot, not two)
+  bool level_packs = false;
   // dataflow ordering over capture streams (null: every launch on `stream`)
   Flow *flow = nullptr;
   // Deferred leaf GEMM launches: products of leaf groups and fused levels
@@ -142,7 +145,18 @@ struct Exec {
   void canon(View v);
 
  private:
-  void fused_level(Scalar alpha, bool acc, Scalar beta, const Lin &L, const Lin &R, View D);
+  // operands of a fused level formed by its table level's one pack: this
+  // level's staging (its A operands, then its B operands) and the staging
+  // base that holds the FP32 amax words
+  struct Prepacked {
+    char *base;
+    char *stg;
+  };
+  void fused_level(Scalar alpha, bool acc, Scalar beta, const Lin &L, const Lin &R, View D,
+                   const Prepacked *pre = nullptr);
+  void level_bytes(const View &L, const View &R, int64_t &abytes, int64_t &bbytes) const;
+  void pack_args(const Lin &LL, const Lin &RL, int g0, int gn, char *stg, const uint32_t *amax, PackArgs &pa,
+                 PackArgs &pb) const;
   // would call() with these sizes and depth run a fused level?
   bool fuses(int64_t m, int64_t k, int64_t n, int depth) const;
   void peel(Kind k, Scalar alpha, bool acc, Scalar beta, View L, View R, View D, int depth, const Arena &ar);

@@ -67,12 +67,12 @@ __device__ __forceinline__ uint32_t red4p(uint32_t x, uint32_t p) {
   return min(x, x - p);
 }
 
-// 8 combined values -> plane 0 and plane 1 (16 bytes each)
-template <int MODE>
-__device__ __forceinline__ void convert8(const uint32_t (&x)[8], uint32_t p, float fs, uint4 &o0, uint4 &o1) {
-  uint32_t w0[4], w1[4];
+// N (even) combined values -> N/2 words of plane 0 and of plane 1
+template <int MODE, int N>
+__device__ __forceinline__ void convert_n(const uint32_t (&x)[N], uint32_t p, float fs, uint32_t (&w0)[N / 2],
+                                          uint32_t (&w1)[N / 2]) {
 #pragma unroll
-  for (int j = 0; j < 4; ++j) {
+  for (int j = 0; j < N / 2; ++j) {
     if (MODE == MODE_MODP2) {
       uint32_t u0 = centre16(x[2 * j], p), u1 = centre16(x[2 * j + 1], p);
       w0[j] = offset_to_h2(prmt(u0, u1, 0x6521u));               // h + 128 = u >> 8
@@ -92,8 +92,24 @@ __device__ __forceinline__ void convert8(const uint32_t (&x)[8], uint32_t p, flo
       w1[j] = *reinterpret_cast<const uint32_t *>(&lo);
     }
   }
+}
+
+// 8 combined values -> plane 0 and plane 1 (16 bytes each)
+template <int MODE>
+__device__ __forceinline__ void convert8(const uint32_t (&x)[8], uint32_t p, float fs, uint4 &o0, uint4 &o1) {
+  uint32_t w0[4], w1[4];
+  convert_n<MODE, 8>(x, p, fs, w0, w1);
   o0 = make_uint4(w0[0], w0[1], w0[2], w0[3]);
   o1 = make_uint4(w1[0], w1[1], w1[2], w1[3]);
+}
+
+// 4 combined values -> plane 0 and plane 1 (8 bytes each)
+template <int MODE>
+__device__ __forceinline__ void emit4(const uint32_t (&x)[4], uint32_t p, float fs, uint16_t *dst, int64_t plane) {
+  uint32_t w0[2], w1[2];
+  convert_n<MODE, 4>(x, p, fs, w0, w1);
+  *reinterpret_cast<uint2 *>(dst) = make_uint2(w0[0], w0[1]);
+  if (MODE != MODE_MODP1) *reinterpret_cast<uint2 *>(dst + plane) = make_uint2(w1[0], w1[1]);
 }
 
 // Bring a raw source value to the representative the combinations use:
@@ -290,25 +306,29 @@ __device__ __forceinline__ void load_source(const PackArgs &a, int q, int r, int
 // plain layout: thread = 8 consecutive columns of one row; every source
 // value is loaded and reduced once, then combined for each output.
 template <int MODE, int SET>
+__device__ __forceinline__ void pack_row_unit(const PackArgs &a, int64_t u, int64_t plane, float fs) {
+  const int r = (int)(u / (a.pcol_pad / 8));
+  const int c0 = (int)(u - (int64_t)r * (a.pcol_pad / 8)) * 8;
+  uint32_t v[kMaxSrc][8];
+#pragma unroll
+  for (int q = 0; q < kMaxSrc; ++q) {
+    if (q < a.nsrc) {
+      load_source<MODE, 8>(a, q, r, c0, v[q]);
+    } else {
+#pragma unroll
+      for (int e = 0; e < 8; ++e) v[q][e] = 0;
+    }
+  }
+  emit_all<MODE, SET>(a, v, (int64_t)r * a.pcol_pad + c0, plane, fs);
+}
+
+template <int MODE, int SET>
 __device__ __forceinline__ void pack_rows_body(const PackArgs &a, int block, int nblocks) {
   const int64_t units = (int64_t)a.prow_pad * (a.pcol_pad / 8);
   const int64_t plane = (int64_t)a.prow_pad * a.pcol_pad;
   const float fs = MODE == MODE_FP32 ? fp16_scale(*a.amax, a.terms) : 1.f;
-  for (int64_t u = block * (int64_t)blockDim.x + threadIdx.x; u < units; u += (int64_t)nblocks * blockDim.x) {
-    const int r = (int)(u / (a.pcol_pad / 8));
-    const int c0 = (int)(u - (int64_t)r * (a.pcol_pad / 8)) * 8;
-    uint32_t v[kMaxSrc][8];
-#pragma unroll
-    for (int q = 0; q < kMaxSrc; ++q) {
-      if (q < a.nsrc) {
-        load_source<MODE, 8>(a, q, r, c0, v[q]);
-      } else {
-#pragma unroll
-        for (int e = 0; e < 8; ++e) v[q][e] = 0;
-      }
-    }
-    emit_all<MODE, SET>(a, v, (int64_t)r * a.pcol_pad + c0, plane, fs);
-  }
+  for (int64_t u = block * (int64_t)blockDim.x + threadIdx.x; u < units; u += (int64_t)nblocks * blockDim.x)
+    pack_row_unit<MODE, SET>(a, u, plane, fs);
 }
 
 // transposed layout: a CTA stages a 32 (source rows) x 64 (source cols) tile
@@ -354,6 +374,149 @@ __global__ void __launch_bounds__(256) pack_pair_kernel(const __grid_constant__ 
   } else {
     const int i = (int)blockIdx.x - na;
     pack_cols_body<MODE, SB>(b, tile, i % tiles_x, i / tiles_x);
+  }
+}
+
+// ------------------------------------------------------------ level pack
+// Every fused level under one table level in one pass (PackLevel).  Level
+// j's operand quadrant q is sum_Q coef[j][Q] * (sub-block q of operand
+// quadrant Q), so each of the 16 sub-blocks is read from DRAM once per
+// position, held on chip, and all levels' 49 operands are formed from it.
+
+// level j's four Winograd sources at one position from the 16 sub-block
+// values w[Q][q][e] (reduced)
+template <int MODE, int N>
+__device__ __forceinline__ void level_sources(const PackLevel &L, int side, int j, const uint32_t (&w)[4][4][N],
+                                              uint32_t (&v)[4][N]) {
+  const uint32_t p = L.p;
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+#pragma unroll
+    for (int e = 0; e < N; ++e) v[q][e] = MODE == MODE_FP32 ? __float_as_uint(0.f) : 0u;
+#pragma unroll
+  for (int Q = 0; Q < 4; ++Q) {
+    const int c = L.coef[side][j][Q];
+    if (c == 0) continue;
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int e = 0; e < N; ++e) v[q][e] = c > 0 ? lin_add<MODE>(v[q][e], w[Q][q][e], p) : lin_sub<MODE>(v[q][e], w[Q][q][e], p);
+  }
+}
+
+// the seven Winograd outputs of one side from the four sources v (quadrants
+// X11, X12, X21, X22), N elements each, output i at out + i * ostride + off
+template <int MODE, int N, int SIDE>
+__device__ __forceinline__ void level_emit(const uint32_t (&v)[4][N], uint32_t p, float fs, uint16_t *out,
+                                           int64_t ostride, int64_t off, int64_t plane) {
+  uint32_t x[N], y[N], z[N];
+  auto put = [&](int i, const uint32_t (&t)[N]) {
+    if constexpr (N == 8) emit8<MODE>(t, p, fs, out + i * ostride + off, plane);
+    else emit4<MODE>(t, p, fs, out + i * ostride + off, plane);
+  };
+  if (SIDE == 0) {
+    put(0, v[0]);  // A11
+    put(1, v[1]);  // A12
+    put(3, v[3]);  // A22
+#pragma unroll
+    for (int e = 0; e < N; ++e) {
+      x[e] = lin_add<MODE>(v[2][e], v[3][e], p);  // S1 = A21 + A22
+      y[e] = lin_sub<MODE>(x[e], v[0][e], p);     // S2 = S1 - A11
+      z[e] = lin_sub<MODE>(v[1][e], y[e], p);     // S4 = A12 - S2
+    }
+    put(4, x);
+    put(5, y);
+    put(2, z);
+#pragma unroll
+    for (int e = 0; e < N; ++e) z[e] = lin_sub<MODE>(v[0][e], v[2][e], p);  // S3 = A11 - A21
+    put(6, z);
+  } else {
+    put(0, v[0]);  // B11
+    put(1, v[2]);  // B21
+    put(2, v[3]);  // B22
+#pragma unroll
+    for (int e = 0; e < N; ++e) {
+      x[e] = lin_sub<MODE>(v[1][e], v[0][e], p);  // T1 = B12 - B11
+      y[e] = lin_sub<MODE>(v[3][e], x[e], p);     // T2 = B22 - T1
+      z[e] = lin_sub<MODE>(y[e], v[2][e], p);     // T4 = T2 - B21
+    }
+    put(4, x);
+    put(5, y);
+    put(3, z);
+#pragma unroll
+    for (int e = 0; e < N; ++e) z[e] = lin_sub<MODE>(v[3][e], v[1][e], p);  // T3 = B22 - B12
+    put(6, z);
+  }
+}
+
+// plain side (A): a thread takes 4 consecutive columns of one row of every
+// sub-block (64 values in registers), then writes every level's outputs
+template <int MODE>
+__global__ void __launch_bounds__(256) level_rows_kernel(const __grid_constant__ PackLevel L) {
+  const int rows = L.rows[0], cols = L.cols[0], pc = L.pcol_pad[0];
+  const int64_t units = (int64_t)L.prow_pad[0] * (pc / 4);
+  const int64_t plane = (int64_t)L.prow_pad[0] * pc;
+  for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < units; u += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(u / (pc / 4));
+    const int c0 = (int)(u - (int64_t)r * (pc / 4)) * 4;
+    uint32_t w[4][4][4];
+#pragma unroll
+    for (int Q = 0; Q < 4; ++Q)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        load_row<4>(L.src[0][Q][q], L.ld[0][Q], r, c0, rows, cols, w[Q][q], L.esz[0][Q]);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) w[Q][q][e] = source_value<MODE>(w[Q][q][e], L.p, L.barrett);
+      }
+    for (int j = 0; j < L.n; ++j) {
+      uint32_t v[4][4];
+      level_sources<MODE, 4>(L, 0, j, w, v);
+      const float fs = MODE == MODE_FP32 ? fp16_scale(L.amax[0], L.terms[0][j]) : 1.f;
+      level_emit<MODE, 4, 0>(v, L.p, fs, L.out[0][j], L.ostride[0], (int64_t)r * pc + c0, plane);
+    }
+  }
+}
+
+// transposed side (B): a block stages a 64 (source rows) x 16 (source cols)
+// tile of every sub-block in shared memory; a thread then takes 4 source
+// rows of one source column (packed row = that column; 16 threads write 128
+// contiguous bytes of it) and writes every level's outputs
+constexpr int kLvlTileK = 64, kLvlTileN = 16;
+template <int MODE>
+__global__ void __launch_bounds__(256) level_cols_kernel(const __grid_constant__ PackLevel L, int tiles_x) {
+  extern __shared__ uint32_t lvl_tile[];  // [16][kLvlTileK][kLvlTileN + 1]
+  constexpr int W = kLvlTileN + 1;
+  const int rows = L.rows[1], cols = L.cols[1], pc = L.pcol_pad[1];
+  const int64_t plane = (int64_t)L.prow_pad[1] * pc;
+  const int bx = blockIdx.x % tiles_x, by = blockIdx.x / tiles_x;
+  const int r0 = by * kLvlTileK, c0 = bx * kLvlTileN, t = threadIdx.x;
+  {
+    const int rr = t >> 2, cc = (t & 3) * 4;
+#pragma unroll
+    for (int Q = 0; Q < 4; ++Q)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        uint32_t x[4];
+        load_row<4>(L.src[1][Q][q], L.ld[1][Q], r0 + rr, c0 + cc, rows, cols, x, L.esz[1][Q]);
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+          lvl_tile[((Q * 4 + q) * kLvlTileK + rr) * W + cc + e] = source_value<MODE>(x[e], L.p, L.barrett);
+      }
+  }
+  __syncthreads();
+  const int pcol = t >> 4, pr4 = (t & 15) * 4;
+  uint32_t w[4][4][4];
+#pragma unroll
+  for (int Q = 0; Q < 4; ++Q)
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) w[Q][q][e] = lvl_tile[((Q * 4 + q) * kLvlTileK + pr4 + e) * W + pcol];
+  for (int j = 0; j < L.n; ++j) {
+    uint32_t v[4][4];
+    level_sources<MODE, 4>(L, 1, j, w, v);
+    const float fs = MODE == MODE_FP32 ? fp16_scale(L.amax[1], L.terms[1][j]) : 1.f;
+    level_emit<MODE, 4, 1>(v, L.p, fs, L.out[1][j], L.ostride[1], (int64_t)(c0 + pcol) * pc + r0 + pr4, plane);
   }
 }
 
@@ -1302,6 +1465,49 @@ cudaError_t launch_pack_pair(const PackArgs &a, const PackArgs &b, int mode, cud
     case MODE_MODP1: return pair_mode<MODE_MODP1>(a, b, s);
     case MODE_MODP2: return pair_mode<MODE_MODP2>(a, b, s);
     case MODE_FP32: return pair_mode<MODE_FP32>(a, b, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <int MODE>
+static cudaError_t level_mode(const PackLevel &L, int side, cudaStream_t s) {
+  if (side == 0) {
+    const int64_t units = (int64_t)L.prow_pad[0] * (L.pcol_pad[0] / 4);
+    const int64_t want = (units + 255) / 256;
+    const int na = (int)(want > 152 * 8 ? 152 * 8 : want);
+    if (na > 0) dev::level_rows_kernel<MODE><<<na, 256, 0, s>>>(L);
+    return cudaGetLastError();
+  }
+  constexpr int smem = 16 * dev::kLvlTileK * (dev::kLvlTileN + 1) * 4;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(dev::level_cols_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  const int tiles_x = L.prow_pad[1] / dev::kLvlTileN, tiles = tiles_x * (L.pcol_pad[1] / dev::kLvlTileK);
+  if (tiles > 0) dev::level_cols_kernel<MODE><<<tiles, 256, smem, s>>>(L, tiles_x);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pack_level(const PackLevel &L, int side, int mode, cudaStream_t s) {
+  if (L.n < 1 || L.n > kMaxOut || side < 0 || side > 1) return cudaErrorInvalidValue;
+  const int planes = mode == MODE_MODP1 ? 1 : 2;
+  for (int side = 0; side < 2; ++side) {
+    if (L.prow_pad[side] <= 0 || L.pcol_pad[side] <= 0 || L.prow_pad[side] % 64 || L.pcol_pad[side] % 64 ||
+        L.rows[side] < 0 || L.cols[side] < 0 ||
+        L.ostride[side] < planes * (int64_t)L.prow_pad[side] * L.pcol_pad[side])
+      return cudaErrorInvalidValue;
+    for (int Q = 0; Q < 4; ++Q)
+      if (L.esz[side][Q] != 4 && L.esz[side][Q] != 2) return cudaErrorInvalidValue;
+  }
+  if (L.prow_pad[0] < L.rows[0] || L.pcol_pad[0] < L.cols[0] || L.prow_pad[1] < L.cols[1] ||
+      L.pcol_pad[1] < L.rows[1])
+    return cudaErrorInvalidValue;
+  switch (mode) {
+    case MODE_MODP1: return level_mode<MODE_MODP1>(L, side, s);
+    case MODE_MODP2: return level_mode<MODE_MODP2>(L, side, s);
+    case MODE_FP32: return level_mode<MODE_FP32>(L, side, s);
   }
   return cudaErrorInvalidValue;
 }

@@ -105,6 +105,31 @@ struct PackArgs {
 enum PackSet : int { PACK_GENERIC = 0, PACK_WINOGRAD_A = 1, PACK_WINOGRAD_B = 2 };
 // a (plain layout) and b (transposed: packed row = source column) in one launch
 cudaError_t launch_pack_pair(const PackArgs &a, const PackArgs &b, int mode, cudaStream_t s);
+// The packs of the n fused levels under one table level in one pass.  Side
+// 0 is the A side (plain layout), side 1 the B side (transposed).  src[s][Q]
+// [q] is sub-block q (X11, X12, X21, X22) of operand quadrant Q of side s;
+// level j's operand is sum_Q coef[s][j][Q] * quadrant Q, and its seven
+// Winograd outputs (Section 2's sums; the order of the Winograd pack sets)
+// are at out[s][j] + i * ostride[s] halves.  rows x cols is a sub-block's
+// extent, prow_pad x pcol_pad an output's packed extent (multiples of 64).
+// launch_pack_level forms one side's outputs (the two sides may run at
+// once).
+struct PackLevel {
+  const char *src[2][4][4];
+  int64_t ld[2][4];
+  int8_t esz[2][4];  // 4, or 2 (16-bit mod p values)
+  int8_t coef[2][kMaxOut][4];
+  uint16_t *out[2][kMaxOut];
+  int64_t ostride[2];
+  int32_t rows[2], cols[2], prow_pad[2], pcol_pad[2];
+  // FP32 mode: amax[s] bounds every entry of side s, terms[s][j] the sum of
+  // |coefficients| of level j's operands (the scale fp16_scale uses)
+  const uint32_t *amax;
+  int32_t terms[2][kMaxOut];
+  uint32_t p, barrett;
+  int32_t n;
+};
+cudaError_t launch_pack_level(const PackLevel &L, int side, int mode, cudaStream_t s);
 
 // ---------------------------------------------------------------- leaf GEMM
 // One product of a grouped leaf launch: P = A' x B' from packed operands.

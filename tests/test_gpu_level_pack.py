@@ -1,0 +1,79 @@
+"""One pack for all seven fused levels under a table level.
+
+At 8192^2 and depth 2 the top level's quadrants (4096^2, 64 MiB) are large
+enough for symbolic pre-additions, so with Table 9 (read-only A and B) every
+product row's operands are signed sums of operand quadrants and one launch
+packs the 49 operand pairs.  Results must match the oracle's classical
+product bit for bit on sampled rows, Freivalds' check on the whole result,
+and the per-level packs of a bounded-staging call (SWMM_FLAG_LOWMEM, which
+never packs a whole table level) bit for bit.  The staging the call reports
+is the 49 pairs' (one slot, also in a graph with the dataflow capture).
+Table 3 overwrites its operand quadrants, so it must keep per-level packs.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import classical, probes
+from paper_0707_2347_gb300 import swmm as S
+from tests.gpu_util import dev, fp_inputs, host, modp_inputs
+
+pytestmark = pytest.mark.gpu
+
+N = 8192
+PAIR = 2 * (2 * 2048 * 2048 * 2)  # one product's A and B operands: 2 limb planes of fp16
+LEVEL = 49 * PAIR
+
+
+@pytest.mark.parametrize("flags", [0, S.FLAG_GRAPH], ids=["eager", "graph"])
+def test_level_pack_t9_modp(handle, flags):
+    p = 65521
+    A, B, C = modp_inputs(N, N, N, p, tag=21)
+    dA, dB = dev(A), dev(B)
+    dC = dev(C)
+    o = S.Opts(mode=S.MODP, p=p, sched=S.T9_ACC, depth=2, flags=flags)
+    for _ in range(2 if flags else 1):  # a graph: capture, then replay
+        dC.copy_(dev(C))
+        handle.muladd(3, dA, dB, 5, dC, o)
+    handle.sync()
+    st = handle.stats()
+    assert st["staging_bytes"] == LEVEL
+    assert st["plan_extra_elems"] == st["paper_extra_elems"] == 2 * 4096 * 4096  # Table 9: two temporaries
+    out = host(dC)
+    rows = np.sort(np.random.default_rng(3).choice(N, 24, replace=False))
+    assert np.array_equal(out[rows], classical.rows_muladd_modp(rows, 3, A, B, 5, C, p))
+    assert probes.freivalds_modp(3, A, B, 5, C, out, p, vectors=2)
+    dL = dev(C)
+    handle.muladd(3, dA, dB, 5, dL, S.Opts(mode=S.MODP, p=p, sched=S.T9_ACC, depth=2, flags=S.FLAG_LOWMEM))
+    handle.sync()
+    assert handle.stats()["staging_bytes"] <= S.LOWMEM_STAGE_BYTES
+    assert torch.equal(dL, dC)
+    assert np.array_equal(host(dA), A) and np.array_equal(host(dB), B)
+
+
+def test_level_pack_t9_fp32(handle):
+    A, B, C = fp_inputs(N, N, N, tag=22)
+    dA, dB, dC = dev(A), dev(B), dev(C)
+    handle.muladd(1.0, dA, dB, 1.0, dC, S.Opts(mode=S.FP32, sched=S.T9_ACC, depth=2))
+    handle.sync()
+    assert handle.stats()["staging_bytes"] == LEVEL + 1024  # plus the amax words
+    rows = np.sort(np.random.default_rng(4).choice(N, 16, replace=False))
+    exact = A[rows].astype(np.float64) @ B.astype(np.float64) + C[rows].astype(np.float64)
+    scale = float(np.abs(A).max()) * float(np.abs(B).max())
+    err = float(np.abs(host(dC)[rows] - exact).max()) / scale
+    assert err <= probes.fp_bound(N), err
+
+
+def test_inplace_table_keeps_level_packs(handle):
+    """Table 3 overwrites A and B quadrants between its products, so its
+    levels pack one at a time (an eager call stages one level)."""
+    p = 65521
+    A, B, _ = modp_inputs(N, N, N, p, tag=23)
+    dA, dB = dev(A), dev(B)
+    dC = torch.zeros((N, N), dtype=torch.int32, device=dA.device)
+    handle.mul_inplace(dA, dB, dC, S.Opts(mode=S.MODP, p=p, sched=S.T3_IP, depth=2))
+    handle.sync()
+    assert handle.stats()["staging_bytes"] == 7 * PAIR
+    out = host(dC)
+    rows = np.sort(np.random.default_rng(5).choice(N, 16, replace=False))
+    assert np.array_equal(out[rows], classical.rows_muladd_modp(rows, 1, A, B, 0, None, p))
