@@ -897,10 +897,12 @@ void Exec::table(Kind k, Scalar alpha, bool acc, Scalar beta, View L, View R, Vi
   };
   // Pre-additions kept symbolic.  When every product of this level is a
   // fused level, a row that writes a signed sum of operand quadrants into a
-  // temporary only records the sum (a Lin); the fused level forms it while
-  // packing.  A recorded sum is written out before any other kind of row
-  // reads the temporary, and before any row writes a block it refers to, so
-  // every value the table reads is the one its rows define.  Only for
+  // temporary, or into a block of C (searched schedules park S and T values
+  // there while C is dead), only records the sum (a Lin); the fused level
+  // forms it while packing.  A recorded sum is written out before any other
+  // kind of row reads its location, and before any row writes a block it
+  // refers to, so every value the table reads is the one its rows define;
+  // a sum still recorded in C when the table ends is written out.  Only for
   // quadrants above kVirtMinBytes: smaller blocks stay in L2 between an
   // addition and its reader, and re-reading several terms in the pack then
   // costs more than the addition saves.
@@ -911,6 +913,7 @@ void Exec::table(Kind k, Scalar alpha, bool acc, Scalar beta, View L, View R, Vi
   View symdst[NLOC];
   bool has[NLOC] = {};
   auto is_tmp = [](Loc l) { return l == LX || l == LY || l == LZ; };
+  auto sym_dst = [&](Loc l) { return is_tmp(l) || (l >= C11 && l <= C22); };  // may hold a recorded sum
   auto operand_quad = [](Loc l, Shape sh) {
     return (sh == SH_A && l >= A11 && l <= A22) || (sh == SH_B && l >= B11 && l <= B22);
   };
@@ -929,7 +932,8 @@ void Exec::table(Kind k, Scalar alpha, bool acc, Scalar beta, View L, View R, Vi
   };
   auto before_write = [&](const View &w) {
     const Rect rw = rect_of(w);
-    for (Loc l : {LX, LY, LZ}) {
+    for (int li = 0; li < NLOC; ++li) {
+      const Loc l = (Loc)li;
       if (!has[l]) continue;
       for (int t = 0; t < sym[l].n; ++t)
         if (overlaps(rect_of(sym[l].v[t]), rw)) {
@@ -1000,7 +1004,7 @@ void Exec::table(Kind k, Scalar alpha, bool acc, Scalar beta, View L, View R, Vi
       if (row.op == OP_ADD) {
         const bool unit = (row.c1 == CF_ONE || row.c1 == CF_NEG) && (row.c2 == CF_ONE || row.c2 == CF_NEG);
         Lin x, y, r;
-        if (unit && is_tmp(row.dst) && row.shape != SH_C && operand(row.s1, row.shape, x) &&
+        if (unit && sym_dst(row.dst) && row.shape != SH_C && operand(row.s1, row.shape, x) &&
             operand(row.s2, row.shape, y) && compose(x, row.c1 == CF_ONE ? 1 : -1, y, row.c2 == CF_ONE ? 1 : -1, r)) {
           ss[row.dst] = r;
           hs[row.dst] = true;
@@ -1110,7 +1114,7 @@ void Exec::table(Kind k, Scalar alpha, bool acc, Scalar beta, View L, View R, Vi
       nar[row.dst] = nd;
       bool recorded = false;
       const bool unit = (row.c1 == CF_ONE || row.c1 == CF_NEG) && (row.c2 == CF_ONE || row.c2 == CF_NEG);
-      if (virt && unit && is_tmp(row.dst) && row.shape != SH_C &&
+      if (virt && unit && sym_dst(row.dst) && row.shape != SH_C &&
           (has[row.s1] || operand_quad(row.s1, row.shape)) && (has[row.s2] || operand_quad(row.s2, row.shape))) {
         Lin r;
         const Lin x = has[row.s1] ? sym[row.s1] : Lin::of(a), y = has[row.s2] ? sym[row.s2] : Lin::of(b);
@@ -1174,6 +1178,7 @@ void Exec::table(Kind k, Scalar alpha, bool acc, Scalar beta, View L, View R, Vi
       }
     }
   }
+  for (int li = C11; li <= C22 && ok(); ++li) materialize((Loc)li);  // temporaries are dead here
   if (!ar.carve) {
     ws_top = mark_top;
     tmp_elems = mark_elems;

@@ -77,3 +77,42 @@ def test_inplace_table_keeps_level_packs(handle):
     out = host(dC)
     rows = np.sort(np.random.default_rng(5).choice(N, 16, replace=False))
     assert np.array_equal(out[rows], classical.rows_muladd_modp(rows, 1, A, B, 0, None, p))
+
+
+@pytest.mark.parametrize("name", ["ab12", "acc16", "aclr14", "accr14"])
+def test_searched_schedules_symbolic_at_8192(handle, name):
+    """The shipped searched schedules at 8192^2 depth 2, where the top
+    level's pre-additions are symbolic: ab12 parks S and T values in blocks
+    of C (recorded, not written, then packed in one pass with the other
+    levels); aclr14 and accr14 overwrite operand quadrants (per-level
+    packs).  Sampled rows against the oracle, Freivalds on the whole result,
+    and the restored inputs bit-exact."""
+    from paper_0707_2347_gb300 import schedules_found as F
+    from paper_0707_2347_gb300 import search as Q
+    rows_, spec = F.rows(name), F.spec(name)
+    Q.set_schedule(handle, rows_, **spec)
+    p, alpha, beta = 65521, 3, 5
+    A, B, C = modp_inputs(N, N, N, p, tag=24)
+    dA, dB, dC = dev(A), dev(B), dev(C)
+    o = S.Opts(mode=S.MODP, p=p, sched=S.CUSTOM, depth=2)
+    if not spec["accumulate"]:
+        beta = 0
+        handle.mul(dA, dB, dC, o)
+        alpha = 1
+    elif len(spec["preserve"]) == 8:
+        handle.muladd(alpha, dA, dB, beta, dC, o)
+    else:
+        handle.mul_inplace(dA, dB, dC, o, alpha=alpha, beta=beta)
+    handle.sync()
+    if name == "ab12":
+        assert handle.stats()["staging_bytes"] == LEVEL
+    out = host(dC)
+    rows = np.sort(np.random.default_rng(7).choice(N, 16, replace=False))
+    assert np.array_equal(out[rows], classical.rows_muladd_modp(rows, alpha, A, B, beta, C if beta else None, p))
+    assert probes.freivalds_modp(alpha, A, B, beta, C if beta else None, out, p, vectors=2)
+    h = N // 2
+    hA, hB = host(dA), host(dB)
+    for blk in spec["preserve"]:
+        M, M0 = (hA, A) if blk[0] == "A" else (hB, B)
+        i, j = int(blk[1]) - 1, int(blk[2]) - 1
+        assert np.array_equal(M[i * h:(i + 1) * h, j * h:(j + 1) * h], M0[i * h:(i + 1) * h, j * h:(j + 1) * h]), blk
