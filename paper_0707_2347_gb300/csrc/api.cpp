@@ -274,7 +274,7 @@ void reset_counts(Exec &x) {
   x.tmp_elems = x.tmp_peak_elems = 0;
   x.add_elems = x.leaf_flops = x.leaf_launches = x.ew_launches = x.leaf_products = 0;
   x.pack_bytes = 0;
-  x.level_packs = false;
+  x.level_packs = 0;
   x.lazy_views.clear();
   x.stage_turn = 0;
 }
@@ -457,8 +457,9 @@ int make_plan(swmm_t h, const Req &q, const swmm_opts *o, bool check_ptrs, Plan 
   execute(P, x);
   x.flush();
   if (!x.fail.empty()) return fail(h, SWMM_EINVAL, x.fail);
-  // small leaf launches share launches (four staging slots in turn)
-  if (x.stage_need > 0 && x.stage_need <= kMergeStageBytes && !x.simt && x.leaf_launches > 1 &&
+  // small leaf launches share launches (four staging slots in turn; leaf
+  // launches of prepacked levels need no slot of their own)
+  if (x.stage_need > 0 && (x.stage_need <= kMergeStageBytes || x.level_packs) && !x.simt && x.leaf_launches > 1 &&
       x.stage_budget == 0) {
     reset_counts(x);
     x.merge = true;
@@ -509,7 +510,7 @@ int enqueue(swmm_t h, const Plan &P, cudaStream_t stream, TimingHook *timing, co
   const Exec &x = P.x;
   Exec r = x;
   r.merge = x.merge && !ext;
-  r.stage_slots = r.merge ? 4 : (use_flow && x.stage_budget == 0 && !x.level_packs ? 2 : 1);
+  r.stage_slots = x.level_packs ? (x.level_packs > 1 ? 2 : 1) : (r.merge ? 4 : (use_flow && x.stage_budget == 0 ? 2 : 1));
   const int64_t stage_bytes = r.stage_slots * ((x.stage_need + 1023) / 1024 * 1024);
   r.dry = false;
   r.lazy_views.clear();

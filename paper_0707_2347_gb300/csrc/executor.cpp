@@ -906,9 +906,12 @@ void Exec::table(Kind k, Scalar alpha, bool acc, Scalar beta, View L, View R, Vi
   // quadrants above kVirtMinBytes: smaller blocks stay in L2 between an
   // addition and its reader, and re-reading several terms in the pack then
   // costs more than the addition saves.
-  constexpr int64_t kVirtMinBytes = 32ll << 20;
-  const bool virt = !simt && fuses(hm, hk, hn, depth - 1) && 4 * hm * hk >= kVirtMinBytes &&
-                    4 * hk * hn >= kVirtMinBytes;
+  // With one pack for the whole level (below) every sub-block is read once,
+  // so the sums are kept symbolic down to kLevelPackMinBytes quadrants.
+  constexpr int64_t kVirtMinBytes = 32ll << 20, kLevelPackMinBytes = 4ll << 20;
+  const bool fuses_below = !simt && fuses(hm, hk, hn, depth - 1);
+  bool virt = fuses_below && 4 * hm * hk >= kVirtMinBytes && 4 * hk * hn >= kVirtMinBytes;
+  const bool level_pack_size = fuses_below && 4 * hm * hk >= kLevelPackMinBytes && 4 * hk * hn >= kLevelPackMinBytes;
   Lin sym[NLOC];
   View symdst[NLOC];
   bool has[NLOC] = {};
@@ -984,7 +987,7 @@ void Exec::table(Kind k, Scalar alpha, bool acc, Scalar beta, View L, View R, Vi
   Prepacked pre[7] = {};
   bool prepacked = false;
   Lin pla[7], plb[7];
-  if (virt && stage_budget == 0) {
+  if (level_pack_size && stage_budget == 0) {
     int nmul = 0;
     bool okp = true;
     bool hs[NLOC] = {};
@@ -1039,7 +1042,8 @@ void Exec::table(Kind k, Scalar alpha, bool acc, Scalar beta, View L, View R, Vi
     const int64_t hdr = fp32 ? 1024 : 0, per = 7 * (abytes + bbytes);
     if (okp && nmul == 7 && hdr + 7 * per <= kLevelPackMaxBytes) {
       prepacked = true;
-      level_packs = true;
+      virt = true;
+      ++level_packs;
       stage_need = std::max(stage_need, hdr + 7 * per);
       ew_launches += fp32 ? 3 : 2;
       pack_bytes += 4 * (L.rows * L.cols + R.rows * R.cols) + 7 * per;

@@ -87,9 +87,10 @@ struct Exec {
   int64_t stage_budget = 0;
   int stage_slots = 1;
   int stage_turn = 0;
-  // a table level packed the operands of all its fused levels in one launch
-  // (their staging is one area, so a Flow gets one slot, not two)
-  bool level_packs = false;
+  // table levels that packed the operands of all their fused levels in one
+  // pass (each stages one area; two areas in turn when there are several,
+  // so one level's pack need not wait for the previous level's products)
+  int level_packs = 0;
   // dataflow ordering over capture streams (null: every launch on `stream`)
   Flow *flow = nullptr;
   // Deferred leaf GEMM launches: products of leaf groups and fused levels
