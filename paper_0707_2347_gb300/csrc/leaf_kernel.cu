@@ -449,6 +449,20 @@ __device__ __forceinline__ void level_emit(const uint32_t (&v)[4][N], uint32_t p
   }
 }
 
+// L2 prefetch of the 4 elements at (r, c) of every sub-block of one side
+// (in-bounds positions only), so that the next tile's loads, issued after
+// this tile's stores, find their lines in L2
+__device__ __forceinline__ void level_prefetch(const PackLevel &L, int side, int r, int c) {
+  if (r >= L.rows[side] || c >= L.cols[side]) return;
+#pragma unroll
+  for (int Q = 0; Q < 4; ++Q)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const char *a = L.src[side][Q][q] + (int64_t)L.esz[side][Q] * ((int64_t)r * L.ld[side][Q] + c);
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(a));
+    }
+}
+
 // plain side (A): a thread takes 4 consecutive columns of one row of every
 // sub-block (64 values in registers), then writes every level's outputs
 template <int MODE>
@@ -456,7 +470,8 @@ __global__ void __launch_bounds__(256) level_rows_kernel(const __grid_constant__
   const int rows = L.rows[0], cols = L.cols[0], pc = L.pcol_pad[0];
   const int64_t units = (int64_t)L.prow_pad[0] * (pc / 4);
   const int64_t plane = (int64_t)L.prow_pad[0] * pc;
-  for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < units; u += (int64_t)gridDim.x * blockDim.x) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < units; u += stride) {
     const int r = (int)(u / (pc / 4));
     const int c0 = (int)(u - (int64_t)r * (pc / 4)) * 4;
     uint32_t w[4][4][4];
@@ -483,15 +498,16 @@ __global__ void __launch_bounds__(256) level_rows_kernel(const __grid_constant__
 // contiguous bytes of it) and writes every level's outputs
 constexpr int kLvlTileK = 64, kLvlTileN = 16;
 template <int MODE>
-__global__ void __launch_bounds__(256) level_cols_kernel(const __grid_constant__ PackLevel L, int tiles_x) {
+__global__ void __launch_bounds__(256) level_cols_kernel(const __grid_constant__ PackLevel L, int tiles_x, int tiles) {
   extern __shared__ uint32_t lvl_tile[];  // [16][kLvlTileK][kLvlTileN + 1]
   constexpr int W = kLvlTileN + 1;
   const int rows = L.rows[1], cols = L.cols[1], pc = L.pcol_pad[1];
   const int64_t plane = (int64_t)L.prow_pad[1] * pc;
-  const int bx = blockIdx.x % tiles_x, by = blockIdx.x / tiles_x;
-  const int r0 = by * kLvlTileK, c0 = bx * kLvlTileN, t = threadIdx.x;
-  {
-    const int rr = t >> 2, cc = (t & 3) * 4;
+  const int t = threadIdx.x, rr = t >> 2, cc = (t & 3) * 4;
+  for (int i = blockIdx.x; i < tiles; i += gridDim.x) {
+    const int bx = i % tiles_x, by = i / tiles_x;
+    const int r0 = by * kLvlTileK, c0 = bx * kLvlTileN;
+    if (i > (int)blockIdx.x) __syncthreads();  // the previous tile's reads are done
 #pragma unroll
     for (int Q = 0; Q < 4; ++Q)
 #pragma unroll
@@ -502,21 +518,25 @@ __global__ void __launch_bounds__(256) level_cols_kernel(const __grid_constant__
         for (int e = 0; e < 4; ++e)
           lvl_tile[((Q * 4 + q) * kLvlTileK + rr) * W + cc + e] = source_value<MODE>(x[e], L.p, L.barrett);
       }
-  }
-  __syncthreads();
-  const int pcol = t >> 4, pr4 = (t & 15) * 4;
-  uint32_t w[4][4][4];
+    __syncthreads();
+    if (i + (int)gridDim.x < tiles) {  // the next tile's lines, while this one is written
+      const int in = i + gridDim.x;
+      level_prefetch(L, 1, (in / tiles_x) * kLvlTileK + rr, (in % tiles_x) * kLvlTileN + cc);
+    }
+    const int pcol = t >> 4, pr4 = (t & 15) * 4;
+    uint32_t w[4][4][4];
 #pragma unroll
-  for (int Q = 0; Q < 4; ++Q)
+    for (int Q = 0; Q < 4; ++Q)
 #pragma unroll
-    for (int q = 0; q < 4; ++q)
+      for (int q = 0; q < 4; ++q)
 #pragma unroll
-      for (int e = 0; e < 4; ++e) w[Q][q][e] = lvl_tile[((Q * 4 + q) * kLvlTileK + pr4 + e) * W + pcol];
-  for (int j = 0; j < L.n; ++j) {
-    uint32_t v[4][4];
-    level_sources<MODE, 4>(L, 1, j, w, v);
-    const float fs = MODE == MODE_FP32 ? fp16_scale(L.amax[1], L.terms[1][j]) : 1.f;
-    level_emit<MODE, 4, 1>(v, L.p, fs, L.out[1][j], L.ostride[1], (int64_t)(c0 + pcol) * pc + r0 + pr4, plane);
+        for (int e = 0; e < 4; ++e) w[Q][q][e] = lvl_tile[((Q * 4 + q) * kLvlTileK + pr4 + e) * W + pcol];
+    for (int j = 0; j < L.n; ++j) {
+      uint32_t v[4][4];
+      level_sources<MODE, 4>(L, 1, j, w, v);
+      const float fs = MODE == MODE_FP32 ? fp16_scale(L.amax[1], L.terms[1][j]) : 1.f;
+      level_emit<MODE, 4, 1>(v, L.p, fs, L.out[1][j], L.ostride[1], (int64_t)(c0 + pcol) * pc + r0 + pr4, plane);
+    }
   }
 }
 
@@ -1486,7 +1506,8 @@ static cudaError_t level_mode(const PackLevel &L, int side, cudaStream_t s) {
     attr_set = true;
   }
   const int tiles_x = L.prow_pad[1] / dev::kLvlTileN, tiles = tiles_x * (L.pcol_pad[1] / dev::kLvlTileK);
-  if (tiles > 0) dev::level_cols_kernel<MODE><<<tiles, 256, smem, s>>>(L, tiles_x);
+  const int grid = tiles < 152 * 2 ? tiles : 152 * 2;  // two resident blocks per SM (registers)
+  if (tiles > 0) dev::level_cols_kernel<MODE><<<grid, 256, smem, s>>>(L, tiles_x, tiles);
   return cudaGetLastError();
 }
 
