@@ -103,6 +103,15 @@ __device__ __forceinline__ void convert8(const uint32_t (&x)[8], uint32_t p, flo
   o1 = make_uint4(w1[0], w1[1], w1[2], w1[3]);
 }
 
+// 2 combined values -> plane 0 and plane 1 (4 bytes each)
+template <int MODE>
+__device__ __forceinline__ void emit2(const uint32_t (&x)[2], uint32_t p, float fs, uint16_t *dst, int64_t plane) {
+  uint32_t w0[1], w1[1];
+  convert_n<MODE, 2>(x, p, fs, w0, w1);
+  *reinterpret_cast<uint32_t *>(dst) = w0[0];
+  if (MODE != MODE_MODP1) *reinterpret_cast<uint32_t *>(dst + plane) = w1[0];
+}
+
 // 4 combined values -> plane 0 and plane 1 (8 bytes each)
 template <int MODE>
 __device__ __forceinline__ void emit4(const uint32_t (&x)[4], uint32_t p, float fs, uint16_t *dst, int64_t plane) {
@@ -232,7 +241,7 @@ __device__ __forceinline__ void emit_all(const PackArgs &a, const uint32_t (&v)[
   }
 }
 
-// n consecutive elements (n = 8 or 4) of row r from column c of one block of
+// n consecutive elements (n = 8, 4 or 2) of row r from column c of one block of
 // 32-bit (esz 4) or 16-bit (esz 2) elements; 0 outside rows x cols; vector
 // loads when aligned
 template <int N>
@@ -248,10 +257,12 @@ __device__ __forceinline__ void load_row(const char *blk, int64_t ld, int r, int
         h[1] = x.y;
         h[2] = x.z;
         h[3] = x.w;
-      } else {
+      } else if constexpr (N == 4) {
         const uint2 x = *reinterpret_cast<const uint2 *>(base);
         h[0] = x.x;
         h[1] = x.y;
+      } else {
+        h[0] = *reinterpret_cast<const uint32_t *>(base);
       }
 #pragma unroll
       for (int i = 0; i < N / 2; ++i) {
@@ -265,7 +276,11 @@ __device__ __forceinline__ void load_row(const char *blk, int64_t ld, int r, int
     }
     return;
   }
-  if (r < rows && c + N <= cols && ((uintptr_t)base & 15) == 0) {
+  if (N == 2 && r < rows && c + N <= cols && ((uintptr_t)base & 7) == 0) {
+    const uint2 x = *reinterpret_cast<const uint2 *>(base);
+    w[0] = x.x;
+    w[1] = x.y;
+  } else if (N >= 4 && r < rows && c + N <= cols && ((uintptr_t)base & 15) == 0) {
 #pragma unroll
     for (int i = 0; i < N / 4; ++i) {
       const uint4 x = *reinterpret_cast<const uint4 *>(base + 16 * i);
@@ -412,7 +427,8 @@ __device__ __forceinline__ void level_emit(const uint32_t (&v)[4][N], uint32_t p
   uint32_t x[N], y[N], z[N];
   auto put = [&](int i, const uint32_t (&t)[N]) {
     if constexpr (N == 8) emit8<MODE>(t, p, fs, out + i * ostride + off, plane);
-    else emit4<MODE>(t, p, fs, out + i * ostride + off, plane);
+    else if constexpr (N == 4) emit4<MODE>(t, p, fs, out + i * ostride + off, plane);
+    else emit2<MODE>(t, p, fs, out + i * ostride + off, plane);
   };
   if (SIDE == 0) {
     put(0, v[0]);  // A11
@@ -463,47 +479,56 @@ __device__ __forceinline__ void level_prefetch(const PackLevel &L, int side, int
     }
 }
 
-// plain side (A): a thread takes 4 consecutive columns of one row of every
-// sub-block (64 values in registers), then writes every level's outputs
+// plain side (A): a thread takes kLvlRowN consecutive columns of one row of
+// every sub-block (16 kLvlRowN values in registers), then writes every
+// level's outputs.  Two columns a thread halve the registers and double the
+// resident warps, but measured slower (277 against 235 us at 8192^2 depth
+// 2); three quarters of the pass's bytes are stores, which then go out in
+// half-width instructions.
+constexpr int kLvlRowN = 4;
 template <int MODE>
 __global__ void __launch_bounds__(256) level_rows_kernel(const __grid_constant__ PackLevel L) {
+  constexpr int N = kLvlRowN;
   const int rows = L.rows[0], cols = L.cols[0], pc = L.pcol_pad[0];
-  const int64_t units = (int64_t)L.prow_pad[0] * (pc / 4);
+  const int64_t units = (int64_t)L.prow_pad[0] * (pc / N);
   const int64_t plane = (int64_t)L.prow_pad[0] * pc;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < units; u += stride) {
-    const int r = (int)(u / (pc / 4));
-    const int c0 = (int)(u - (int64_t)r * (pc / 4)) * 4;
-    uint32_t w[4][4][4];
+    const int r = (int)(u / (pc / N));
+    const int c0 = (int)(u - (int64_t)r * (pc / N)) * N;
+    uint32_t w[4][4][N];
 #pragma unroll
     for (int Q = 0; Q < 4; ++Q)
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        load_row<4>(L.src[0][Q][q], L.ld[0][Q], r, c0, rows, cols, w[Q][q], L.esz[0][Q]);
+        load_row<N>(L.src[0][Q][q], L.ld[0][Q], r, c0, rows, cols, w[Q][q], L.esz[0][Q]);
 #pragma unroll
-        for (int e = 0; e < 4; ++e) w[Q][q][e] = source_value<MODE>(w[Q][q][e], L.p, L.barrett);
+        for (int e = 0; e < N; ++e) w[Q][q][e] = source_value<MODE>(w[Q][q][e], L.p, L.barrett);
       }
     for (int j = 0; j < L.n; ++j) {
-      uint32_t v[4][4];
-      level_sources<MODE, 4>(L, 0, j, w, v);
+      uint32_t v[4][N];
+      level_sources<MODE, N>(L, 0, j, w, v);
       const float fs = MODE == MODE_FP32 ? fp16_scale(L.amax[0], L.terms[0][j]) : 1.f;
-      level_emit<MODE, 4, 0>(v, L.p, fs, L.out[0][j], L.ostride[0], (int64_t)r * pc + c0, plane);
+      level_emit<MODE, N, 0>(v, L.p, fs, L.out[0][j], L.ostride[0], (int64_t)r * pc + c0, plane);
     }
   }
 }
 
-// transposed side (B): a block stages a 64 (source rows) x 16 (source cols)
-// tile of every sub-block in shared memory; a thread then takes 4 source
-// rows of one source column (packed row = that column; 16 threads write 128
-// contiguous bytes of it) and writes every level's outputs
-constexpr int kLvlTileK = 64, kLvlTileN = 16;
+// transposed side (B): a block of kLvlColThreads stages a 64 (source rows)
+// x 16 (source cols) tile of every sub-block in shared memory; a thread then
+// takes 2 source rows of one source column (packed row = that column; 32
+// threads write 128 contiguous bytes of it) and writes every level's
+// outputs.  Persistent over the tiles, with an L2 prefetch of the next one.
+constexpr int kLvlTileK = 64, kLvlTileN = 16, kLvlColThreads = 512;
 template <int MODE>
-__global__ void __launch_bounds__(256) level_cols_kernel(const __grid_constant__ PackLevel L, int tiles_x, int tiles) {
+__global__ void __launch_bounds__(kLvlColThreads, 2)
+    level_cols_kernel(const __grid_constant__ PackLevel L, int tiles_x, int tiles) {
   extern __shared__ uint32_t lvl_tile[];  // [16][kLvlTileK][kLvlTileN + 1]
   constexpr int W = kLvlTileN + 1;
   const int rows = L.rows[1], cols = L.cols[1], pc = L.pcol_pad[1];
   const int64_t plane = (int64_t)L.prow_pad[1] * pc;
-  const int t = threadIdx.x, rr = t >> 2, cc = (t & 3) * 4;
+  const int t = threadIdx.x, rr = t >> 3, cc = (t & 7) * 2;  // load: 64 rows x 8 pairs
+  const int pcol = t >> 5, pr2 = (t & 31) * 2;                // emit: 16 columns x 32 row pairs
   for (int i = blockIdx.x; i < tiles; i += gridDim.x) {
     const int bx = i % tiles_x, by = i / tiles_x;
     const int r0 = by * kLvlTileK, c0 = bx * kLvlTileN;
@@ -512,10 +537,10 @@ __global__ void __launch_bounds__(256) level_cols_kernel(const __grid_constant__
     for (int Q = 0; Q < 4; ++Q)
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        uint32_t x[4];
-        load_row<4>(L.src[1][Q][q], L.ld[1][Q], r0 + rr, c0 + cc, rows, cols, x, L.esz[1][Q]);
+        uint32_t x[2];
+        load_row<2>(L.src[1][Q][q], L.ld[1][Q], r0 + rr, c0 + cc, rows, cols, x, L.esz[1][Q]);
 #pragma unroll
-        for (int e = 0; e < 4; ++e)
+        for (int e = 0; e < 2; ++e)
           lvl_tile[((Q * 4 + q) * kLvlTileK + rr) * W + cc + e] = source_value<MODE>(x[e], L.p, L.barrett);
       }
     __syncthreads();
@@ -523,19 +548,18 @@ __global__ void __launch_bounds__(256) level_cols_kernel(const __grid_constant__
       const int in = i + gridDim.x;
       level_prefetch(L, 1, (in / tiles_x) * kLvlTileK + rr, (in % tiles_x) * kLvlTileN + cc);
     }
-    const int pcol = t >> 4, pr4 = (t & 15) * 4;
-    uint32_t w[4][4][4];
+    uint32_t w[4][4][2];
 #pragma unroll
     for (int Q = 0; Q < 4; ++Q)
 #pragma unroll
       for (int q = 0; q < 4; ++q)
 #pragma unroll
-        for (int e = 0; e < 4; ++e) w[Q][q][e] = lvl_tile[((Q * 4 + q) * kLvlTileK + pr4 + e) * W + pcol];
+        for (int e = 0; e < 2; ++e) w[Q][q][e] = lvl_tile[((Q * 4 + q) * kLvlTileK + pr2 + e) * W + pcol];
     for (int j = 0; j < L.n; ++j) {
-      uint32_t v[4][4];
-      level_sources<MODE, 4>(L, 1, j, w, v);
+      uint32_t v[4][2];
+      level_sources<MODE, 2>(L, 1, j, w, v);
       const float fs = MODE == MODE_FP32 ? fp16_scale(L.amax[1], L.terms[1][j]) : 1.f;
-      level_emit<MODE, 4, 1>(v, L.p, fs, L.out[1][j], L.ostride[1], (int64_t)(c0 + pcol) * pc + r0 + pr4, plane);
+      level_emit<MODE, 2, 1>(v, L.p, fs, L.out[1][j], L.ostride[1], (int64_t)(c0 + pcol) * pc + r0 + pr2, plane);
     }
   }
 }
@@ -1492,7 +1516,7 @@ cudaError_t launch_pack_pair(const PackArgs &a, const PackArgs &b, int mode, cud
 template <int MODE>
 static cudaError_t level_mode(const PackLevel &L, int side, cudaStream_t s) {
   if (side == 0) {
-    const int64_t units = (int64_t)L.prow_pad[0] * (L.pcol_pad[0] / 4);
+    const int64_t units = (int64_t)L.prow_pad[0] * (L.pcol_pad[0] / dev::kLvlRowN);
     const int64_t want = (units + 255) / 256;
     const int na = (int)(want > 152 * 8 ? 152 * 8 : want);
     if (na > 0) dev::level_rows_kernel<MODE><<<na, 256, 0, s>>>(L);
@@ -1506,8 +1530,8 @@ static cudaError_t level_mode(const PackLevel &L, int side, cudaStream_t s) {
     attr_set = true;
   }
   const int tiles_x = L.prow_pad[1] / dev::kLvlTileN, tiles = tiles_x * (L.pcol_pad[1] / dev::kLvlTileK);
-  const int grid = tiles < 152 * 2 ? tiles : 152 * 2;  // two resident blocks per SM (registers)
-  if (tiles > 0) dev::level_cols_kernel<MODE><<<grid, 256, smem, s>>>(L, tiles_x, tiles);
+  const int grid = tiles < 152 * 2 ? tiles : 152 * 2;  // two resident blocks per SM
+  if (tiles > 0) dev::level_cols_kernel<MODE><<<grid, dev::kLvlColThreads, smem, s>>>(L, tiles_x, tiles);
   return cudaGetLastError();
 }
 
