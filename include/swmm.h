@@ -170,7 +170,10 @@ typedef struct {
   int64_t staging_bytes;      /* device bytes of tensor-core operand staging
                                  (packed limb planes of the leaf operands;
                                  not part of the schedules' temporaries) */
-  int64_t reserved[7];
+  int64_t pack_bytes;         /* bytes the operand packs read and write */
+  int64_t level_packs;        /* table levels whose fused levels' operands
+                                 were formed in one pass */
+  int64_t reserved[5];
 } swmm_stats;
 
 /* Create a handle bound to CUDA device `device` and stream `cuda_stream`
@@ -293,6 +296,16 @@ int swmm_autotune(swmm_t h, int64_t m, int64_t k, int64_t n, int32_t mode, uint3
 int swmm_workspace_elems(swmm_t h, int64_t m, int64_t k, int64_t n,
                          const swmm_opts *opts, int64_t *paper_elems,
                          int64_t *plan_elems);
+
+/* The counts of the plan for (m, k, n, opts) as an eager call would run it,
+ * in *out (the fields of swmm_stats; staging_bytes for an eager call, whose
+ * fused levels share one staging area unless launches are merged): the
+ * planning pass of the library, with no operands and no device work.  The
+ * entry point is the one the schedule's contract implies (as
+ * swmm_workspace_elems), with unit scalars; the final canonical pass over
+ * blocks of C last written by reduce-adds, which only a real call knows,
+ * is not counted.  h may be NULL. */
+int swmm_plan_stats(swmm_t h, int64_t m, int64_t k, int64_t n, const swmm_opts *opts, swmm_stats *out);
 
 /* Leaf GEMM timing recorded by calls made with SWMM_FLAG_TIMING since the
  * last reset.  Waits for the handle's stream, then returns the summed

@@ -503,6 +503,15 @@ void canon_lazy(Exec &r, const View &b) {
   for (const View &v : lazy_in(r, b)) r.canon(v);
 }
 
+// Staging areas a run of plan x uses in turn: one area per table level
+// packed in one pass (two when there are several), four for merged leaf
+// launches, two for fused levels under the dataflow capture, else one.
+int stage_slots_for(const Exec &x, bool merge, bool use_flow) {
+  if (x.level_packs) return x.level_packs > 1 ? 2 : 1;
+  if (merge) return 4;
+  return use_flow && x.stage_budget == 0 ? 2 : 1;
+}
+
 // Issue a planned call on `stream`: workspace, kernels, final canonical
 // pass, release.  Adds its counters to `st`.
 int enqueue(swmm_t h, const Plan &P, cudaStream_t stream, TimingHook *timing, const Scratch *ext, swmm_stats &st,
@@ -510,7 +519,7 @@ int enqueue(swmm_t h, const Plan &P, cudaStream_t stream, TimingHook *timing, co
   const Exec &x = P.x;
   Exec r = x;
   r.merge = x.merge && !ext;
-  r.stage_slots = x.level_packs ? (x.level_packs > 1 ? 2 : 1) : (r.merge ? 4 : (use_flow && x.stage_budget == 0 ? 2 : 1));
+  r.stage_slots = stage_slots_for(x, r.merge, use_flow);
   const int64_t stage_bytes = r.stage_slots * ((x.stage_need + 1023) / 1024 * 1024);
   r.dry = false;
   r.lazy_views.clear();
@@ -614,6 +623,8 @@ int enqueue(swmm_t h, const Plan &P, cudaStream_t stream, TimingHook *timing, co
   st.leaf_launches += r.leaf_launches;
   st.ew_launches += r.ew_launches;
   st.leaf_products += r.leaf_products;
+  st.pack_bytes += r.pack_bytes;
+  st.level_packs += r.level_packs;
   if (r.cuda_err != cudaSuccess) return fail(h, SWMM_ECUDA, r.fail);
   if (!r.fail.empty()) return fail(h, SWMM_EINVAL, r.fail);
   return SWMM_OK;
@@ -857,8 +868,9 @@ int plan_only(swmm_t h, int64_t m, int64_t k, int64_t n, const swmm_opts *opts, 
     acc_inplace = !ro && h->custom.accumulate;
   }
   static const uint32_t one = 1;
-  return make_plan(h, placeholder_req(entry, m, k, n, &one, acc_inplace || entry == 1 ? &one : nullptr), opts, false,
-                   P);
+  static const float onef = 1.f;
+  const void *u = opts->mode == SWMM_FP32 ? (const void *)&onef : (const void *)&one;
+  return make_plan(h, placeholder_req(entry, m, k, n, u, acc_inplace || entry == 1 ? u : nullptr), opts, false, P);
 }
 
 // The handle's own schedule: checked in the pebble game, lowered to rows.
@@ -1022,6 +1034,30 @@ int swmm_workspace_elems(swmm_t h, int64_t m, int64_t k, int64_t n, const swmm_o
   if (rc != SWMM_OK) return rc;
   if (paper_out) *paper_out = P.paper;
   if (plan_out) *plan_out = P.x.tmp_peak_elems;
+  return SWMM_OK;
+}
+
+int swmm_plan_stats(swmm_t h, int64_t m, int64_t k, int64_t n, const swmm_opts *opts, swmm_stats *out) {
+  swmm_ctx planner;  // planning needs no device: a NULL handle is accepted
+  if (!h) h = &planner;
+  h->last_error.clear();
+  if (!out) return fail(h, SWMM_EINVAL, "out is NULL");
+  Plan P;
+  const int rc = plan_only(h, m, k, n, opts, P);
+  if (rc != SWMM_OK) return rc;
+  const Exec &x = P.x;
+  std::memset(out, 0, sizeof(*out));
+  out->workspace_bytes = x.ws_peak;
+  out->plan_extra_elems = x.tmp_peak_elems;
+  out->paper_extra_elems = P.paper;
+  out->add_elems = x.add_elems;
+  out->leaf_flops = x.leaf_flops;
+  out->leaf_launches = x.leaf_launches;
+  out->ew_launches = x.ew_launches;
+  out->leaf_products = x.leaf_products;
+  out->staging_bytes = x.stage_need > 0 ? stage_slots_for(x, x.merge, false) * ((x.stage_need + 1023) / 1024 * 1024) : 0;
+  out->pack_bytes = x.pack_bytes;
+  out->level_packs = x.level_packs;
   return SWMM_OK;
 }
 

@@ -48,7 +48,8 @@ class _Stats(ctypes.Structure):
                 ("paper_extra_elems", ctypes.c_int64), ("add_elems", ctypes.c_int64),
                 ("leaf_flops", ctypes.c_int64), ("leaf_launches", ctypes.c_int64),
                 ("ew_launches", ctypes.c_int64), ("leaf_products", ctypes.c_int64),
-                ("staging_bytes", ctypes.c_int64), ("reserved", ctypes.c_int64 * 7)]
+                ("staging_bytes", ctypes.c_int64), ("pack_bytes", ctypes.c_int64),
+                ("level_packs", ctypes.c_int64), ("reserved", ctypes.c_int64 * 5)]
 
 
 class Problem(ctypes.Structure):
@@ -65,7 +66,7 @@ EXPORTS = ["swmm_create", "swmm_destroy", "swmm_set_stream", "swmm_mul", "swmm_m
            "swmm_mul_inplace",
            "swmm_muladd_batched", "swmm_autotune", "swmm_workspace_elems", "swmm_leaf_timing", "swmm_get_stats",
            "swmm_sync", "swmm_strerror", "swmm_last_error", "swmm_matvec", "swmm_residual", "swmm_muladd_host",
-           "swmm_test_hook", "swmm_memory_use",
+           "swmm_test_hook", "swmm_memory_use", "swmm_plan_stats",
            # include/swmm_search.h (host only, see search.py)
            "swmm_schedule_search", "swmm_schedule_check", "swmm_search_node_name", "swmm_search_node_count",
            "swmm_set_schedule", "swmm_schedule_workspace", "swmm_table_rows"]
@@ -147,6 +148,17 @@ def autotune(m, k, n, mode=MODP, p=65521):
     if rc != OK:
         raise SwmmError(rc, "autotune failed")
     return s.value, d.value, t.value, e.value
+
+
+def plan_stats(m, k, n, opts) -> dict:
+    """The counts of the plan an eager call with these sizes and options
+    would run (swmm_plan_stats); no GPU needed."""
+    lib = load()
+    st = _Stats()
+    rc = lib.swmm_plan_stats(None, m, k, n, ctypes.byref(opts.c()), ctypes.byref(st))
+    if rc != OK:
+        raise SwmmError(rc, "planning failed")
+    return {f: getattr(st, f) for f, _ in _Stats._fields_ if f != "reserved"}
 
 
 def _scalar(mode, v):

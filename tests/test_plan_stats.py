@@ -1,0 +1,69 @@
+"""The planning pass's counts on the CPU (swmm_plan_stats): level packs,
+staging, additions and launches derived from the tables by hand.
+
+Table 9 at 8192^2 depth 2 (C <- AB + C, read-only A and B): the top level's
+eight S/T rows are recorded as sums and its seven fused levels are packed in
+one pass per side (2 launches) reading A and B once (2 x 8192^2 x 4 B) and
+writing 49 operand pairs of 2 limb planes of 2048 x 2048 fp16 per operand;
+the seven C-side rows (Z1, Z3, W1, U2, U1, U5, U7) each touch a 4096^2
+block, and the product P1, which Table 9 writes into a temporary without
+accumulation, needs that temporary zeroed first: 10 elementwise launches.
+Table 1 at 16384^2 depth 3: the top level runs its 15 rows; each of the
+seven level-2 Table 1 calls packs in one pass (2), runs its 7 C-side rows
+and zeroes the destination of each of its 7 non-accumulating fused levels:
+15 + 7 x 16 = 127.
+"""
+import pytest
+
+from paper_0707_2347_gb300 import swmm as S
+
+PAIR = 2 * (2 * 2048 * 2048 * 2)  # A and B operand of one 2048^3 product, 2 fp16 limb planes each
+
+
+def test_table9_level_pack_counts():
+    n = 8192
+    st = S.plan_stats(n, n, n, S.Opts(mode=S.MODP, p=65521, sched=S.T9_ACC, depth=2))
+    assert st["level_packs"] == 1
+    assert st["staging_bytes"] == 49 * PAIR
+    assert st["pack_bytes"] == 4 * 2 * n * n + 49 * PAIR
+    assert st["ew_launches"] == 2 + 7 + 1
+    assert st["add_elems"] == 7 * (n // 2) ** 2
+    assert st["leaf_products"] == 49 and st["leaf_flops"] == 49 * 2 * (n // 4) ** 3
+    assert st["plan_extra_elems"] == st["paper_extra_elems"] == 2 * (n // 2) ** 2
+
+
+def test_bounded_staging_and_inplace_tables_pack_per_level():
+    n = 8192
+    low = S.plan_stats(n, n, n, S.Opts(mode=S.MODP, p=65521, sched=S.T9_ACC, depth=2, flags=S.FLAG_LOWMEM))
+    assert low["level_packs"] == 0 and low["staging_bytes"] <= S.LOWMEM_STAGE_BYTES
+    # Table 3 overwrites operand quadrants between its products
+    ip = S.plan_stats(n, n, n, S.Opts(mode=S.MODP, p=65521, sched=S.T3_IP, depth=2))
+    assert ip["level_packs"] == 0 and ip["staging_bytes"] == 7 * PAIR
+
+
+def test_table1_depth3_counts():
+    """Every level-2 table of Table 1 (read-only, C <- AB) packs in one pass;
+    planned with disjoint placeholder addresses, no recorded sum is written
+    out because some unrelated block was written (with every placeholder at
+    address 0 the count was higher)."""
+    n = 16384
+    st = S.plan_stats(n, n, n, S.Opts(mode=S.MODP, p=65521, sched=S.T1_DHSS, depth=3))
+    assert st["level_packs"] == 7
+    assert st["ew_launches"] == 15 + 7 * (2 + 7 + 7)
+    assert st["leaf_products"] == 343
+
+
+def test_fp32_level_pack_stages_amax_words():
+    n = 16384
+    st = S.plan_stats(n, n, n, S.Opts(mode=S.FP32, sched=S.T9_ACC, depth=2))
+    pair = 2 * (2 * 4096 * 4096 * 2)
+    assert st["level_packs"] == 1
+    assert st["staging_bytes"] == 49 * pair + 1024  # the amax words share the area
+    assert st["ew_launches"] == 3 + 7 + 1  # amax pass, two level-pack launches
+
+
+def test_plan_stats_rejects_bad_options():
+    with pytest.raises(S.SwmmError):  # Table 3 needs k = n <= m
+        S.plan_stats(500, 1000, 1000, S.Opts(mode=S.MODP, p=65521, sched=S.T3_IP, depth=2))
+    with pytest.raises(S.SwmmError):  # p must satisfy 2 < p < 2^16
+        S.plan_stats(100, 100, 100, S.Opts(mode=S.MODP, p=1, sched=S.T9_ACC, depth=1))
