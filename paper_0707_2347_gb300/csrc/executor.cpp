@@ -915,8 +915,10 @@ void Exec::table(Kind k, Scalar alpha, bool acc, Scalar beta, View L, View R, Vi
   Lin sym[NLOC];
   View symdst[NLOC];
   bool has[NLOC] = {};
+  bool dirty[NLOC] = {};  // written by a row (not a recorded sum) in this call
   auto is_tmp = [](Loc l) { return l == LX || l == LY || l == LZ; };
   auto sym_dst = [&](Loc l) { return is_tmp(l) || (l >= C11 && l <= C22); };  // may hold a recorded sum
+  auto operand_loc = [](Loc l) { return l >= A11 && l <= B22; };
   auto operand_quad = [](Loc l, Shape sh) {
     return (sh == SH_A && l >= A11 && l <= A22) || (sh == SH_B && l >= B11 && l <= B22);
   };
@@ -924,6 +926,7 @@ void Exec::table(Kind k, Scalar alpha, bool acc, Scalar beta, View L, View R, Vi
   auto materialize = [&](Loc l) {
     if (!has[l]) return;
     has[l] = false;
+    dirty[l] = true;
     const Lin &v = sym[l];
     const View &d = symdst[l];
     if (v.n == 1) {
@@ -990,38 +993,48 @@ void Exec::table(Kind k, Scalar alpha, bool acc, Scalar beta, View L, View R, Vi
   if (level_pack_size && stage_budget == 0) {
     int nmul = 0;
     bool okp = true;
-    bool hs[NLOC] = {};
+    bool hs[NLOC] = {}, dirty[NLOC] = {};
     Lin ss[NLOC];
+    // an operand quadrant is a term only while it holds its input value
     auto operand = [&](Loc l, Shape sh, Lin &out) {
       if (hs[l]) {
         out = ss[l];
         return true;
       }
-      if (!operand_quad(l, sh)) return false;
+      if (!operand_quad(l, sh) || dirty[l]) return false;
       out = Lin::of(at(l, sh));
       return true;
     };
+    // a row writes location l (shape sh): a recorded sum with a term there
+    // would have to be written out first
+    auto written = [&](Loc l, Shape sh) {
+      dirty[l] = true;
+      hs[l] = false;
+      const Rect rw = rect_of(at(l, sh));
+      for (int li = 0; li < NLOC; ++li)
+        for (int t = 0; hs[li] && t < ss[li].n; ++t)
+          if (overlaps(rect_of(ss[li].v[t]), rw)) okp = false;
+    };
     for (const Row &row : *K.table) {
-      if ((row.dst >= A11 && row.dst <= A22) || (row.dst >= B11 && row.dst <= B22)) okp = false;
       if (!okp) break;
       if (row.op == OP_ADD) {
         const bool unit = (row.c1 == CF_ONE || row.c1 == CF_NEG) && (row.c2 == CF_ONE || row.c2 == CF_NEG);
         Lin x, y, r;
-        if (unit && sym_dst(row.dst) && row.shape != SH_C && operand(row.s1, row.shape, x) &&
+        if (unit && (sym_dst(row.dst) || operand_loc(row.dst)) && row.shape != SH_C && operand(row.s1, row.shape, x) &&
             operand(row.s2, row.shape, y) && compose(x, row.c1 == CF_ONE ? 1 : -1, y, row.c2 == CF_ONE ? 1 : -1, r)) {
           ss[row.dst] = r;
           hs[row.dst] = true;
           continue;
         }
         okp = !hs[row.s1] && !hs[row.s2];  // a recorded sum would be written out
-        hs[row.dst] = false;
+        written(row.dst, row.shape);
       } else if (row.op == OP_COPY) {
         okp = !hs[row.s1];
-        hs[row.dst] = false;
+        written(row.dst, row.shape);
       } else {
         okp = nmul < 7 && operand(row.s1, SH_A, pla[nmul]) && operand(row.s2, SH_B, plb[nmul]);
         ++nmul;
-        hs[row.dst] = false;
+        if (okp) written(row.dst, SH_C);
       }
     }
     // each level's operand over the four operand quadrants of its side
@@ -1102,6 +1115,11 @@ void Exec::table(Kind k, Scalar alpha, bool acc, Scalar beta, View L, View R, Vi
       }
     }
   }
+  // With one pass packing the level, operand quadrants are read before any
+  // row runs: a quadrant a row has written (dirty) is no longer a term, and
+  // sums may be recorded in operand quadrants too (in-place tables park
+  // them there; the blocks keep their input values).
+  auto quad_term = [&](Loc l, Shape sh) { return operand_quad(l, sh) && !(prepacked && dirty[l]); };
   int jmul = 0;
   auto same_lin = [&](const Lin &x, const Lin &y) {
     if (x.n != y.n) return false;
@@ -1118,8 +1136,8 @@ void Exec::table(Kind k, Scalar alpha, bool acc, Scalar beta, View L, View R, Vi
       nar[row.dst] = nd;
       bool recorded = false;
       const bool unit = (row.c1 == CF_ONE || row.c1 == CF_NEG) && (row.c2 == CF_ONE || row.c2 == CF_NEG);
-      if (virt && unit && sym_dst(row.dst) && row.shape != SH_C &&
-          (has[row.s1] || operand_quad(row.s1, row.shape)) && (has[row.s2] || operand_quad(row.s2, row.shape))) {
+      if (virt && unit && (sym_dst(row.dst) || (prepacked && operand_loc(row.dst))) && row.shape != SH_C &&
+          (has[row.s1] || quad_term(row.s1, row.shape)) && (has[row.s2] || quad_term(row.s2, row.shape))) {
         Lin r;
         const Lin x = has[row.s1] ? sym[row.s1] : Lin::of(a), y = has[row.s2] ? sym[row.s2] : Lin::of(b);
         if (compose(x, row.c1 == CF_ONE ? 1 : -1, y, row.c2 == CF_ONE ? 1 : -1, r)) {
@@ -1134,6 +1152,7 @@ void Exec::table(Kind k, Scalar alpha, bool acc, Scalar beta, View L, View R, Vi
         materialize(row.s2);
         before_write(d);
         has[row.dst] = false;
+        dirty[row.dst] = true;
         add(d, a, b, coef(row.c1), coef(row.c2));
       }
     } else if (row.op == OP_COPY) {
@@ -1144,6 +1163,7 @@ void Exec::table(Kind k, Scalar alpha, bool acc, Scalar beta, View L, View R, Vi
       materialize(row.s1);
       before_write(d);
       has[row.dst] = false;
+      dirty[row.dst] = true;
       ++ew_launches;
       add_elems += d.rows * d.cols;
       {  // a copy keeps the source's representatives
@@ -1167,6 +1187,7 @@ void Exec::table(Kind k, Scalar alpha, bool acc, Scalar beta, View L, View R, Vi
       const View d = at(row.dst, SH_C);
       const Scalar al = coef(row.c1), be = row.acc ? coef(row.cacc) : Scalar{};
       before_write(d);
+      dirty[row.dst] = true;
       if (virt) {
         // a fused level reads its operands (symbolic or not) and writes d
         const Lin la = has[row.s1] ? sym[row.s1] : Lin::of(a), lb = has[row.s2] ? sym[row.s2] : Lin::of(b);

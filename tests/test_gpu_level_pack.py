@@ -83,10 +83,10 @@ def test_inplace_table_keeps_level_packs(handle):
 def test_searched_schedules_symbolic_at_8192(handle, name):
     """The shipped searched schedules at 8192^2 depth 2, where the top
     level's pre-additions are symbolic: ab12 parks S and T values in blocks
-    of C (recorded, not written, then packed in one pass with the other
-    levels); aclr14 and accr14 overwrite operand quadrants (per-level
-    packs).  Sampled rows against the oracle, Freivalds on the whole result,
-    and the restored inputs bit-exact."""
+    of C, aclr14 and accr14 in operand quadrants they may overwrite
+    (recorded, not written; packed in one pass where no product is stored
+    in a quadrant a later product reads).  Sampled rows against the oracle,
+    Freivalds on the whole result, and the preserved inputs bit-exact."""
     from paper_0707_2347_gb300 import schedules_found as F
     from paper_0707_2347_gb300 import search as Q
     rows_, spec = F.rows(name), F.spec(name)

@@ -32,13 +32,31 @@ def test_table9_level_pack_counts():
     assert st["plan_extra_elems"] == st["paper_extra_elems"] == 2 * (n // 2) ** 2
 
 
-def test_bounded_staging_and_inplace_tables_pack_per_level():
+def test_bounded_staging_and_inplace_tables():
+    """Bounded staging never packs a whole level.  Tables 3, 4 and 5 store
+    products in operand quadrants that later products read, so their
+    levels pack one at a time; Tables 6, 7 and 8 only park S and T sums in
+    operand quadrants (recorded, the blocks keep their input values until
+    the products are written), so they pack in one pass."""
     n = 8192
     low = S.plan_stats(n, n, n, S.Opts(mode=S.MODP, p=65521, sched=S.T9_ACC, depth=2, flags=S.FLAG_LOWMEM))
     assert low["level_packs"] == 0 and low["staging_bytes"] <= S.LOWMEM_STAGE_BYTES
-    # Table 3 overwrites operand quadrants between its products
-    ip = S.plan_stats(n, n, n, S.Opts(mode=S.MODP, p=65521, sched=S.T3_IP, depth=2))
-    assert ip["level_packs"] == 0 and ip["staging_bytes"] == 7 * PAIR
+    for sched in (S.T3_IP, S.T4_OVL, S.T5_OVR):
+        st = S.plan_stats(n, n, n, S.Opts(mode=S.MODP, p=65521, sched=sched, depth=2))
+        assert st["level_packs"] == 0 and st["staging_bytes"] == 7 * PAIR, sched
+    for sched in (S.T6_ACLR, S.T7_ACCR, S.T8_ACR):
+        st = S.plan_stats(n, n, n, S.Opts(mode=S.MODP, p=65521, sched=sched, depth=2))
+        assert st["level_packs"] == 1 and st["staging_bytes"] == 49 * PAIR, sched
+
+
+def test_table9_depth3_every_level2_call_packs_once():
+    """8192^2 depth 3: all seven level-2 calls (four by Table 9, one by
+    Table 1, one each by Tables 6 and 7) pack in one pass, two areas in
+    turn."""
+    n = 8192
+    st = S.plan_stats(n, n, n, S.Opts(mode=S.MODP, p=65521, sched=S.T9_ACC, depth=3))
+    assert st["level_packs"] == 7
+    assert st["staging_bytes"] == 2 * 49 * (2 * (2 * 1024 * 1024 * 2))
 
 
 def test_table1_depth3_counts():
