@@ -238,7 +238,7 @@ int swmm_muladd_host(swmm_t h, int64_t m, int64_t k, int64_t n, const void *alph
  * memory (the paper has no counterpart: it is a deployment variant).  Code
  * running where cudaMalloc/cudaMallocAsync are unavailable or forbidden --
  * inside a memory budget owned by another allocator, in a real-time path
- * that must not reach the driver's allocator, or in a process whose pools
+ * that must not reach the CUDA driver's allocator, or in a process whose pools
  * are reserved -- gets the schedule's temporaries and the tensor-core
  * operand staging from one static device array of
  * SWMM_NOALLOC_SCRATCH_BYTES bytes that every GPU which loads the library

@@ -1,7 +1,7 @@
 """swmm_muladd_noalloc: the allocation-free variant of swmm_muladd.
 
 Some callers cannot call cudaMalloc (their memory budget belongs to another
-allocator, or they run where reaching the driver's allocator is not
+allocator, or they run where reaching the CUDA driver's allocator is not
 allowed).  This entry point takes its scratch from a static device array
 instead.  The test calls it through the C ABI twice in a row and checks each
 result against the regular entry point on the same inputs; it also checks
