@@ -273,7 +273,7 @@ void reset_counts(Exec &x) {
   x.ws_top = x.ws_peak = x.stage_need = 0;
   x.tmp_elems = x.tmp_peak_elems = 0;
   x.add_elems = x.leaf_flops = x.leaf_launches = x.ew_launches = x.leaf_products = 0;
-  x.pack_bytes = 0;
+  x.pack_bytes = x.level_pack_bytes = 0;
   x.level_packs = 0;
   x.lazy_views.clear();
   x.stage_turn = 0;
@@ -825,7 +825,10 @@ std::vector<Plan> group_classical(std::vector<Plan> &each) {
 // ---------------------------------------------------------------- autotuner
 // Cost model of a planned call on one GB300 (microseconds): tensor work at a
 // rate that falls with small leaf products, HBM-bound passes, and a fixed
-// cost per launch.
+// cost per launch.  Additions and per-level packs move about 5.5 TB/s; the
+// one-pass level packs, whose stores are three quarters of their bytes,
+// about 4.2 TB/s (measured: 8.7 GB in 1.99 ms at 16384^2 depth 2, 0.55 GB
+// in 0.134 ms per level-2 table at 8192^2 depth 3).
 double model_us(const Plan &P) {
   const Exec &x = P.x;
   const double limbs = x.mode == MODE_MODP1 ? 1.0 : (x.mode == MODE_MODP2 ? 4.0 : 3.0);
@@ -833,10 +836,13 @@ double model_us(const Plan &P) {
   const double per_product = x.leaf_products ? (double)x.leaf_flops / (double)x.leaf_products : 0.0;
   const double tiles = per_product / (2.0 * 128.0 * 128.0 * 1024.0);  // 128 x 128 x 1024 tile units
   const double eff = 0.95 * tiles / (tiles + 6.0) + 0.05;
-  const double rate = 1.75e9 * eff;  // flop/us at the sustained tensor peak
-  const double bytes = (double)x.add_elems * 12.0 + (double)x.pack_bytes;
+  // limb flop/us at the sustained tensor peak: 1.75e9 for the mod-p limbs,
+  // 1.45e9 for FP32 mode's hi/lo products (16384^3 classical: 1737 against
+  // 1443 TFLOP/s measured, the latter with its amax passes)
+  const double rate = (x.mode == MODE_FP32 ? 1.45e9 : 1.75e9) * eff;
+  const double bytes = (double)x.add_elems * 12.0 + (double)(x.pack_bytes - x.level_pack_bytes);
   const double launches = (double)(x.leaf_launches + x.ew_launches);
-  return flops / rate + bytes / 5.5e6 + launches * 2.5;
+  return flops / rate + bytes / 5.5e6 + (double)x.level_pack_bytes / 4.2e6 + launches * 2.5;
 }
 
 // A call without operands, for planning only: placeholder addresses, never

@@ -1060,6 +1060,7 @@ void Exec::table(Kind k, Scalar alpha, bool acc, Scalar beta, View L, View R, Vi
       stage_need = std::max(stage_need, hdr + 7 * per);
       ew_launches += fp32 ? 3 : 2;
       pack_bytes += 4 * (L.rows * L.cols + R.rows * R.cols) + 7 * per;
+      level_pack_bytes += 4 * (L.rows * L.cols + R.rows * R.cols) + 7 * per;
       if (!dry) {
         char *base = next_stage();
         if (!base) return;

@@ -112,7 +112,8 @@ struct Exec {
   // statistics
   int64_t tmp_elems = 0, tmp_peak_elems = 0;
   int64_t add_elems = 0, leaf_flops = 0, leaf_launches = 0, ew_launches = 0, leaf_products = 0;
-  int64_t pack_bytes = 0;  // bytes the operand packs read and write
+  int64_t pack_bytes = 0;        // bytes the operand packs read and write
+  int64_t level_pack_bytes = 0;  // the part of pack_bytes moved by one-pass level packs
 
   // Blocks holding unreduced representatives mod p (destinations of a fused
   // level's reduce-adds) that no later operation has brought back to
