@@ -528,6 +528,8 @@ int enqueue(swmm_t h, const Plan &P, cudaStream_t stream, TimingHook *timing, co
   r.ws_top = r.ws_peak = 0;
   r.tmp_elems = r.tmp_peak_elems = 0;
   r.add_elems = r.leaf_flops = r.leaf_launches = r.ew_launches = r.leaf_products = 0;
+  r.pack_bytes = r.level_pack_bytes = 0;
+  r.level_packs = 0;  // counted again by the run (the plan's count chose the staging areas)
   r.stage_need = x.stage_need;
   if (ext) {
     // caller-provided scratch: carve, never allocate

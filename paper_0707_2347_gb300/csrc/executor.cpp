@@ -1204,7 +1204,14 @@ void Exec::table(Kind k, Scalar alpha, bool acc, Scalar beta, View L, View R, Vi
       }
     }
   }
-  for (int li = C11; li <= C22 && ok(); ++li) materialize((Loc)li);  // temporaries are dead here
+  // Temporaries are dead here; a sum still recorded in C is written out,
+  // and so is one recorded in an operand block that a row wrote earlier
+  // (the block holds neither its input nor the value the rows define,
+  // which a table that restores the block relies on).  An operand block
+  // never written keeps its input value.
+  for (int li = C11; li <= C22 && ok(); ++li) materialize((Loc)li);
+  for (int li = A11; li <= B22 && ok(); ++li)
+    if (dirty[li]) materialize((Loc)li);
   if (!ar.carve) {
     ws_top = mark_top;
     tmp_elems = mark_elems;

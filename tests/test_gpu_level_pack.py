@@ -116,3 +116,36 @@ def test_searched_schedules_symbolic_at_8192(handle, name):
         M, M0 = (hA, A) if blk[0] == "A" else (hB, B)
         i, j = int(blk[1]) - 1, int(blk[2]) - 1
         assert np.array_equal(M[i * h:(i + 1) * h, j * h:(j + 1) * h], M0[i * h:(i + 1) * h, j * h:(j + 1) * h]), blk
+
+
+@pytest.mark.parametrize("sched,keep,packs", [
+    (S.T6_ACLR, "", 1), (S.T7_ACCR, "A", 1), (S.T8_ACR, "A", 1),
+    (S.T3_IP, "", 0), (S.T4_OVL, "B", 0), (S.T5_OVR, "A", 0)],
+    ids=["AcLR", "AccR", "AcR", "IP", "OvL", "OvR"])
+def test_inplace_tables_at_level_pack_size(handle, sched, keep, packs):
+    """The printed in-place tables at 2048^2 depth 2 (1024^2 quadrants, the
+    smallest that pack in one pass): Tables 6-8 park their sums in operand
+    quadrants as records and pack once, Tables 3-5 pack per level.  The
+    whole result bit for bit against the oracle, and the blocks each table
+    leaves untouched (Table 8 also B11 and B22) bit-identical."""
+    p, n, alpha, beta = 65521, 2048, 3, 5
+    A, B, C = modp_inputs(n, n, n, p, tag=25)
+    dA, dB, dC = dev(A), dev(B), dev(C)
+    o = S.Opts(mode=S.MODP, p=p, sched=sched, depth=2)
+    acc = sched in (S.T6_ACLR, S.T7_ACCR, S.T8_ACR)
+    if acc:
+        handle.mul_inplace(dA, dB, dC, o, alpha=alpha, beta=beta)
+    else:
+        handle.mul_inplace(dA, dB, dC, o, alpha=alpha)
+    handle.sync()
+    assert handle.stats()["level_packs"] == packs
+    want = classical.muladd_modp(alpha, A, B, beta if acc else 0, C, p)
+    assert np.array_equal(host(dC), want)
+    hA, hB = host(dA), host(dB)
+    if "A" in keep:
+        assert np.array_equal(hA, A)
+    if "B" in keep:
+        assert np.array_equal(hB, B)
+    if sched == S.T8_ACR:
+        h = n // 2
+        assert np.array_equal(hB[:h, :h], B[:h, :h]) and np.array_equal(hB[h:, h:], B[h:, h:])
