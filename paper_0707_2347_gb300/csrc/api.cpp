@@ -348,7 +348,10 @@ void execute(const Plan &P, Exec &e) {
     e.call(kind_of(P.sched), P.alpha, P.accum, P.beta, P.L, P.R, P.D, P.depth, Arena{});
 }
 
-int make_plan(swmm_t h, const Req &q, const swmm_opts *o, bool check_ptrs, Plan &P) {
+// level_packs: table levels may pack their fused levels in one pass (off
+// for calls on a caller's static scratch, which must fit the smaller
+// per-level staging)
+int make_plan(swmm_t h, const Req &q, const swmm_opts *o, bool check_ptrs, Plan &P, bool level_packs = true) {
   if (!o) return fail(h, SWMM_EINVAL, "opts is NULL");
   if (o->mode != SWMM_MODP && o->mode != SWMM_FP32) return fail(h, SWMM_EINVAL, "unknown mode");
   if (o->mode == SWMM_MODP && (o->p <= 2 || o->p >= 65536)) return fail(h, SWMM_EINVAL, "p must satisfy 2 < p < 65536");
@@ -424,6 +427,7 @@ int make_plan(swmm_t h, const Req &q, const swmm_opts *o, bool check_ptrs, Plan 
   x.num_sms = h->num_sms;
   x.stage_budget = (o->flags & SWMM_FLAG_LOWMEM) ? h->lowmem_bytes : 0;
   x.wait_ns = h->wait_ns;
+  x.level_pack_ok = level_packs;
   x.stall_left = &h->stall_left;
   x.err = h->d_err;
   x.custom = h->has_custom ? &h->custom_info : nullptr;
@@ -759,7 +763,7 @@ int run(swmm_t h, const Req &q, const swmm_opts *o, const Scratch *ext = nullptr
     if (GraphEntry *g = find_graph(h, key)) return launch_graph(h, g);
   }
   std::vector<Plan> plans(1);
-  int rc = make_plan(h, q, o, true, plans[0]);
+  int rc = make_plan(h, q, o, true, plans[0], ext == nullptr);
   if (rc != SWMM_OK) return rc;
   return run_plans(h, plans, o->flags, ext, key);
 }

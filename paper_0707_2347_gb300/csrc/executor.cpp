@@ -990,7 +990,7 @@ void Exec::table(Kind k, Scalar alpha, bool acc, Scalar beta, View L, View R, Vi
   Prepacked pre[7] = {};
   bool prepacked = false;
   Lin pla[7], plb[7];
-  if (level_pack_size && stage_budget == 0) {
+  if (level_pack_size && stage_budget == 0 && level_pack_ok) {
     int nmul = 0;
     bool okp = true;
     bool hs[NLOC] = {}, dirty[NLOC] = {};

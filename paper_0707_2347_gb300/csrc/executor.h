@@ -91,6 +91,7 @@ struct Exec {
   // pass (each stages one area; two areas in turn when there are several,
   // so one level's pack need not wait for the previous level's products)
   int level_packs = 0;
+  bool level_pack_ok = true;  // the call may pack table levels in one pass
   // dataflow ordering over capture streams (null: every launch on `stream`)
   Flow *flow = nullptr;
   // Deferred leaf GEMM launches: products of leaf groups and fused levels
