@@ -189,6 +189,13 @@ int swmm_schedule_workspace(const swmm_search_spec *spec, const swmm_search_row 
                             int64_t k, int64_t n, const swmm_opts *opts, int64_t *paper_elems,
                             int64_t *plan_elems, double *model_us);
 
+/* The plan's counts for a call of schedule `rows`, as swmm_plan_stats gives
+ * them for the printed schedules (temporaries, staging, additions,
+ * launches, pack bytes, one-pass level packs); no handle, no device.
+ * opts->sched must be SWMM_CUSTOM. */
+int swmm_schedule_stats(const swmm_search_spec *spec, const swmm_search_row *rows, int32_t nrows, int64_t m,
+                        int64_t k, int64_t n, const swmm_opts *opts, swmm_stats *out);
+
 /* The rows of the paper's table `sched` (SWMM_T1_DHSS ... SWMM_T9_ACC,
  * SWMM_T4M_OVL) as the library runs them, in the form swmm_schedule_check
  * and swmm_set_schedule take (node = -1; a recursive call of the table

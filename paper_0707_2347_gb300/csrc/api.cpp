@@ -863,6 +863,24 @@ Req placeholder_req(int entry, int64_t m, int64_t k, int64_t n, const void *alph
              alpha, beta};
 }
 
+// The counts of a planned call, as an eager run would report them (no
+// final canonical pass; the staging of an eager call).
+void plan_counts(const Plan &P, swmm_stats *out) {
+  const Exec &x = P.x;
+  std::memset(out, 0, sizeof(*out));
+  out->workspace_bytes = x.ws_peak;
+  out->plan_extra_elems = x.tmp_peak_elems;
+  out->paper_extra_elems = P.paper;
+  out->add_elems = x.add_elems;
+  out->leaf_flops = x.leaf_flops;
+  out->leaf_launches = x.leaf_launches;
+  out->ew_launches = x.ew_launches;
+  out->leaf_products = x.leaf_products;
+  out->staging_bytes = x.stage_need > 0 ? stage_slots_for(x, x.merge, false) * ((x.stage_need + 1023) / 1024 * 1024) : 0;
+  out->pack_bytes = x.pack_bytes;
+  out->level_packs = x.level_packs;
+}
+
 // The dry run of a call with no operands: the entry point the schedule's
 // contract implies, unit scalars.
 int plan_only(swmm_t h, int64_t m, int64_t k, int64_t n, const swmm_opts *opts, Plan &P) {
@@ -1057,21 +1075,23 @@ int swmm_plan_stats(swmm_t h, int64_t m, int64_t k, int64_t n, const swmm_opts *
   Plan P;
   const int rc = plan_only(h, m, k, n, opts, P);
   if (rc != SWMM_OK) return rc;
-  const Exec &x = P.x;
-  std::memset(out, 0, sizeof(*out));
-  out->workspace_bytes = x.ws_peak;
-  out->plan_extra_elems = x.tmp_peak_elems;
-  out->paper_extra_elems = P.paper;
-  out->add_elems = x.add_elems;
-  out->leaf_flops = x.leaf_flops;
-  out->leaf_launches = x.leaf_launches;
-  out->ew_launches = x.ew_launches;
-  out->leaf_products = x.leaf_products;
-  out->staging_bytes = x.stage_need > 0 ? stage_slots_for(x, x.merge, false) * ((x.stage_need + 1023) / 1024 * 1024) : 0;
-  out->pack_bytes = x.pack_bytes;
-  out->level_packs = x.level_packs;
+  plan_counts(P, out);
   return SWMM_OK;
 }
+
+int swmm_schedule_stats(const swmm_search_spec *spec, const swmm_search_row *rows, int32_t nrows, int64_t m,
+                        int64_t k, int64_t n, const swmm_opts *opts, swmm_stats *out) {
+  swmm_ctx planner;  // no device
+  int rc = set_schedule(&planner, spec, rows, nrows);
+  if (rc != SWMM_OK) return rc;
+  if (!opts || opts->sched != SWMM_CUSTOM || !out) return SWMM_EINVAL;
+  Plan P;
+  rc = plan_only(&planner, m, k, n, opts, P);
+  if (rc != SWMM_OK) return rc;
+  plan_counts(P, out);
+  return SWMM_OK;
+}
+
 
 int swmm_autotune(swmm_t h, int64_t m, int64_t k, int64_t n, int32_t mode, uint32_t p, int32_t *sched,
                   int32_t *depth, double *est_us, int64_t *extra_elems) {

@@ -183,6 +183,18 @@ def schedule_workspace(rows, m, k, n, opts, *, accumulate=False, preserve=(), te
     return _plan(rows, m, k, n, opts, spec)[:2]
 
 
+def schedule_stats(rows, m, k, n, opts, *, accumulate=False, preserve=(), temps=0, kinds=(), max_copies=0,
+                   recompute=False) -> dict:
+    """The plan's counts (swmm_stats fields) for a call of `rows`; no device."""
+    spec = _spec(accumulate, preserve, temps, kinds, -1, max_copies, recompute, MAX_ROWS, 0)
+    st = swmm._Stats()
+    rc = _lib().swmm_schedule_stats(ctypes.byref(spec), _crows(rows), len(rows), m, k, n, ctypes.byref(opts.c()),
+                                    ctypes.byref(st))
+    if rc != swmm.OK:
+        raise swmm.SwmmError(rc, "schedule planning failed")
+    return {f: getattr(st, f) for f, _ in swmm._Stats._fields_ if f != "reserved"}
+
+
 def schedule_model_us(rows, m, k, n, opts, *, accumulate=False, preserve=(), temps=0, kinds=(), max_copies=0,
                       recompute=False):
     """The autotuner's modelled time (microseconds) for a call of `rows`."""

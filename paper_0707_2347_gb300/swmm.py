@@ -69,7 +69,7 @@ EXPORTS = ["swmm_create", "swmm_destroy", "swmm_set_stream", "swmm_mul", "swmm_m
            "swmm_test_hook", "swmm_memory_use", "swmm_plan_stats",
            # include/swmm_search.h (host only, see search.py)
            "swmm_schedule_search", "swmm_schedule_check", "swmm_search_node_name", "swmm_search_node_count",
-           "swmm_set_schedule", "swmm_schedule_workspace", "swmm_table_rows"]
+           "swmm_set_schedule", "swmm_schedule_workspace", "swmm_schedule_stats", "swmm_table_rows"]
 
 _lib = None
 

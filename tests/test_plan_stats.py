@@ -85,3 +85,20 @@ def test_plan_stats_rejects_bad_options():
         S.plan_stats(500, 1000, 1000, S.Opts(mode=S.MODP, p=65521, sched=S.T3_IP, depth=2))
     with pytest.raises(S.SwmmError):  # p must satisfy 2 < p < 2^16
         S.plan_stats(100, 100, 100, S.Opts(mode=S.MODP, p=1, sched=S.T9_ACC, depth=1))
+
+
+def test_searched_schedules_level_packs():
+    """The shipped searched schedules at 8192^2 depth 2: ab12 (parks S and T
+    in C), acc16 and accr14 pack all seven fused levels in one pass;
+    aclr14 stores a product in an operand quadrant that a later product
+    reads and packs per level.  Planned temporaries equal the contract's."""
+    from paper_0707_2347_gb300 import schedules_found as F
+    from paper_0707_2347_gb300 import search as Q
+    n = 8192
+    o = S.Opts(mode=S.MODP, p=65521, sched=S.CUSTOM, depth=2)
+    packs = {"ab12": 1, "acc16": 1, "accr14": 1, "aclr14": 0}
+    for name, want in packs.items():
+        st = Q.schedule_stats(F.rows(name), n, n, n, o, **F.spec(name))
+        assert st["level_packs"] == want, name
+        assert st["staging_bytes"] == (49 if want else 7) * PAIR, name
+        assert st["plan_extra_elems"] == st["paper_extra_elems"], name
