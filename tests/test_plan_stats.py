@@ -102,3 +102,18 @@ def test_searched_schedules_level_packs():
         assert st["level_packs"] == want, name
         assert st["staging_bytes"] == (49 if want else 7) * PAIR, name
         assert st["plan_extra_elems"] == st["paper_extra_elems"], name
+
+
+def test_cost_model_tracks_measured_times():
+    """The autotuner's model of Table 9 (mod 65521) against times measured
+    on a GB300 with graph replays (inputs resident): 16384^2 depth 1 18.63
+    ms, depth 2 18.84 ms, 8192^2 depth 3 4.149 ms, 32768^2 depth 2 135.0
+    ms.  Within 5% each; a ranking aid, not a measurement."""
+    from paper_0707_2347_gb300 import search as Q
+    rows = Q.table_rows(S.T9_ACC)
+    keep = ("A11", "A12", "A21", "A22", "B11", "B12", "B21", "B22")
+    for n, depth, ms in [(16384, 1, 18.63), (16384, 2, 18.84), (8192, 3, 4.149), (32768, 2, 135.0)]:
+        o = S.Opts(mode=S.MODP, p=65521, sched=S.CUSTOM, depth=depth)
+        us = Q.schedule_model_us(rows, n, n, n, o, accumulate=True, preserve=keep, temps=2, kinds=(1, 6, 7, 9),
+                                 recompute=True)
+        assert abs(us / 1000.0 - ms) < 0.05 * ms, (n, depth, us, ms)
